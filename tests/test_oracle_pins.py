@@ -1,0 +1,301 @@
+"""Pins of the CPU FP64 oracle against things other than itself.
+
+Each test ties a piece of the oracle to the mathematics or to a number the
+paper prints: brute force, a library transform, closed forms of Sec. 2.3,
+discrete identities (Parseval, Wiener-Khinchin), symmetries, and the grid rule
+of Tables 1-5.  A plausible mistake in the oracle (dropped chirp, wrong sign,
+transposed operand, wrong ROI origin, wrong zone rule) fails at least one.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+# --------------------------------------------------------------------------
+# Transforms
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 8, 11, 14])
+def test_fft_matches_numpy(oracle_mod, k):
+    rng = np.random.default_rng(k)
+    L = 1 << k
+    x = rng.standard_normal(L) + 1j * rng.standard_normal(L)
+    assert rel(oracle_mod.fft(x), np.fft.fft(x)) < 1e-13
+    assert rel(oracle_mod.fft(x, inverse=True), np.fft.ifft(x) * L) < 1e-13
+
+
+@pytest.mark.parametrize("N,M", [(1, 1), (7, 3), (64, 64), (200, 37), (513, 256)])
+def test_czt_bluestein_matches_eq9_direct_sum(oracle_mod, N, M):
+    rng = np.random.default_rng(N * 1000 + M)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    alpha, omega = rng.uniform(-0.5, 0.5), rng.uniform(-0.01, 0.01)
+    ref = np.array([np.sum(x * np.exp(-2j * np.pi * (alpha * np.arange(N) + omega * m * np.arange(N))))
+                    for m in range(M)])
+    assert rel(oracle_mod.czt(x, M, alpha, omega), ref) < 1e-12
+    assert rel(oracle_mod.czt(x, M, alpha, omega, direct=True), ref) < 1e-12
+
+
+@pytest.mark.parametrize("N", [16, 100, 257])
+def test_czt_dft_special_case(oracle_mod, N):
+    """A = 1, W = exp(-2 pi i / N), M = N recovers the DFT (Sec. 2.6)."""
+    rng = np.random.default_rng(N)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    assert rel(oracle_mod.czt(x, N, 0.0, 1.0 / N), np.fft.fft(x)) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Three evaluations of the field agree (brute force pins the CZT method)
+# --------------------------------------------------------------------------
+
+def _tiny(oracle_mod, **kw):
+    base = dict(D=4e-3 / 8, f=20e-3 / 8, lam=632.8e-9, M=16, p=0.4e-6)
+    base.update(kw)
+    return oracle_mod.Geometry(**base)
+
+
+@pytest.mark.parametrize("case", ["fzp", "fzp_oddM", "fzp_exact", "lens", "deform", "offaxis_pitch"])
+def test_o1_o2_o3_agree(oracle_mod, case):
+    O = oracle_mod
+    if case == "fzp":
+        g = _tiny(O)
+    elif case == "fzp_oddM":
+        g = _tiny(O, M=15, p=0.31e-6)
+    elif case == "fzp_exact":
+        g = _tiny(O, kind=O.FZP_EXACT)
+    elif case == "lens":
+        g = _tiny(O, kind=O.LENS, M=12)
+    elif case == "deform":
+        d = O.Deform(amp=632.8e-9 / 4, period=1.3e-4, theta=0.7, taper=0.4,
+                     ridges=[(1e-5, -2e-5, 0.3, 632.8e-9 / 8, 3e-5), (-4e-5, 0.0, 2.0, -632.8e-9 / 10, 5e-5)])
+        g = _tiny(O, deform=d)
+    else:
+        g = _tiny(O, M=10, p=1.1e-6)
+    u1 = O.field_direct(g)
+    assert rel(O.field_separable(g), u1) < 1e-12
+    assert rel(O.field_czt(g), u1) < 1e-12
+    # a sub-range of rows (stripe) as well
+    j0, j1 = 37, 211
+    u1s = O.field_direct(g, j0, j1)
+    assert rel(O.field_czt(g, j0, j1), u1s) < 1e-12
+    assert rel(O.field_separable(g, j0, j1), u1s) < 1e-12
+
+
+def test_row_linearity(oracle_mod):
+    """U is linear in aperture rows (Sec. 2.6: rows transformed in independent batches)."""
+    O = oracle_mod
+    g = _tiny(O, M=20)
+    full = O.field_czt(g)
+    a = 301
+    assert rel(O.field_czt(g, 0, a) + O.field_czt(g, a, g.N), full) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Discrete identities on the full (SFFT-like) window
+# --------------------------------------------------------------------------
+
+def _full_window(O, N=101, kind=None):
+    D, f, lam = 4e-3 / 40, 20e-3 / 40, 632.8e-9
+    dx = D / N * 1.02
+    p = lam * f / (N * dx)  # Eq. 8: dx_out = lambda z / (N dx_in)
+    kw = dict(D=D, f=f, lam=lam, M=N, p=p, dx=dx, N=N)
+    if kind is not None:
+        kw["kind"] = kind
+    return O.Geometry(**kw)
+
+
+def test_parseval_full_window(oracle_mod):
+    """With dx_out = lambda f/(N dx_in) and M = N the CZT is an N-point DFT, so
+    sum |U|^2 dx_out^2 = sum |U0|^2 dx_in^2 exactly (energy conservation)."""
+    O = oracle_mod
+    g = _full_window(O)
+    U = O.field_czt(g)
+    U0 = O.aperture_rows(g, 0, g.N)
+    lhs = np.sum(np.abs(U) ** 2) * g.p ** 2
+    rhs = np.sum(np.abs(U0) ** 2) * g.dx ** 2
+    assert abs(lhs / rhs - 1) < 1e-12
+
+
+def test_wiener_khinchin_full_window(oracle_mod):
+    """On the full window |fft2(I)| equals the modulus of the circular
+    autocorrelation of the chirped aperture field (Sec. 2.3 MTF machinery)."""
+    O = oracle_mod
+    g = _full_window(O, N=61)
+    U = O.field_czt(g)
+    I = np.abs(U) ** 2
+    U0 = O.aperture_rows(g, 0, g.N)
+    u = (np.arange(g.N) - g.c) * g.dx
+    a = U0 * np.exp(1j * np.pi * (u[None, :] ** 2 + u[:, None] ** 2) / (g.lam * g.f))
+    Fa = np.fft.fft2(a)
+    ac = np.fft.ifft2(np.abs(Fa) ** 2)  # circular autocorrelation of a
+    lhs = np.abs(np.fft.fft2(I))
+    rhs = np.abs(ac) * np.abs(lhs[0, 0]) / np.abs(ac[0, 0])
+    assert rel(lhs, rhs) < 1e-10
+
+
+# --------------------------------------------------------------------------
+# Closed forms of Sec. 2.3 (ideal lens -> Airy; binary FZP -> 1/pi^2)
+# --------------------------------------------------------------------------
+
+def test_closed_forms_match_printed_values(oracle_mod):
+    O = oracle_mod
+    gold = json.load(open(os.path.join(GOLDEN, "airy_constants.json")))
+    fw = O.airy_fwhm_factor()
+    assert abs(fw - 1.028994) < 2e-6
+    assert round(fw, 3) == gold["fwhm_factor_printed"][1]
+    assert math.floor(fw * 1000) / 1000 == gold["fwhm_factor_printed"][0]
+    assert round(100 * O.binary_fzp_efficiency(), 1) == gold["de_binary_printed_percent"]
+    assert round(O.AIRY_NULL, 2) == gold["null_factor_printed"]
+    assert abs(O.airy_encircled(O.AIRY_NULL) - 0.837785) < 2e-6
+    assert abs(O.circ_mtf(0.5) - 0.391002) < 1e-6
+
+
+def test_ideal_lens_gives_airy(oracle_mod):
+    """A perfect thin lens (circ pupil, phase -pi r^2/(lambda f)) focuses to the
+    Airy pattern: FWHM 1.028994 lambda f / D, EE(r_null) = 0.837785 and the
+    circular-pupil MTF at nu_cut/2 (0.391002).  The ROI truncates the PSF tails,
+    which raises the normalised MTF by the energy fraction that leaves the ROI;
+    the pin multiplies that fraction back (bound measured: < 1e-3)."""
+    O = oracle_mod
+    D, f, lam = 4e-3, 20e-3, 632.8e-9
+    N = 2001
+    g = O.Geometry(D=D, f=f, lam=lam, M=512, p=lam * (f / D) / 8, dx=D / (N - 1) * 1.0000001, N=N, kind=O.LENS)
+    m = O.metrics(g, O.field_czt(g))
+    lfD = lam * f / (2 * g.R)
+    assert abs(m["fwhm_x"] / (O.airy_fwhm_factor() * lfD) - 1) < 1e-4
+    assert abs(m["fwhm_y"] / (O.airy_fwhm_factor() * lfD) - 1) < 1e-4
+    assert abs(m["de_lobe"] / O.airy_encircled(O.AIRY_NULL) - 1) < 1e-4  # lens: all incident power in one order
+    assert abs(m["mtf_half_cut"] * m["de_roi"] / O.circ_mtf(0.5) - 1) < 1e-3
+    # MTF curve over the band, same correction
+    nu = (np.arange(16) + 0.5) / 16
+    ref = np.array([O.circ_mtf(v) for v in nu])
+    assert np.max(np.abs(m["mtf16"] * m["de_roi"] - ref)) < 2.5e-3
+
+
+@pytest.fixture(scope="module")
+def config1(oracle_mod):
+    O = oracle_mod
+    g = O.Geometry(D=4e-3, f=20e-3, lam=632.8e-9, M=256, p=0.2e-6)
+    U = O.field_czt(g)
+    return g, U, O.metrics(g, U)
+
+
+def test_config1_grid(config1, oracle_mod):
+    g, _, _ = config1
+    assert g.N == 5057 and g.c == 2528
+    assert g.total_zones() == 315
+
+
+def test_binary_fzp_efficiency_and_fwhm(config1, oracle_mod):
+    """Binary amplitude FZP: first order carries 1/pi^2 of the incident power
+    (Sec. 2.3), so the main lobe holds EE(r_null)/pi^2 = 0.084885; the other
+    orders perturb it by O(1/zones) (315 zones here).  The focal spot is the
+    Airy spot of the full aperture."""
+    O = oracle_mod
+    g, U, m = config1
+    target = O.airy_encircled(O.AIRY_NULL) * O.binary_fzp_efficiency()
+    assert abs(m["de_lobe"] / target - 1) < 1e-2
+    airy = O.airy_fwhm_factor() * g.lam * g.f / (2 * g.R)
+    assert abs(m["fwhm_x"] / airy - 1) < 5e-3
+    assert abs(m["fwhm_x"] / m["fwhm_y"] - 1) < 1e-12
+    assert abs(m["p_in"] / m["p_in_disc"] - 1) < 1e-3  # pixel count vs pi R^2 (reading 5)
+
+
+def test_focal_plane_symmetry(config1):
+    """Flat FZP on a centred grid: I is invariant under transpose and under the
+    mirror n -> M - n about the on-axis sample M/2."""
+    g, U, _ = config1
+    I = np.abs(U) ** 2
+    assert rel(I, I.T) < 1e-12
+    M = g.M
+    assert rel(I[1:, :], I[1:, :][::-1, :]) < 1e-12
+    assert np.unravel_index(np.argmax(I), I.shape) == (M // 2, M // 2)
+
+
+# --------------------------------------------------------------------------
+# Mask and grid rule
+# --------------------------------------------------------------------------
+
+def test_mask_structure(oracle_mod):
+    O = oracle_mod
+    g = O.Geometry(D=4e-3 / 4, f=20e-3 / 4, lam=632.8e-9, M=8, p=1e-6)
+    mask = O.mask_rows(g, 0, g.N).astype(np.int64)
+    c = g.c
+    assert mask[c, c] == 0  # negative-centred: zone 0 opaque (Sec. 4.1)
+    assert np.array_equal(mask, mask.T) and np.array_equal(mask, mask[::-1, :])
+    inside = O.count_aperture(g)
+    # zones have equal area (r_m^2 = m lambda f), half of them open
+    assert abs(mask.sum() / inside - 0.5) < 2.0 / g.total_zones()
+    # zone boundaries along the centre row sit at r_m = sqrt(m lambda f) (Eq. 4)
+    row = mask[c, c:]
+    flips = np.nonzero(np.diff(row))[0] + 1  # first index of each new run
+    r_flip = flips * g.dx
+    r_m = np.sqrt(np.arange(1, len(flips) + 1) * g.lam * g.f)
+    assert np.all(np.abs(r_flip - r_m) <= g.dx)
+
+
+def test_total_zones_eq3(oracle_mod):
+    """Total_Zones = floor(n_exact) of Eq. 3, checked by counting exact radii
+    r_n = sqrt(n lambda f + n^2 lambda^2 / 4) that fit inside R."""
+    O = oracle_mod
+    for D, f in [(4e-3, 20e-3), (0.08, 1.5), (0.25, 1.25)]:
+        g = O.Geometry(D=D, f=f, lam=632.8e-9, M=8, p=1e-6)
+        n = 0
+        while (n + 1) * g.lam * g.f + ((n + 1) * g.lam) ** 2 / 4 <= g.R ** 2:
+            n += 1
+        assert g.total_zones() == n
+
+
+def test_v8_grid_tables(oracle_mod):
+    """Nx of Tables 1-5 from the Fig. 18 grid rule (ceil, forced odd)."""
+    O = oracle_mod
+    gold = json.load(open(os.path.join(GOLDEN, "v8_grid_tables.json")))
+    lam = gold["lambda"]
+    for row in gold["rows"]:
+        R = row["D"] / 2
+        edge = lam * row["f"] / R
+        dx = edge / row["k"]
+        assert abs(dx * 1e6 - row["dx_um_printed"]) < 5e-4 + 1e-9
+        g = O.Geometry(D=row["D"], f=row["f"], lam=lam, M=8, p=1e-6, dx=dx)
+        assert g.N == row["Nx"], row
+
+
+# --------------------------------------------------------------------------
+# Extractor pieces on synthetic inputs with known answers
+# --------------------------------------------------------------------------
+
+def test_fwhm_extractor_gaussian(oracle_mod):
+    M, p, sigma = 256, 0.1e-6, 0.9e-6
+    x = (np.arange(M) - M // 2) * p
+    row = np.exp(-x ** 2 / (2 * sigma ** 2))
+    fw = oracle_mod.fwhm_row(row, p)
+    assert abs(fw / (2 * math.sqrt(2 * math.log(2)) * sigma) - 1) < 2e-4
+
+
+def test_mtf_extractor_gaussian(oracle_mod):
+    """A Gaussian PSF has a Gaussian OTF, exp(-2 pi^2 sigma^2 nu^2); each radial
+    bin must hold the mean of that closed form over the FFT samples whose
+    radial frequency falls in the bin (bins of nu_Nyq / 200)."""
+    M, p, sigma = 256, 0.1e-6, 0.5e-6
+    x = (np.arange(M) - M // 2) * p
+    I = np.exp(-(x[None, :] ** 2 + x[:, None] ** 2) / (2 * sigma ** 2))
+    c, mean = oracle_mod.mtf_radial(I, p)
+    fu = np.fft.fftfreq(M, d=p)
+    nu = np.hypot(fu[None, :], fu[:, None])
+    b = np.floor(nu * 2 * p * 200).astype(int)
+    ok = b < 200
+    ref = np.bincount(b[ok], weights=np.exp(-2 * np.pi ** 2 * sigma ** 2 * nu[ok] ** 2), minlength=200)
+    cnt = np.bincount(b[ok], minlength=200)
+    has = cnt > 0
+    assert np.array_equal(np.isfinite(mean), has)
+    assert np.max(np.abs(mean[has] - ref[has] / cnt[has])) < 1e-10
+    # the first sample off DC lands in bin floor(200 * 2 p / (M p)) = 1
+    assert np.isfinite(mean[0]) and mean[0] == 1.0
