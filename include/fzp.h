@@ -1,0 +1,189 @@
+/*
+ * fzp.h -- C ABI of libfzp.so, a GB300 (sm_103a) library that evaluates the
+ * Fresnel diffraction integral of a full-aperture Fresnel zone plate (FZP) on a
+ * fixed focal-plane region of interest (ROI) by stripe-processed chirp-z
+ * transforms.
+ *
+ * The operation (Eq. 1-2, Sec. 2.1; Fig. 2 and Fig. 18):
+ *
+ *   U(x_m, y_n) = e^{ikf} e^{i pi (x_m^2 + y_n^2)/(lambda f)} dx^2 / (i lambda f)
+ *                 * sum_{j,i} T[j,i] e^{i phi[j,i]} e^{i pi (u_i^2 + v_j^2)/(lambda f)}
+ *                   * e^{-2 pi i (x_m u_i + y_n v_j)/(lambda f)},           I = |U|^2
+ *
+ * with the aperture grid u_i = (i - c) dx, c = (N-1)/2 (N odd, Fig. 2 Stage 1),
+ * the ROI grid x_m = (m - M/2) p (sample M/2 on the axis), T the binary FZP
+ * mask (open where floor(r^2/(lambda f)) is odd and r <= R_eff, Fig. 2 Stage 2,
+ * paraxial radii of Eq. 4, centre zone opaque) and phi an optional membrane
+ * deformation phase (4 pi / lambda) w(u, v).  The mask is generated inside the
+ * kernels stripe by stripe and never stored.
+ *
+ * Conventions shared by every call:
+ *   - Units are SI (metres).  Complex data are interleaved (re, im) pairs of
+ *     IEEE doubles ("complex128"); 2-D arrays are row-major with the y index n
+ *     slowest: element (n, m) at offset n*M + m.
+ *   - "device" pointers are CUDA global-memory addresses on the current device;
+ *     the caller allocates and owns them.  `stream` is a cudaStream_t passed as
+ *     void* (NULL = legacy default stream).  Calls that take a stream enqueue
+ *     work and return without synchronising unless stated otherwise.
+ *   - Every call returns an fzp_status; nothing throws or aborts across the
+ *     ABI.  fzp_last_error() gives a human-readable message for the calling
+ *     thread's last failure.
+ *   - Invalid arguments are rejected with FZP_E_INVALID before any device
+ *     memory is allocated or any work is enqueued.
+ */
+#ifndef FZP_H_
+#define FZP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define FZP_API __attribute__((visibility("default")))
+#else
+#define FZP_API
+#endif
+
+typedef enum {
+  FZP_OK = 0,
+  FZP_E_INVALID = 1,     /* bad argument; nothing was allocated or enqueued          */
+  FZP_E_OOM = 2,         /* device or host allocation failed; nothing leaked          */
+  FZP_E_CUDA = 3,        /* a CUDA runtime call failed (message names it)             */
+  FZP_E_TIMEOUT = 4,     /* a bounded device-side wait ran out; results are invalid   */
+  FZP_E_UNSUPPORTED = 5  /* valid request the library does not implement              */
+} fzp_status;
+
+/* Kernel form of the row transform. */
+typedef enum {
+  FZP_FORM_AUTO = 0,      /* dense for split-BF16/BF16 precision, Bluestein otherwise  */
+  FZP_FORM_BLUESTEIN = 1, /* (a) separable Bluestein CZT with hand-written FFTs (Sec. 2.6) */
+  FZP_FORM_DENSE = 2      /* (b) tensor-core contraction U = K diag T K^T (separability of Eq. 2) */
+} fzp_form;
+
+/* Arithmetic of the row transform.  Phase arguments are always reduced in
+ * FP64 and the cross-stripe ROI sum is always FP64. */
+typedef enum {
+  FZP_PREC_FP64 = 0,       /* Bluestein in FP64 throughout                          */
+  FZP_PREC_FP32 = 1,       /* Bluestein in FP32 (complex64)                          */
+  FZP_PREC_SPLIT_BF16 = 2, /* dense: K = K_hi + K_lo in BF16, T exact, FP32 accumulate */
+  FZP_PREC_BF16 = 3        /* dense: K_hi only (reduced accuracy, for error studies)   */
+} fzp_precision;
+
+/* Membrane deformation w(u,v) [m]; phase phi = (4 pi / lambda) w:
+ *   w = amp sin(2 pi (u cos theta + v sin theta) / period) (1 - taper (r/R)^2)
+ *     + sum_{k < n_ridges} h_k exp(-d_k^2 / (2 sigma_k^2)),
+ *   d_k = distance of (u,v) to the line through (px_k, py_k) at angle alpha_k,
+ *   sigma_k = width_k / (2 sqrt(2 ln 2)).   n_ridges <= 3.                    */
+typedef struct fzp_deform {
+  double amp, period, theta, taper;
+  int32_t n_ridges;
+  int32_t reserved;
+  double ridge_px[3], ridge_py[3], ridge_alpha[3], ridge_h[3], ridge_width[3];
+} fzp_deform;
+
+/* Problem statement (Fig. 2 ENTRY: N_in, N_out, D, f, lambda0). */
+typedef struct fzp_params {
+  double D;            /* aperture diameter [m], > 0                                   */
+  double f;            /* focal length = propagation distance [m], > 0                 */
+  double lambda;       /* wavelength [m], > 0                                          */
+  double dx;           /* aperture pitch [m]; 0 -> lambda f / (4 D): four samples per
+                          outermost zone width (Eq. 5); must satisfy Eq. 6,
+                          dx <= lambda f / (2 D)                                       */
+  int64_t N;           /* samples per aperture side; 0 -> ceil(D / dx) forced odd;
+                          a given N must be odd                                        */
+  int32_t M;           /* ROI samples per side: a power of two in [64, 1024]          */
+  int32_t form;        /* fzp_form                                                     */
+  double pitch;        /* ROI pitch p [m], > 0                                         */
+  int32_t precision;   /* fzp_precision                                                */
+  int32_t stripe_rows; /* aperture rows per stripe; 0 -> library default              */
+  const fzp_deform* deform; /* NULL: flat membrane.  Copied by fzp_plan.               */
+} fzp_params;
+
+/* Opaque plan: geometry, zone-threshold table, chirp / kernel tables and the
+ * workspace of one problem.  Owned by the caller between fzp_plan and
+ * fzp_plan_destroy.  A plan must not be used by two streams at once. */
+typedef struct fzp_plan_s* fzp_plan_t;
+
+/* Read-only description of a plan. */
+typedef struct fzp_plan_info {
+  int64_t N;             /* aperture samples per side                              */
+  int64_t c;             /* index of the on-axis sample, (N-1)/2                   */
+  int64_t total_zones;   /* floor(n_exact) of Eq. 3 (Fig. 2 Stage 2)               */
+  int64_t n_thresholds;  /* entries of the zone-threshold table                    */
+  double dx;             /* aperture pitch [m]                                     */
+  double R;              /* aperture radius R_eff = min(D/2, lambda f/(2 dx)) [m]  */
+  double kappa;          /* dx^2 / (lambda f): zone index = floor(s kappa)         */
+  double x0;             /* first ROI coordinate [m]                               */
+  int32_t M;             /* ROI samples per side                                   */
+  int32_t form;          /* resolved fzp_form                                      */
+  int32_t precision;     /* fzp_precision                                          */
+  int32_t stripe_rows;   /* resolved stripe height                                 */
+  int64_t fft_length;    /* Bluestein length L = 2^ceil(log2(N + M - 1)) (Sec. 2.6) */
+  size_t device_bytes;   /* device memory owned by the plan                        */
+} fzp_plan_info;
+
+/* Metrics of Fig. 2 Stage 4 / Fig. 18 Stage 5. */
+typedef struct fzp_metrics_t {
+  double fwhm_x, fwhm_y; /* FWHM of the centre row / column [m]: parabolic peak,
+                            half-maximum crossings of the not-a-knot cubic spline */
+  double de_lobe;        /* sum_{r <= r_null} I p^2 / P_in, r_null = 1.21967 lambda f / (2R) */
+  double de_roi;         /* sum_ROI I p^2 / P_in                                  */
+  double p_in;           /* incident power: (# samples with r <= R_eff) dx^2       */
+  double p_in_disc;      /* pi R^2 (the v8 normalisation, Fig. 18)                 */
+  double peak;           /* I at the on-axis sample (M/2, M/2)                     */
+  double strehl;         /* peak / (pi R^2 / (lambda f))^2 (Fig. 18 Stage 5)       */
+  double mtf_half_cut;   /* radial MTF at nu_cut/2, nu_cut = 2R/(lambda f)         */
+  double mtf16[16];      /* radial MTF at (q + 1/2) nu_cut / 16, q = 0..15         */
+  int64_t aperture_count;/* samples with r <= R_eff                                */
+} fzp_metrics_t;
+
+/* Build a plan (Fig. 2 Stage 1-2; Fig. 18 Stage 1-2): validate `params`,
+ * derive the grids, build the zone-threshold table and the form's tables,
+ * and allocate the workspace.  Synchronises the device.  On failure *out is
+ * NULL and nothing is leaked.  Errors: FZP_E_INVALID (bad parameters,
+ * Eq. 6 violated, M out of range), FZP_E_OOM, FZP_E_CUDA, FZP_E_UNSUPPORTED
+ * (e.g. dense form with FP64 precision). */
+FZP_API fzp_status fzp_plan(const fzp_params* params, fzp_plan_t* out);
+
+/* Copy the plan description into *out (host memory). */
+FZP_API fzp_status fzp_plan_info_get(fzp_plan_t plan, fzp_plan_info* out);
+
+/* Release everything the plan owns.  NULL is accepted.  Synchronises the device. */
+FZP_API fzp_status fzp_plan_destroy(fzp_plan_t plan);
+
+/* Contribution of aperture rows [row_begin, row_end) to the ROI field
+ * (Fig. 2 Stage 3 / Fig. 18 Stage 3-4: row pass per stripe, column pass, output
+ * chirp and Fresnel prefactor).  The field is linear in the rows, so calls over
+ * disjoint row ranges with accumulate = 1 sum to the full-aperture field
+ * (resumable and shardable, Sec. 7.2).
+ *   d_field    device, complex128, M*M, caller-owned; written (accumulate = 0)
+ *              or added to (accumulate != 0).
+ *   stream     cudaStream_t; work is enqueued, no host synchronisation.
+ * Errors: FZP_E_INVALID (range outside [0, N], NULL field), FZP_E_CUDA. */
+FZP_API fzp_status fzp_propagate_roi(fzp_plan_t plan, int64_t row_begin, int64_t row_end, void* d_field,
+                             int accumulate, void* stream);
+
+/* I = |U|^2 (Fig. 2: I(x', y') = |U_out|^2).
+ *   d_field device complex128 M*M (input), d_intensity device double M*M (output). */
+FZP_API fzp_status fzp_intensity(fzp_plan_t plan, const void* d_field, void* d_intensity, void* stream);
+
+/* Metric extractor on a full ROI field (Fig. 2 Stage 4; Fig. 18 Stage 5).
+ * Runs on the device, then synchronises `stream` and writes *out (host).
+ * Also reports any device-side timeout recorded by earlier calls on this plan
+ * (FZP_E_TIMEOUT). */
+FZP_API fzp_status fzp_metrics(fzp_plan_t plan, const void* d_field, void* stream, fzp_metrics_t* out);
+
+/* Message of the calling thread's last failed call ("" if none). */
+FZP_API const char* fzp_last_error(void);
+
+/* Library version string. */
+FZP_API const char* fzp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FZP_H_ */

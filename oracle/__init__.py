@@ -306,17 +306,25 @@ def fwhm_row(row: np.ndarray, p: float) -> float:
 def mtf_radial(I: np.ndarray, p: float, bins: int = MTF_BINS):
     """OTF = |fft2(I)| normalised at DC, radially averaged in `bins` equal bins
     over [0, nu_Nyq], nu_Nyq = 1/(2p) (Fig. 2 Stage 4, Fig. 18 Stage 5).
-    Returns (bin centres [cycles/m], bin means)."""
+
+    Reading: FFT sample (ku, kv) (integer frequency indices, numpy fftfreq
+    order) has radial frequency |k| / (M p) and falls in bin
+    floor(bins |k| / (M/2)), evaluated exactly in integers so that samples on a
+    bin edge have a well-defined bin.  Returns (bin centres [cycles/m], means).
+    """
     M = I.shape[0]
     otf = np.abs(np.fft.fft2(I))
     otf = otf / otf[0, 0]
-    fu = np.fft.fftfreq(M, d=p)
-    nu = np.hypot(fu[None, :], fu[:, None])
-    nyq = 1.0 / (2.0 * p)
-    b = np.floor(nu / nyq * bins).astype(np.int64)
+    k = np.rint(np.fft.fftfreq(M) * M).astype(np.int64)
+    r2 = k[None, :] ** 2 + k[:, None] ** 2
+    q = (4 * bins * bins * r2) // (M * M)
+    b = np.floor(np.sqrt(q.astype(np.float64))).astype(np.int64)
+    b -= (b * b > q).astype(np.int64)
+    b += ((b + 1) * (b + 1) <= q).astype(np.int64)
     ok = b < bins
     s = np.bincount(b[ok], weights=otf[ok], minlength=bins)
     n = np.bincount(b[ok], minlength=bins)
+    nyq = 1.0 / (2.0 * p)
     centres = (np.arange(bins) + 0.5) * nyq / bins
     with np.errstate(invalid="ignore"):
         mean = s / n

@@ -1,0 +1,184 @@
+"""Python binding of libfzp.so (argument marshalling only).
+
+libfzp evaluates the Fresnel diffraction integral (Eq. 1-2) of a full-aperture
+Fresnel zone plate onto a focal-plane region of interest by stripe-processed
+chirp-z transforms (Sec. 2.6, Fig. 2, Fig. 18) on a GB300 GPU.  Every step of
+the computation runs in the library's CUDA kernels; this module only converts
+Python arguments into the C structures of ``include/fzp.h`` and passes device
+pointers (``torch`` tensors, used for device memory and streams) through.
+
+There is no CPU fallback: if the compiled library is missing, importing the
+binding raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfzp.so")
+
+FZP_OK, FZP_E_INVALID, FZP_E_OOM, FZP_E_CUDA, FZP_E_TIMEOUT, FZP_E_UNSUPPORTED = range(6)
+FORM_AUTO, FORM_BLUESTEIN, FORM_DENSE = 0, 1, 2
+PREC_FP64, PREC_FP32, PREC_SPLIT_BF16, PREC_BF16 = 0, 1, 2, 3
+
+_STATUS = {0: "FZP_OK", 1: "FZP_E_INVALID", 2: "FZP_E_OOM", 3: "FZP_E_CUDA", 4: "FZP_E_TIMEOUT",
+           5: "FZP_E_UNSUPPORTED"}
+
+
+class FzpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Deform(ctypes.Structure):
+    _fields_ = [("amp", ctypes.c_double), ("period", ctypes.c_double), ("theta", ctypes.c_double),
+                ("taper", ctypes.c_double), ("n_ridges", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ridge_px", ctypes.c_double * 3), ("ridge_py", ctypes.c_double * 3),
+                ("ridge_alpha", ctypes.c_double * 3), ("ridge_h", ctypes.c_double * 3),
+                ("ridge_width", ctypes.c_double * 3)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_double), ("f", ctypes.c_double), ("lam", ctypes.c_double),
+                ("dx", ctypes.c_double), ("N", ctypes.c_int64), ("M", ctypes.c_int32),
+                ("form", ctypes.c_int32), ("pitch", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("stripe_rows", ctypes.c_int32), ("deform", ctypes.POINTER(Deform))]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("c", ctypes.c_int64), ("total_zones", ctypes.c_int64),
+                ("n_thresholds", ctypes.c_int64), ("dx", ctypes.c_double), ("R", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("x0", ctypes.c_double), ("M", ctypes.c_int32),
+                ("form", ctypes.c_int32), ("precision", ctypes.c_int32), ("stripe_rows", ctypes.c_int32),
+                ("fft_length", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
+
+
+class Metrics(ctypes.Structure):
+    _fields_ = [("fwhm_x", ctypes.c_double), ("fwhm_y", ctypes.c_double), ("de_lobe", ctypes.c_double),
+                ("de_roi", ctypes.c_double), ("p_in", ctypes.c_double), ("p_in_disc", ctypes.c_double),
+                ("peak", ctypes.c_double), ("strehl", ctypes.c_double), ("mtf_half_cut", ctypes.c_double),
+                ("mtf16", ctypes.c_double * 16), ("aperture_count", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "mtf16"}
+        d["mtf16"] = list(self.mtf16)
+        return d
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfzp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_2609_01978_gb300/build.py (or "
+                              "__graft_entry__.build()) first; there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        sig = {
+            "fzp_plan": [ctypes.POINTER(Params), ctypes.POINTER(vp)],
+            "fzp_plan_info_get": [vp, ctypes.POINTER(PlanInfo)],
+            "fzp_plan_destroy": [vp],
+            "fzp_propagate_roi": [vp, i64, i64, vp, i32, vp],
+            "fzp_intensity": [vp, vp, vp, vp],
+            "fzp_metrics": [vp, vp, vp, ctypes.POINTER(Metrics)],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.fzp_last_error.restype = ctypes.c_char_p
+        L.fzp_last_error.argtypes = []
+        L.fzp_version.restype = ctypes.c_char_p
+        L.fzp_version.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != FZP_OK:
+        raise FzpError(st, lib().fzp_last_error().decode())
+
+
+def _ptr(x) -> Optional[int]:
+    """Device pointer of a torch tensor, or an int address, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s) -> Optional[int]:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def make_deform(amp=0.0, period=1e-2, theta=0.0, taper=0.0, ridges=()) -> Deform:
+    d = Deform()
+    d.amp, d.period, d.theta, d.taper = amp, period, theta, taper
+    d.n_ridges = len(ridges)
+    for k, (px, py, al, h, w) in enumerate(ridges):
+        d.ridge_px[k], d.ridge_py[k], d.ridge_alpha[k], d.ridge_h[k], d.ridge_width[k] = px, py, al, h, w
+    return d
+
+
+class Plan:
+    """fzp_plan / fzp_propagate_roi / fzp_metrics / fzp_plan_destroy."""
+
+    def __init__(self, D: float, f: float, lam: float, M: int, pitch: float, dx: float = 0.0, N: int = 0,
+                 form: int = FORM_AUTO, precision: int = PREC_FP32, stripe_rows: int = 0,
+                 deform: Optional[Deform] = None):
+        self._deform = deform
+        p = Params(D=D, f=f, lam=lam, dx=dx, N=N, M=M, form=form, pitch=pitch, precision=precision,
+                   stripe_rows=stripe_rows, deform=ctypes.pointer(deform) if deform is not None else None)
+        h = ctypes.c_void_p()
+        _check(lib().fzp_plan(ctypes.byref(p), ctypes.byref(h)))
+        self._h = h
+        self.M = M
+
+    @property
+    def info(self) -> dict:
+        inf = PlanInfo()
+        _check(lib().fzp_plan_info_get(self._h, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in inf._fields_}
+
+    def propagate_roi(self, row_begin: int, row_end: int, field, accumulate: bool = False, stream=None):
+        _check(lib().fzp_propagate_roi(self._h, row_begin, row_end, _ptr(field), int(accumulate), _stream(stream)))
+
+    def intensity(self, field, out, stream=None):
+        _check(lib().fzp_intensity(self._h, _ptr(field), _ptr(out), _stream(stream)))
+
+    def metrics(self, field, stream=None) -> dict:
+        m = Metrics()
+        _check(lib().fzp_metrics(self._h, _ptr(field), _stream(stream), ctypes.byref(m)))
+        return m.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fzp_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def version() -> str:
+    return lib().fzp_version().decode()

@@ -1,0 +1,392 @@
+// bluestein.cu -- form (a): row chirp-z transform by Bluestein's identity
+// (Sec. 2.6; Eq. 9-10; Fig. 2 Stage 3; Fig. 18 Stage 3 "row Bluestein at fixed
+// length nfft"), with FFTs written here.
+//
+// For aperture row j the row transform is
+//   C[j, m] = sum_i x_i K[m, i],  x_i = T[j, i] e^{i phi[j, i]},
+//   K[m, i] = exp(2 pi i theta(m, i)),  theta = di^2 kappa/2 - (m - M/2) di delta.
+// With m i = (m^2 + i^2 - (m - i)^2) / 2 (Bluestein):
+//   theta(m, i) = pre(i) + post(m) + delta (m - i)^2 / 2,
+//   pre(i)  = di^2 kappa/2 - delta i^2/2 + delta (M/2) i,
+//   post(m) = -delta m^2/2 + delta m c - delta (M/2) c,
+// so C[j, .] = e^{2 pi i post} .* (y * h)[0..M) with y_i = x_i e^{2 pi i pre(i)} and
+// the chirp h_k = e^{i pi delta k^2}, k in (-N, M): one linear convolution of
+// length >= N + M - 1, done as FFT_L, pointwise product with FFT_L(h), IFFT_L.
+//
+// Large L is split four-step (Bailey, ref. [24] of the paper), L = L1 * L2,
+// n = L2 n1 + n2, k = k1 + L1 k2:
+//   pass F1 (L1 > 1): for each column n2 an L1-point FFT over n1, times e^{-2 pi i n2 k1 / L}
+//   pass F2         : for each row k1 an L2-point FFT over n2 -> Y[k1 + L1 k2],
+//                     times H, L2-point inverse FFT; only m < M outputs kept,
+//                     times e^{+2 pi i k1 m / L}
+//   pass F3 (L1 > 1): sum over k1, times e^{2 pi i post(m)} / L -> row intermediate.
+// The mask and the input chirp are generated inside F1 (or F2 when L1 = 1):
+// the aperture is never stored.
+#include <algorithm>
+#include <cmath>
+
+#include "fzp_internal.cuh"
+
+namespace fzp {
+namespace {
+
+template <typename R> struct Traits;
+template <> struct Traits<float> { static constexpr int L2MAX = 8192; };
+template <> struct Traits<double> { static constexpr int L2MAX = 4096; };
+
+__host__ __device__ inline int ilog2(int64_t v) { int r = 0; while ((1ll << r) < v) ++r; return r; }
+
+__device__ __forceinline__ int brev(int v, int bits) { return (int)(__brev((unsigned)v) >> (32 - bits)); }
+
+template <typename C> __device__ __forceinline__ C conjc(C a) { a.y = -a.y; return a; }
+
+// Batched in-place radix-2 DIT: `batch` transforms of length n = 2^logn stored
+// contiguously; input in bit-reversed order, output natural; forward sign.
+// tw[t] = e^{-2 pi i t / twN}.
+template <typename C>
+__device__ void dit(C* x, int logn, int batch, const C* __restrict__ tw, int twN) {
+  const int n = 1 << logn, nb = (n >> 1) * batch;
+  for (int s = 1; s <= logn; ++s) {
+    const int half = 1 << (s - 1);
+    const int stride = twN >> s;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+      const int col = t >> (logn - 1), b = t & ((n >> 1) - 1);
+      const int k = b & (half - 1);
+      const int i0 = col * n + ((b >> (s - 1)) << s) + k, i1 = i0 + half;
+      const C w = tw[k * stride];
+      const C a = x[i0], v = cmul(x[i1], w);
+      x[i0] = cadd(a, v);
+      x[i1] = csub(a, v);
+    }
+    __syncthreads();
+  }
+}
+
+// In-place radix-2 DIF, natural input, bit-reversed output, inverse sign (no 1/n).
+template <typename C>
+__device__ void dif_inverse(C* x, int logn, const C* __restrict__ tw, int twN) {
+  const int n = 1 << logn, nb = n >> 1;
+  for (int s = logn; s >= 1; --s) {
+    const int half = 1 << (s - 1);
+    const int stride = twN >> s;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      const int k = b & (half - 1);
+      const int i0 = ((b >> (s - 1)) << s) + k, i1 = i0 + half;
+      const C w = conjc(tw[k * stride]);
+      const C a = x[i0], v = x[i1];
+      x[i0] = cadd(a, v);
+      x[i1] = cmul(csub(a, v), w);
+    }
+    __syncthreads();
+  }
+}
+
+struct RowArgs {
+  MaskGeom mg;
+  int64_t N, L, L1, L2;
+  int logL1, logL2, M;
+  int64_t j0;        // first aperture row of this launch
+  int64_t rows;      // rows in this launch
+  int B;             // columns per F1 block
+  int has_deform;
+  fzp_deform def;
+  double dx, R, inv_lambda;
+  const void* pre;   // N
+  const void* H;     // [L1][L2]
+  void* Z;           // [rows][L1][L2]
+  void* G;           // [rows][L1][M]
+  const void* post;  // M, includes 1/L
+  const void* tw;    // twN/2 entries
+  int twN;
+  void* C1;          // [2M][c1_stride]
+  int64_t c1_stride; // row length of C1
+  int64_t c1_j0;     // aperture row of C1 column 0
+  const void* vin;   // input sequence for the table-building mode (length L)
+};
+
+// Aperture transmission of sample (j, i): T e^{i phi}, optional deformation.
+template <typename R>
+__device__ __forceinline__ typename Cplx<R>::T aperture(const RowArgs& a, int64_t j, int64_t i) {
+  typename Cplx<R>::T v;
+  v.x = 0; v.y = 0;
+  if (i >= a.N) return v;
+  if (!mask_open(j - a.mg.c, i - a.mg.c, a.mg)) return v;
+  if (!a.has_deform) { v.x = 1; return v; }
+  const double u = (double)(i - a.mg.c) * a.dx, w = (double)(j - a.mg.c) * a.dx;
+  const fzp_deform& d = a.def;
+  const double tt = (u * cos(d.theta) + w * sin(d.theta)) / d.period;  // turns
+  const double r2 = (u * u + w * w) / (a.R * a.R);
+  double wz = d.amp * sinpi(2.0 * frac_turns(tt)) * (1.0 - d.taper * r2);
+  for (int k = 0; k < d.n_ridges; ++k) {
+    const double dist = (u - d.ridge_px[k]) * (-sin(d.ridge_alpha[k])) + (w - d.ridge_py[k]) * cos(d.ridge_alpha[k]);
+    const double sg = d.ridge_width[k] / (2.0 * sqrt(2.0 * log(2.0)));
+    wz += d.ridge_h[k] * exp(-dist * dist / (2.0 * sg * sg));
+  }
+  return cis_turns<R>(2.0 * wz * a.inv_lambda);  // phi / (2 pi) = 2 w / lambda
+}
+
+// mode 0: generate y = aperture * pre; mode 1: read the table input `vin`.
+template <typename R>
+__global__ void __launch_bounds__(256) k_f1(RowArgs a, int mode) {
+  using C = typename Cplx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const int B = a.B;
+  const int64_t r = blockIdx.y;
+  const int64_t j = a.j0 + r;
+  const int64_t n2_0 = (int64_t)blockIdx.x * B;
+  const int L1 = (int)a.L1;
+  const C* pre = reinterpret_cast<const C*>(a.pre);
+  const C* vin = reinterpret_cast<const C*>(a.vin);
+  // load, bit-reversed within each column
+  for (int t = threadIdx.x; t < L1 * B; t += blockDim.x) {
+    const int n1 = t / B, b = t % B;
+    const int64_t n = (int64_t)n1 * a.L2 + n2_0 + b;
+    C x;
+    if (mode == 0) {
+      x = aperture<R>(a, j, n);
+      if (x.x != 0 || x.y != 0) x = cmul(x, pre[n]);
+    } else {
+      x = vin[n];
+    }
+    sm[b * L1 + brev(n1, a.logL1)] = x;
+  }
+  __syncthreads();
+  dit(sm, a.logL1, B, reinterpret_cast<const C*>(a.tw), a.twN);
+  C* Z = reinterpret_cast<C*>(a.Z) + r * a.L;
+  for (int t = threadIdx.x; t < L1 * B; t += blockDim.x) {
+    const int k1 = t / B, b = t % B;
+    const int64_t n2 = n2_0 + b;
+    const C w = twiddle<R>((n2 * k1) & (a.L - 1), a.L, -1.0f);
+    Z[(int64_t)k1 * a.L2 + n2] = cmul(sm[b * L1 + k1], w);
+  }
+}
+
+// mode 0: full row transform; mode 1: forward FFT only, result -> Z as [k1][k2].
+template <typename R>
+__global__ void __launch_bounds__(512) k_f2(RowArgs a, int mode) {
+  using C = typename Cplx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const int64_t k1 = blockIdx.x;
+  const int64_t r = blockIdx.y;
+  const int64_t j = a.j0 + r;
+  const int L2 = (int)a.L2;
+  const C* tw = reinterpret_cast<const C*>(a.tw);
+  const C* pre = reinterpret_cast<const C*>(a.pre);
+  if (a.L1 == 1) {
+    const C* vin = reinterpret_cast<const C*>(a.vin);
+    for (int n = threadIdx.x; n < L2; n += blockDim.x) {
+      C x;
+      if (mode == 0) {
+        x = aperture<R>(a, j, n);
+        if (x.x != 0 || x.y != 0) x = cmul(x, pre[n]);
+      } else {
+        x = vin[n];
+      }
+      sm[brev(n, a.logL2)] = x;
+    }
+  } else {
+    const C* Z = reinterpret_cast<const C*>(a.Z) + r * a.L + k1 * a.L2;
+    for (int n = threadIdx.x; n < L2; n += blockDim.x) sm[brev(n, a.logL2)] = Z[n];
+  }
+  __syncthreads();
+  dit(sm, a.logL2, 1, tw, a.twN);
+  if (mode == 1) {
+    C* out = reinterpret_cast<C*>(a.Z) + r * a.L + k1 * a.L2;
+    for (int k = threadIdx.x; k < L2; k += blockDim.x) out[k] = sm[k];
+    return;
+  }
+  const C* H = reinterpret_cast<const C*>(a.H) + k1 * a.L2;
+  for (int k = threadIdx.x; k < L2; k += blockDim.x) sm[k] = cmul(sm[k], H[k]);
+  __syncthreads();
+  dif_inverse(sm, a.logL2, tw, a.twN);
+  if (a.L1 == 1) {
+    // finalize directly: C = post(m) * z[m]  (post includes 1/L)
+    const C* post = reinterpret_cast<const C*>(a.post);
+    R* C1 = reinterpret_cast<R*>(a.C1);
+    const int64_t jl = j - a.c1_j0;
+    for (int m = threadIdx.x; m < a.M; m += blockDim.x) {
+      const C v = cmul(sm[brev(m, a.logL2)], post[m]);
+      C1[(int64_t)c1_row_re(m) * a.c1_stride + jl] = v.x;
+      C1[(int64_t)c1_row_im(m) * a.c1_stride + jl] = v.y;
+    }
+    return;
+  }
+  C* G = reinterpret_cast<C*>(a.G) + (r * a.L1 + k1) * a.M;
+  for (int m = threadIdx.x; m < a.M; m += blockDim.x) {
+    const C w = twiddle<R>((k1 * m) & (a.L - 1), a.L, 1.0f);
+    G[m] = cmul(sm[brev(m, a.logL2)], w);
+  }
+}
+
+// Sum over k1; tile of 32 rows x 32 m; writes C1 coalesced along rows.
+template <typename R>
+__global__ void __launch_bounds__(256) k_f3(RowArgs a) {
+  using C = typename Cplx<R>::T;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 warps
+  const int m0 = blockIdx.x * 32;
+  const int64_t r0 = (int64_t)blockIdx.y * 32;
+  __shared__ C tile[32][33];
+  const C* G = reinterpret_cast<const C*>(a.G);
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int64_t r = r0 + rr;
+    C acc;
+    acc.x = 0; acc.y = 0;
+    if (r < a.rows)
+      for (int64_t k1 = 0; k1 < a.L1; ++k1) acc = cadd(acc, G[(r * a.L1 + k1) * a.M + m0 + tx]);
+    tile[rr][tx] = cmul(acc, reinterpret_cast<const C*>(a.post)[m0 + tx]);
+  }
+  __syncthreads();
+  R* C1 = reinterpret_cast<R*>(a.C1);
+  for (int mm = ty; mm < 32; mm += 8) {
+    const int64_t r = r0 + tx;
+    if (r >= a.rows) continue;
+    const int m = m0 + mm;
+    const int64_t jl = a.j0 + r - a.c1_j0;
+    const C v = tile[tx][mm];
+    C1[(int64_t)c1_row_re(m) * a.c1_stride + jl] = v.x;
+    C1[(int64_t)c1_row_im(m) * a.c1_stride + jl] = v.y;
+  }
+}
+
+// Tables: pre(i), post(m)/L, convolution chirp v (length L), twiddles.
+template <typename R>
+__global__ void k_tables(int64_t N, int M, int64_t L, int64_t c, double kappa, double delta, void* pre, void* post,
+                         void* v, void* tw, int twN) {
+  using C = typename Cplx<R>::T;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < L; t += stride) {
+    if (t < N) {
+      const double di = (double)(t - c), ti = (double)t;
+      const double ph = di * di * (0.5 * kappa) - (0.5 * delta) * (ti * ti) + delta * (double)(M / 2) * ti;
+      reinterpret_cast<C*>(pre)[t] = cis_turns<R>(ph);
+    }
+    if (t < M) {
+      const double tm = (double)t;
+      const double ph = -(0.5 * delta) * tm * tm + delta * tm * (double)c - delta * (double)(M / 2) * (double)c;
+      C z = cis_turns<R>(ph);
+      z.x /= (R)L; z.y /= (R)L;
+      reinterpret_cast<C*>(post)[t] = z;
+    }
+    // chirp h_k = e^{i pi delta k^2}: index k for k < M, index L - k for 0 < k < N
+    C h;
+    h.x = 0; h.y = 0;
+    int64_t k = -1;
+    if (t < M) k = t;
+    else if (t > L - N) k = L - t;
+    if (k >= 0) {
+      const double kk = (double)k;
+      h = cis_turns<R>(0.5 * delta * kk * kk);
+    }
+    reinterpret_cast<C*>(v)[t] = h;
+    if (t < twN / 2) reinterpret_cast<C*>(tw)[t] = twiddle<R>(t, twN, -1.0f);
+  }
+}
+
+static RowArgs make_args(const Plan& P) {
+  const Bluestein& b = P.bs;
+  RowArgs a{};
+  a.mg = P.mg;
+  a.N = P.N; a.L = b.L; a.L1 = b.L1; a.L2 = b.L2; a.logL1 = ilog2(b.L1); a.logL2 = ilog2(b.L2); a.M = P.M;
+  // F1 columns per block: a power of two, at most 16, F1 tile <= 64 KiB
+  {
+    const int64_t csz = P.precision == FZP_PREC_FP64 ? 16 : 8;
+    int64_t B = 16;
+    while (B > 1 && B * b.L1 * csz > 65536) B >>= 1;
+    a.B = (int)std::min<int64_t>(B, b.L2);
+  }
+  a.has_deform = P.has_deform ? 1 : 0;
+  a.def = P.deform;
+  a.dx = P.dx; a.R = P.R; a.inv_lambda = 1.0 / P.lambda;
+  a.pre = b.d_pre; a.H = b.d_H; a.Z = b.d_Z; a.G = b.d_G; a.post = b.d_post; a.tw = b.d_tw;
+  a.twN = (int)b.L2;
+  a.c1_stride = P.chunk_rows;
+  a.C1 = P.precision == FZP_PREC_FP64 ? (void*)P.d_C1d : (void*)P.d_C1;
+  a.vin = b.d_tab;
+  return a;
+}
+
+template <typename R>
+fzp_status build_tables_t(Plan& P) {
+  using C = typename Cplx<R>::T;
+  Bluestein& b = P.bs;
+  b.L = 1;
+  while (b.L < P.N + P.M - 1) b.L <<= 1;
+  b.L2 = b.L < Traits<R>::L2MAX ? b.L : Traits<R>::L2MAX;
+  b.L1 = b.L / b.L2;
+  if (P.M > b.L2) return set_error(FZP_E_UNSUPPORTED, "M larger than the inner FFT length");
+  const int twN = (int)b.L2;
+  // row batch: Z workspace of about 1 GiB
+  const int64_t zbytes = (int64_t)sizeof(C) * b.L;
+  b.rows = b.L1 > 1 ? std::max<int64_t>(1, std::min<int64_t>(P.chunk_rows, (1ll << 30) / zbytes)) : P.chunk_rows;
+  if (b.rows > 65535) b.rows = 65535;
+  FZP_CUDA_TRY(cudaMalloc(&b.d_pre, sizeof(C) * P.N));
+  FZP_CUDA_TRY(cudaMalloc(&b.d_H, sizeof(C) * b.L));
+  FZP_CUDA_TRY(cudaMalloc(&b.d_tab, sizeof(C) * (b.L + twN / 2 + P.M)));
+  b.d_tw = reinterpret_cast<C*>(b.d_tab) + b.L;
+  b.d_post = reinterpret_cast<C*>(b.d_tw) + twN / 2;
+  const int64_t zrows = b.L1 > 1 ? b.rows : 1;
+  FZP_CUDA_TRY(cudaMalloc(&b.d_Z, sizeof(C) * b.L * zrows));
+  if (b.L1 > 1) FZP_CUDA_TRY(cudaMalloc(&b.d_G, sizeof(C) * b.L1 * P.M * b.rows));
+  P.device_bytes += sizeof(C) * (P.N + b.L + b.L + twN / 2 + P.M + b.L * zrows) +
+                    (b.L1 > 1 ? sizeof(C) * b.L1 * P.M * b.rows : 0);
+  k_tables<R><<<1024, 256>>>(P.N, P.M, b.L, P.c, P.kappa, P.delta, b.d_pre, b.d_post, b.d_tab, b.d_tw, twN);
+  FZP_CUDA_TRY(cudaGetLastError());
+  // H = FFT_L(v) in the [k1][k2] order: F1 (table mode) + F2 (forward only) into Z, then copy.
+  RowArgs a = make_args(P);
+  a.j0 = 0;
+  a.rows = 1;
+  if (b.L1 > 1) {
+    const size_t sm = sizeof(C) * b.L1 * a.B;
+    FZP_CUDA_TRY(cudaFuncSetAttribute(k_f1<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_f1<R><<<dim3((unsigned)(b.L2 / a.B), 1), 256, sm>>>(a, 1);
+    FZP_CUDA_TRY(cudaGetLastError());
+  }
+  {
+    const size_t sm = sizeof(C) * b.L2;
+    FZP_CUDA_TRY(cudaFuncSetAttribute(k_f2<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_f2<R><<<dim3((unsigned)b.L1, 1), 512, sm>>>(a, 1);
+    FZP_CUDA_TRY(cudaGetLastError());
+  }
+  FZP_CUDA_TRY(cudaMemcpy(b.d_H, b.d_Z, sizeof(C) * b.L, cudaMemcpyDeviceToDevice));
+  if (b.L1 == 1) {  // Z only served the table build
+    FZP_CUDA_TRY(cudaFree(b.d_Z));
+    b.d_Z = nullptr;
+  }
+  return FZP_OK;
+}
+
+template <typename R>
+fzp_status rows_t(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
+  using C = typename Cplx<R>::T;
+  const Bluestein& b = P.bs;
+  RowArgs a = make_args(P);
+  a.c1_j0 = j0;
+  for (int64_t r0 = 0; r0 < rows; r0 += b.rows) {
+    const int64_t rb = std::min<int64_t>(b.rows, rows - r0);
+    a.j0 = j0 + r0;
+    a.rows = rb;
+    if (b.L1 > 1) {
+      k_f1<R><<<dim3((unsigned)(b.L2 / a.B), (unsigned)rb), 256, sizeof(C) * b.L1 * a.B, s>>>(a, 0);
+      k_f2<R><<<dim3((unsigned)b.L1, (unsigned)rb), 512, sizeof(C) * b.L2, s>>>(a, 0);
+      k_f3<R><<<dim3((unsigned)(P.M / 32), (unsigned)((rb + 31) / 32)), 256, 0, s>>>(a);
+    } else {
+      k_f2<R><<<dim3(1, (unsigned)rb), 512, sizeof(C) * b.L2, s>>>(a, 0);
+    }
+  }
+  FZP_CUDA_TRY(cudaGetLastError());
+  return FZP_OK;
+}
+
+}  // namespace
+
+fzp_status bluestein_build_tables(Plan& P) {
+  return P.precision == FZP_PREC_FP64 ? build_tables_t<double>(P) : build_tables_t<float>(P);
+}
+
+fzp_status bluestein_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream) {
+  return P.precision == FZP_PREC_FP64 ? rows_t<double>(P, j0, rows, stream) : rows_t<float>(P, j0, rows, stream);
+}
+
+}  // namespace fzp

@@ -1,0 +1,184 @@
+// fzp_internal.cuh -- shared declarations of libfzp (CUDA C++, sm_103a).
+//
+// Notation (Eq. 2 and Fig. 2):
+//   aperture sample (j, i), i, j in [0, N), centred index di = i - c, c = (N-1)/2,
+//   u_i = di * dx;  ROI sample (n, m), x_m = (m - M/2) p.
+//   Row kernel K[m, i] = exp(2 pi i theta(m, i)) with the phase in turns
+//     theta(m, i) = di^2 kappa / 2 - (m - M/2) di delta,
+//     kappa = dx^2 / (lambda f),  delta = p dx / (lambda f)   (Eq. 2, Eq. 10).
+//   The same matrix serves the column pass (the grids of both axes coincide):
+//     U = Pre * chirp_out .* (K T K^T).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fzp.h"
+
+namespace fzp {
+
+// --------------------------------------------------------------------------
+// Host-side error handling (thread-local message, no exceptions across ABI)
+// --------------------------------------------------------------------------
+fzp_status set_error(fzp_status st, const char* fmt, ...);
+
+#define FZP_CUDA_TRY(call)                                                              \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return ::fzp::set_error(e_ == cudaErrorMemoryAllocation ? FZP_E_OOM : FZP_E_CUDA, \
+                              "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                              __FILE__, __LINE__);                                      \
+  } while (0)
+
+// --------------------------------------------------------------------------
+// Mask geometry: exact binary FZP rule (paraxial radii, centre opaque)
+//   open(s) = s <= s_R  and  zone(s) odd,   zone(s) = floor(fl(s * kappa)),
+//   s = di^2 + dj^2 an exact integer.  zone(s) = #{m >= 1 : S_m <= s} with the
+//   threshold table S_m = min{s : floor(fl(s kappa)) >= m} built on the host.
+// --------------------------------------------------------------------------
+struct MaskGeom {
+  int64_t c;          // on-axis index
+  int64_t sR;         // largest s inside the aperture disc
+  uint64_t K64;       // floor(kappa * 2^64): fixed-point zone rate
+  const int64_t* thr; // device: thr[m-1] = S_m, m = 1..nthr
+  int64_t nthr;
+};
+
+// zone(s) for 0 <= s <= sR.  The 64x64->128 fixed-point product gives
+// floor(s kappa) except within 2^-19 of an integer; there the threshold table
+// decides, which reproduces floor(fl(s kappa)) bit for bit.
+__device__ __forceinline__ int64_t zone_of(int64_t s, const MaskGeom& g) {
+  const uint64_t hi = __umul64hi((uint64_t)s, g.K64);
+  const uint64_t lo = (uint64_t)s * g.K64;
+  int64_t z = (int64_t)hi;
+  if (lo < (1ull << 31) || lo >= 0xFFFFE00000000000ull) {
+    if (z >= 1 && __ldg(g.thr + (z - 1)) > s) z -= 1;
+    else if (z < g.nthr && __ldg(g.thr + z) <= s) z += 1;
+  }
+  return z;
+}
+
+__device__ __forceinline__ bool mask_open(int64_t dj, int64_t di, const MaskGeom& g) {
+  const int64_t s = dj * dj + di * di;
+  if (s > g.sR) return false;
+  return (zone_of(s, g) & 1) != 0;
+}
+
+// --------------------------------------------------------------------------
+// Phase helpers.  Phases are carried in turns; the integer part is removed in
+// FP64 before the (co)sine is evaluated.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double frac_turns(double t) { return t - rint(t); }
+
+__device__ __forceinline__ float2 cis_turns_f(double t) {
+  float s, c;
+  sincospif((float)(2.0 * frac_turns(t)), &s, &c);
+  return make_float2(c, s);
+}
+
+__device__ __forceinline__ double2 cis_turns_d(double t) {
+  double s, c;
+  sincospi(2.0 * frac_turns(t), &s, &c);
+  return make_double2(c, s);
+}
+
+template <typename R> struct Cplx;
+template <> struct Cplx<float> { using T = float2; };
+template <> struct Cplx<double> { using T = double2; };
+
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+
+template <typename R> __device__ __forceinline__ typename Cplx<R>::T cis_turns(double t);
+template <> __device__ __forceinline__ float2 cis_turns<float>(double t) { return cis_turns_f(t); }
+template <> __device__ __forceinline__ double2 cis_turns<double>(double t) { return cis_turns_d(t); }
+
+// e^{sign 2 pi i r / L} for an exact integer r (0 <= r < L, L a power of two).
+template <typename R> __device__ __forceinline__ typename Cplx<R>::T twiddle(int64_t r, int64_t L, float sign);
+template <> __device__ __forceinline__ float2 twiddle<float>(int64_t r, int64_t L, float sign) {
+  float s, c;
+  sincospif(sign * 2.0f * (float)r / (float)L, &s, &c);
+  return make_float2(c, s);
+}
+template <> __device__ __forceinline__ double2 twiddle<double>(int64_t r, int64_t L, float sign) {
+  double s, c;
+  sincospi((double)sign * 2.0 * (double)r / (double)L, &s, &c);
+  return make_double2(c, s);
+}
+
+// --------------------------------------------------------------------------
+// Plan
+// --------------------------------------------------------------------------
+struct Bluestein {
+  int64_t L = 0;     // convolution length, power of two >= N + M - 1
+  int64_t L1 = 1;    // four-step split L = L1 * L2 (L1 = 1: single pass)
+  int64_t L2 = 0;
+  void* d_pre = nullptr;  // N entries: e^{2 pi i pre(i)} (complex64 or complex128)
+  void* d_H = nullptr;    // L entries: FFT_L of the convolution chirp, stored [k1][k2]
+  void* d_Z = nullptr;    // workspace [rows][L1][L2]
+  void* d_G = nullptr;    // workspace [rows][L1][M]
+  void* d_tab = nullptr;  // table block: chirp v (L) | twiddles (L2/2) | post (M)
+  void* d_tw = nullptr;   // into d_tab
+  void* d_post = nullptr; // into d_tab
+  int64_t rows = 0;       // rows per batch of the workspace
+};
+
+struct Dense {
+  void* d_A = nullptr;     // kernel matrix, split-BF16, pre-swizzled tiles
+  int64_t kblocks = 0;     // ceil(N / 64)
+  int ntiles = 0;          // 2M / 128 row tiles of the kernel matrix
+  int promote_kblocks = 0; // K blocks per TMEM accumulation chunk
+  int num_sms = 0;
+};
+
+struct Plan {
+  // problem
+  double D, f, lambda, dx, R, p, x0;
+  int64_t N, c;
+  int M;
+  int form, precision, stripe_rows;
+  // derived
+  double kappa, delta, dx2, R2;
+  int64_t total_zones;
+  MaskGeom mg;
+  int64_t* d_thr = nullptr;
+  bool has_deform = false;
+  fzp_deform deform{};
+  // workspace shared by both forms
+  float* d_C1 = nullptr;       // row intermediate [2M][chunk_rows] (FP32 forms)
+  double* d_C1d = nullptr;     // row intermediate [2M][chunk_rows] (FP64 form)
+  int64_t chunk_rows = 0;
+  double2* d_Uacc = nullptr;   // FP64 ROI accumulator M*M
+  int* d_err = nullptr;        // device error word (bounded waits)
+  double* d_metrics = nullptr; // device scratch for the metric extractor
+  size_t device_bytes = 0;
+  Bluestein bs;
+  Dense dn;
+};
+
+// Launchers implemented in the .cu files.  All enqueue on `stream`.
+fzp_status bluestein_build_tables(Plan& P);
+fzp_status bluestein_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream);
+fzp_status dense_build_tables(Plan& P);
+fzp_status dense_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream);
+fzp_status column_pass(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream);
+fzp_status epilogue(Plan& P, void* d_field, int accumulate, cudaStream_t stream);
+fzp_status intensity(Plan& P, const void* d_field, void* d_I, cudaStream_t stream);
+fzp_status metrics(Plan& P, const void* d_field, cudaStream_t stream, fzp_metrics_t* out);
+
+// Row index into the C1 layout: kernel row tile t = m / 64 holds the real parts
+// of m = 64t..64t+63 in rows [0,64) and the imaginary parts in rows [64,128).
+__host__ __device__ __forceinline__ int c1_row_re(int m) { return (m >> 6) * 128 + (m & 63); }
+__host__ __device__ __forceinline__ int c1_row_im(int m) { return (m >> 6) * 128 + 64 + (m & 63); }
+
+}  // namespace fzp
+
+// The opaque handle of the C ABI is the plan itself.
+struct fzp_plan_s : public fzp::Plan {};

@@ -1,0 +1,264 @@
+// plan.cu -- C ABI entry points, parameter validation, grids and the exact
+// zone-threshold table (Fig. 2 Stage 1-2; Fig. 18 Stage 1-2).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fzp_internal.cuh"
+
+namespace fzp {
+
+static thread_local char g_errmsg[512] = "";
+
+fzp_status set_error(fzp_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_errmsg, sizeof(g_errmsg), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+// fl(s * a) with s an exact integer below 2^53 (one IEEE multiply).
+static inline double mul_exact_int(int64_t s, double a) {
+  volatile double prod = (double)s * a;  // volatile: no contraction, no reassociation
+  return prod;
+}
+
+// Largest s >= 0 with fl(s * dx2) <= R2 (aperture disc, Fig. 2 Stage 2).
+static int64_t disc_limit(double dx2, double R2) {
+  int64_t s = (int64_t)std::floor(R2 / dx2);
+  if (s < 0) s = 0;
+  while (mul_exact_int(s + 1, dx2) <= R2) ++s;
+  while (s > 0 && mul_exact_int(s, dx2) > R2) --s;
+  return s;
+}
+
+static inline int64_t zone_host(int64_t s, double kappa) {
+  return (int64_t)std::floor(mul_exact_int(s, kappa));
+}
+
+// S_m = min{s : floor(fl(s kappa)) >= m}, m = 1..count.
+static void thresholds(double kappa, int64_t count, std::vector<int64_t>& S) {
+  S.resize((size_t)count);
+  for (int64_t m = 1; m <= count; ++m) {
+    int64_t s = (int64_t)std::ceil((double)m / kappa);
+    if (s < 0) s = 0;
+    while (s > 0 && zone_host(s - 1, kappa) >= m) --s;
+    while (zone_host(s, kappa) < m) ++s;
+    S[(size_t)(m - 1)] = s;
+  }
+}
+
+static void release(fzp_plan_s* P) {
+  if (!P) return;
+  void* ptrs[] = {P->d_thr, P->d_C1, P->d_C1d, P->d_Uacc, P->d_err, P->d_metrics,
+                  P->bs.d_pre, P->bs.d_H, P->bs.d_Z, P->bs.d_G, P->bs.d_tab, P->dn.d_A};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete P;
+}
+
+static fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
+  if (!(in->D > 0) || !(in->f > 0) || !(in->lambda > 0) || !(in->pitch > 0) || !std::isfinite(in->D) ||
+      !std::isfinite(in->f) || !std::isfinite(in->lambda) || !std::isfinite(in->pitch))
+    return set_error(FZP_E_INVALID, "D, f, lambda and pitch must be finite and positive");
+  if (in->dx < 0 || !std::isfinite(in->dx)) return set_error(FZP_E_INVALID, "dx must be >= 0");
+  if (in->M < 64 || in->M > 1024 || (in->M & (in->M - 1)) != 0)
+    return set_error(FZP_E_INVALID, "M must be a power of two in [64, 1024] (got %d)", in->M);
+  if (in->N < 0 || (in->N > 0 && (in->N % 2) == 0))
+    return set_error(FZP_E_INVALID, "N must be 0 (derive) or odd (got %lld)", (long long)in->N);
+  if (in->stripe_rows < 0) return set_error(FZP_E_INVALID, "stripe_rows must be >= 0");
+  if (in->form < FZP_FORM_AUTO || in->form > FZP_FORM_DENSE) return set_error(FZP_E_INVALID, "unknown form");
+  if (in->precision < FZP_PREC_FP64 || in->precision > FZP_PREC_BF16)
+    return set_error(FZP_E_INVALID, "unknown precision");
+  if (in->deform && (in->deform->n_ridges < 0 || in->deform->n_ridges > 3))
+    return set_error(FZP_E_INVALID, "deform.n_ridges must be in [0, 3]");
+  const double lf = in->lambda * in->f;
+  P.D = in->D; P.f = in->f; P.lambda = in->lambda; P.p = in->pitch; P.M = in->M;
+  P.dx = in->dx > 0 ? in->dx : lf / (4.0 * in->D);
+  // Eq. 6: dx <= lambda f / (2 D)  (two samples across the outermost zone)
+  if (P.dx > lf / (2.0 * in->D) * (1.0 + 1e-12))
+    return set_error(FZP_E_INVALID, "dx = %g violates Eq. 6 (dx <= lambda f / (2D) = %g)", P.dx, lf / (2.0 * in->D));
+  if (in->N > 0) {
+    P.N = in->N;
+  } else {
+    const double n = std::ceil(in->D / P.dx);
+    if (!(n < 1e9)) return set_error(FZP_E_INVALID, "grid too large (N = %g)", n);
+    P.N = (int64_t)n;
+    if ((P.N % 2) == 0) P.N += 1;  // forced odd: sample c on the axis (Fig. 2 Stage 1)
+  }
+  if (P.N < 3) return set_error(FZP_E_INVALID, "N must be >= 3");
+  P.c = (P.N - 1) / 2;
+  P.R = std::min(in->D / 2.0, lf / (2.0 * P.dx));  // R_eff (Fig. 2 Stage 2)
+  P.x0 = -(double)(P.M / 2) * P.p;
+  P.dx2 = P.dx * P.dx;
+  P.R2 = P.R * P.R;
+  P.kappa = P.dx2 / lf;
+  P.delta = P.p * P.dx / lf;  // Eq. 10: W = exp(-2 pi i dx_out dx_in / (lambda z))
+  // Eq. 3 zone count: (lambda^2/4) n^2 + lambda f n - R^2 = 0
+  {
+    const double a = in->lambda * in->lambda / 4.0, b = lf, cc = -P.R2;
+    P.total_zones = (int64_t)std::floor((-b + std::sqrt(b * b - 4 * a * cc)) / (2 * a));
+  }
+  // form / precision
+  P.precision = in->precision;
+  P.form = in->form;
+  const bool dense_prec = (P.precision == FZP_PREC_SPLIT_BF16 || P.precision == FZP_PREC_BF16);
+  if (P.form == FZP_FORM_AUTO) P.form = dense_prec ? FZP_FORM_DENSE : FZP_FORM_BLUESTEIN;
+  if (P.form == FZP_FORM_DENSE && !dense_prec)
+    return set_error(FZP_E_UNSUPPORTED, "dense form runs in split-BF16 or BF16 precision only");
+  if (P.form == FZP_FORM_BLUESTEIN && dense_prec)
+    return set_error(FZP_E_UNSUPPORTED, "Bluestein form runs in FP32 or FP64 precision only");
+  if (in->deform) {
+    if (P.form == FZP_FORM_DENSE)
+      return set_error(FZP_E_UNSUPPORTED, "deformation phase is supported by the Bluestein form only");
+    P.has_deform = true;
+    P.deform = *in->deform;
+  }
+  P.stripe_rows = in->stripe_rows;
+  return FZP_OK;
+}
+
+static fzp_status build_mask_tables(Plan& P) {
+  P.mg.c = P.c;
+  P.mg.sR = disc_limit(P.dx2, P.R2);
+  const int64_t zmax = zone_host(P.mg.sR, P.kappa);
+  // zone_of() error analysis needs s_R < 2^44 and zone < 2^19.
+  if (P.mg.sR >= (1ll << 44) || zmax + 1 >= (1ll << 19))
+    return set_error(FZP_E_UNSUPPORTED, "aperture too large for the exact zone rule (s_R=%lld, zones=%lld)",
+                     (long long)P.mg.sR, (long long)zmax);
+  const double k64 = std::ldexp(P.kappa, 64);
+  if (!(k64 < 18446744073709551616.0)) return set_error(FZP_E_INVALID, "kappa >= 1: grid far too coarse");
+  P.mg.K64 = (uint64_t)std::floor(k64);
+  std::vector<int64_t> S;
+  thresholds(P.kappa, zmax + 2, S);
+  P.mg.nthr = (int64_t)S.size();
+  FZP_CUDA_TRY(cudaMalloc(&P.d_thr, S.size() * sizeof(int64_t)));
+  P.device_bytes += S.size() * sizeof(int64_t);
+  FZP_CUDA_TRY(cudaMemcpy(P.d_thr, S.data(), S.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  P.mg.thr = P.d_thr;
+  return FZP_OK;
+}
+
+// Rows of [0, N) that intersect the aperture disc: dj^2 <= s_R.
+static void disc_rows(const Plan& P, int64_t& jlo, int64_t& jhi) {
+  int64_t b = (int64_t)std::floor(std::sqrt((double)P.mg.sR));
+  while ((b + 1) * (b + 1) <= P.mg.sR) ++b;
+  while (b * b > P.mg.sR) --b;
+  jlo = P.c - b;
+  jhi = P.c + b + 1;
+  if (jlo < 0) jlo = 0;
+  if (jhi > P.N) jhi = P.N;
+}
+
+}  // namespace fzp
+
+using namespace fzp;
+
+extern "C" {
+
+const char* fzp_last_error(void) { return g_errmsg; }
+
+const char* fzp_version(void) { return "libfzp 0.1 (sm_103a)"; }
+
+fzp_status fzp_plan(const fzp_params* params, fzp_plan_t* out) {
+  if (!out) return set_error(FZP_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!params) return set_error(FZP_E_INVALID, "params is NULL");
+  fzp_plan_s* P = new (std::nothrow) fzp_plan_s();
+  if (!P) return set_error(FZP_E_OOM, "host allocation failed");
+  fzp_status st = validate_and_derive(params, *P);
+  if (st != FZP_OK) { release(P); return st; }
+  g_errmsg[0] = 0;
+  st = build_mask_tables(*P);
+  if (st == FZP_OK) {
+    const int64_t M2 = 2 * (int64_t)P->M;
+    // Row intermediate for a chunk of rows; the default budget keeps it <= 8 GiB.
+    const int64_t budget_rows = (int64_t)((8ull << 30) / (uint64_t)(M2 * (P->precision == FZP_PREC_FP64 ? 8 : 4)));
+    int64_t rows = std::min<int64_t>(P->N, budget_rows);
+    rows = (rows + 255) / 256 * 256;
+    P->chunk_rows = rows;
+    cudaError_t e = cudaSuccess;
+    if (P->precision == FZP_PREC_FP64) e = cudaMalloc(&P->d_C1d, (size_t)(M2 * rows) * sizeof(double));
+    else e = cudaMalloc(&P->d_C1, (size_t)(M2 * rows) * sizeof(float));
+    P->device_bytes += (size_t)(M2 * rows) * (P->precision == FZP_PREC_FP64 ? 8 : 4);
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_Uacc, (size_t)P->M * P->M * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_metrics, 8192 * sizeof(double) + (size_t)P->M * P->M * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMemset(P->d_err, 0, sizeof(int));
+    P->device_bytes += (size_t)P->M * P->M * sizeof(double2) * 2 + 8192 * sizeof(double) + sizeof(int);
+    if (e != cudaSuccess) {
+      st = set_error(e == cudaErrorMemoryAllocation ? FZP_E_OOM : FZP_E_CUDA, "workspace allocation: %s",
+                     cudaGetErrorString(e));
+      cudaGetLastError();
+    }
+  }
+  if (st == FZP_OK) st = (P->form == FZP_FORM_DENSE) ? dense_build_tables(*P) : bluestein_build_tables(*P);
+  if (st == FZP_OK) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) st = set_error(FZP_E_CUDA, "plan build: %s", cudaGetErrorString(e));
+  }
+  if (st != FZP_OK) {
+    cudaGetLastError();
+    release(P);
+    return st;
+  }
+  *out = P;
+  return FZP_OK;
+}
+
+fzp_status fzp_plan_info_get(fzp_plan_t plan, fzp_plan_info* out) {
+  if (!plan || !out) return set_error(FZP_E_INVALID, "NULL argument");
+  const Plan& P = *plan;
+  out->N = P.N; out->c = P.c; out->total_zones = P.total_zones; out->n_thresholds = P.mg.nthr;
+  out->dx = P.dx; out->R = P.R; out->kappa = P.kappa; out->x0 = P.x0;
+  out->M = P.M; out->form = P.form; out->precision = P.precision;
+  out->stripe_rows = P.stripe_rows;
+  out->fft_length = P.bs.L;
+  out->device_bytes = P.device_bytes;
+  return FZP_OK;
+}
+
+fzp_status fzp_plan_destroy(fzp_plan_t plan) {
+  if (!plan) return FZP_OK;
+  cudaDeviceSynchronize();
+  release(plan);
+  return FZP_OK;
+}
+
+fzp_status fzp_propagate_roi(fzp_plan_t plan, int64_t row_begin, int64_t row_end, void* d_field, int accumulate,
+                             void* stream) {
+  if (!plan || !d_field) return set_error(FZP_E_INVALID, "NULL plan or field");
+  Plan& P = *plan;
+  if (row_begin < 0 || row_end > P.N || row_begin > row_end)
+    return set_error(FZP_E_INVALID, "row range [%lld, %lld) outside [0, %lld]", (long long)row_begin,
+                     (long long)row_end, (long long)P.N);
+  cudaStream_t s = (cudaStream_t)stream;
+  FZP_CUDA_TRY(cudaMemsetAsync(P.d_Uacc, 0, (size_t)P.M * P.M * sizeof(double2), s));
+  int64_t jlo, jhi;
+  disc_rows(P, jlo, jhi);
+  const int64_t a = std::max(row_begin, jlo), b = std::min(row_end, jhi);
+  for (int64_t j0 = a; j0 < b; j0 += P.chunk_rows) {
+    const int64_t rows = std::min(P.chunk_rows, b - j0);
+    fzp_status st = (P.form == FZP_FORM_DENSE) ? dense_rows(P, j0, rows, s) : bluestein_rows(P, j0, rows, s);
+    if (st != FZP_OK) return st;
+    st = column_pass(P, j0, rows, s);
+    if (st != FZP_OK) return st;
+  }
+  return epilogue(P, d_field, accumulate, s);
+}
+
+fzp_status fzp_intensity(fzp_plan_t plan, const void* d_field, void* d_intensity, void* stream) {
+  if (!plan || !d_field || !d_intensity) return set_error(FZP_E_INVALID, "NULL argument");
+  return intensity(*plan, d_field, d_intensity, (cudaStream_t)stream);
+}
+
+fzp_status fzp_metrics(fzp_plan_t plan, const void* d_field, void* stream, fzp_metrics_t* out) {
+  if (!plan || !d_field || !out) return set_error(FZP_E_INVALID, "NULL argument");
+  return metrics(*plan, d_field, (cudaStream_t)stream, out);
+}
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every function include/fzp.h declares, and rejects invalid input before it
+touches the device."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fzp():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2609_01978_gb300 as m
+    return m
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"FZP_API\s+[\w\s\*]+?\b(fzp_\w+)\s*\(", txt))
+    return names
+
+
+def test_exports_every_declared_symbol(fzp):
+    names = _declared()
+    assert {"fzp_plan", "fzp_propagate_roi", "fzp_metrics", "fzp_plan_destroy", "fzp_last_error"} <= names
+    L = fzp.lib()
+    for n in sorted(names):
+        assert hasattr(L, n), n
+
+
+@pytest.mark.parametrize("kw,frag", [
+    (dict(D=-1.0), "positive"),
+    (dict(f=0.0), "positive"),
+    (dict(lam=float("nan")), "finite"),
+    (dict(pitch=0.0), "positive"),
+    (dict(M=100), "power of two"),
+    (dict(M=32), "power of two"),
+    (dict(M=2048), "power of two"),
+    (dict(N=1000), "odd"),
+    (dict(dx=2e-6), "Eq. 6"),
+    (dict(form=7), "form"),
+    (dict(precision=9), "precision"),
+])
+def test_invalid_parameters_rejected(fzp, kw, frag):
+    base = dict(D=1e-3, f=5e-3, lam=632.8e-9, M=64, pitch=0.4e-6)
+    base.update(kw)
+    with pytest.raises(fzp.FzpError) as ei:
+        fzp.Plan(**base)
+    assert ei.value.status == fzp.FZP_E_INVALID
+    assert frag in str(ei.value)
+
+
+def test_unsupported_combinations(fzp):
+    base = dict(D=1e-3, f=5e-3, lam=632.8e-9, M=64, pitch=0.4e-6)
+    with pytest.raises(fzp.FzpError) as ei:
+        fzp.Plan(form=fzp.FORM_DENSE, precision=fzp.PREC_FP32, **base)
+    assert ei.value.status == fzp.FZP_E_UNSUPPORTED
+    with pytest.raises(fzp.FzpError) as ei:
+        fzp.Plan(form=fzp.FORM_BLUESTEIN, precision=fzp.PREC_SPLIT_BF16, **base)
+    assert ei.value.status == fzp.FZP_E_UNSUPPORTED
+
+
+def test_null_arguments(fzp):
+    import ctypes
+    L = fzp.lib()
+    assert L.fzp_plan(None, None) == fzp.FZP_E_INVALID
+    h = ctypes.c_void_p()
+    assert L.fzp_plan(None, ctypes.byref(h)) == fzp.FZP_E_INVALID and not h.value
+    assert L.fzp_propagate_roi(None, 0, 1, None, 0, None) == fzp.FZP_E_INVALID
+    assert L.fzp_metrics(None, None, None, None) == fzp.FZP_E_INVALID
+    assert L.fzp_plan_destroy(None) == fzp.FZP_OK
+    assert b"NULL" in L.fzp_last_error() or L.fzp_last_error() != b""

@@ -290,7 +290,10 @@ def test_mtf_extractor_gaussian(oracle_mod):
     c, mean = oracle_mod.mtf_radial(I, p)
     fu = np.fft.fftfreq(M, d=p)
     nu = np.hypot(fu[None, :], fu[:, None])
-    b = np.floor(nu * 2 * p * 200).astype(int)
+    # bin of each sample: largest b with b <= 200 |k| / (M/2), by exact integer search
+    kk = [int(round(v)) for v in np.fft.fftfreq(M) * M]
+    b = np.array([[max(t for t in range(0, 300) if (t * M) ** 2 <= 160000 * (kv * kv + ku * ku))
+                   for ku in kk] for kv in kk])
     ok = b < 200
     ref = np.bincount(b[ok], weights=np.exp(-2 * np.pi ** 2 * sigma ** 2 * nu[ok] ** 2), minlength=200)
     cnt = np.bincount(b[ok], minlength=200)
