@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Benchmark of the stripe-processed CZT Fresnel propagator (one JSON line).
+
+A step is one pass of the whole hot path over the workload: every aperture row
+of a procedurally generated binary Fresnel zone plate through the row transform
+(mask generation, chirps, row CZT), the column pass with FP64 cross-stripe
+accumulation, the output chirp / prefactor epilogue, and the metric extractor
+(FWHM, DE, MTF).  The metric is aperture samples (N^2 per step) per second into
+a 512^2 ROI.
+
+Workload (default "fzp-d0.25m"): binary amplitude FZP, D = 0.25 m,
+lambda = 632.8 nm, f/# = 5 (f = 1.25 m), 4 samples per outermost zone width
+(dx = 0.791 um, N = 316,057 per side, 9.99e10 samples), ROI 512^2 at
+lambda f/# / 8 = 0.3955 um, centred on the focus.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--form dense|bluestein]
+                  [--impl ours|reference] [--workload fzp-d0.25m|fzp-d1m]
+
+Under torchrun (N > 1) every rank propagates its own copy of the aperture
+(independent problems: weak scaling, no collective on the data path); rank 0
+prints the line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "fzp-d0.25m": dict(D=0.25, lam=632.8e-9, fnum=5.0, M=512),
+    "fzp-d1m": dict(D=1.0, lam=632.8e-9, fnum=5.0, M=512),
+}
+METRIC = "aperture Gsamples/s into 512² ROI, split-BF16 vs FP32 CZT at ≤1e-4 PSF error"
+UNIT = "Gsamples/s"
+SM_COUNT = 152
+SM_MAX_MHZ_NOMINAL = 2070.0
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _print(obj):
+    print(json.dumps(obj), flush=True)
+
+
+def bluestein_f2_flops(info: dict, rows: int) -> float:
+    """Algorithmic FP32 flops of the dominant Bluestein pass (forward L2-point FFT,
+    product with H, inverse L2-point FFT) for `rows` aperture rows: per row and
+    per inner transform 2 x 5 L2 log2 L2 + 6 L2, L1 inner transforms per row."""
+    L = info["fft_length"]
+    L2 = min(L, 8192)
+    L1 = L // L2
+    lg = L2.bit_length() - 1
+    return rows * L1 * (10.0 * L2 * lg + 6.0 * L2)
+
+
+def run_reference(args, wl):
+    """The oracle (CPU FP64 Bluestein CZT, fzp_oracle.c) timed on the host cores on
+    a bounded sample of aperture rows of the same workload."""
+    import oracle as O
+    g = O.Geometry(D=wl["D"], f=wl["D"] * wl["fnum"], lam=wl["lam"], M=wl["M"], p=wl["lam"] * wl["fnum"] / 8)
+    rows = args.ref_rows
+    j0 = g.c - rows // 2
+    for _ in range(args.warmup):
+        O.field_czt(g, j0, j0 + rows)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.field_czt(g, j0, j0 + rows)
+    dt = time.perf_counter() - t0
+    value = args.steps * rows * g.N / dt / 1e9
+    cores = O.max_threads()
+    sample = f"{rows} central aperture rows of {g.N} (x {args.steps} steps), full row and column CZT, FP64"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (procedural zone plate)",
+            "config": {"workload": args.workload, "N": g.N, "M": g.M, "rows_per_step": rows},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def cpu_baseline(wl, budget_s: float = 15.0) -> dict:
+    import oracle as O
+    g = O.Geometry(D=wl["D"], f=wl["D"] * wl["fnum"], lam=wl["lam"], M=wl["M"], p=wl["lam"] * wl["fnum"] / 8)
+    rows = 16
+    j0 = g.c - rows // 2
+    t0 = time.perf_counter()
+    O.field_czt(g, j0, j0 + rows)
+    dt = time.perf_counter() - t0
+    rows = max(16, min(g.N, int(rows * budget_s / max(dt, 1e-3))))
+    j0 = g.c - rows // 2
+    t0 = time.perf_counter()
+    O.field_czt(g, j0, j0 + rows)
+    dt = time.perf_counter() - t0
+    return {"value": rows * g.N / dt / 1e9, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+            "sample": f"{rows} central aperture rows of N = {g.N} (row + column CZT, FP64), {dt:.1f} s",
+            "seconds": dt}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fzp-d0.25m", choices=sorted(WORKLOADS))
+    ap.add_argument("--form", default="bluestein", choices=["dense", "bluestein"])
+    ap.add_argument("--ref-rows", type=int, default=48)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    ws, rank, local = _dist()
+
+    if args.impl == "reference":
+        if rank == 0:
+            _print(run_reference(args, wl))
+        return
+
+    import torch
+    import __graft_entry__
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    import paper_2609_01978_gb300 as fzp
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+        if rank != 0:
+            __graft_entry__.build()  # already built by rank 0; loads the library
+        dist.barrier()
+    D, lam, fnum, M = wl["D"], wl["lam"], wl["fnum"], wl["M"]
+    if args.form == "dense":
+        form, prec, dtype = fzp.FORM_DENSE, fzp.PREC_SPLIT_BF16, "bf16x2"
+    else:
+        form, prec, dtype = fzp.FORM_BLUESTEIN, fzp.PREC_FP32, "f32"
+    params = dict(D=D, f=D * fnum, lam=lam, M=M, pitch=lam * fnum / 8, form=form, precision=prec)
+    plan = fzp.Plan(**params)
+    info = plan.info
+    N = info["N"]
+    stream = torch.cuda.current_stream(dev)
+    U = torch.empty((M, M), dtype=torch.complex128, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MiB > L2 (129 MB)
+
+    def step():
+        flush.fill_(1.0)  # evict L2 between steps
+        plan.propagate_roi(0, N, U, stream=stream)
+        return plan.metrics(U, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    plan.profile(True)
+    plan.profile_read()  # reset counters
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        m = step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof = plan.profile_read()
+    plan.profile(False)
+    clocks = sampler.stop() if sampler else None
+    if pg:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * args.steps * N * N / (ms / 1e3) / 1e9
+
+    # roofline of the dominant kernel, from CUDA events on its own stream
+    peaks, peak_kind = _peaks()
+    avg_ms = prof["dominant_ms"] / max(1, prof["dominant_launches"])
+    if args.form == "dense":
+        flops_launch = prof.get("flops_per_launch", 0.0)
+        achieved = flops_launch / (avg_ms / 1e3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": prof["dominant_name"], "peak_source": peak_kind + " bf16 sustained"}
+    else:
+        launches = max(1, prof["dominant_launches"])
+        rows_per_launch = N * args.steps / launches
+        flops_launch = bluestein_f2_flops(info, rows_per_launch)
+        achieved = flops_launch / (avg_ms / 1e3) / 1e12
+        peak = SM_COUNT * 128 * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12  # FP32 FMA lanes x clock
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": prof["dominant_name"],
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+
+    # end to end through the public API with host buffers: plan from host
+    # parameters (zone-threshold table uploaded), propagate, copy the ROI field
+    # to pinned host memory, metrics to host, destroy.
+    host = torch.empty((M, M), dtype=torch.complex128, pin_memory=True)
+    e2e_steps = max(1, args.e2e_steps)
+    torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    t0 = time.perf_counter()
+    h2d = 0
+    for _ in range(e2e_steps):
+        with fzp.Plan(**params) as p2:
+            h2d = 8 * p2.info["n_thresholds"] + 96
+            p2.propagate_roi(0, N, U, stream=stream)
+            host.copy_(U, non_blocking=True)
+            p2.metrics(U, stream=stream)
+            torch.cuda.synchronize(dev)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if pg:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": ws * N * N / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": M * M * 16 + 8 * 28,
+           "note": "fzp_plan + fzp_propagate_roi + field to pinned host + fzp_metrics + fzp_plan_destroy"}
+    plan.close()
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": dtype, "data": "synthetic (procedural binary zone plate)",
+           "config": {"workload": args.workload, "form": args.form, "D_m": D, "lambda_m": lam, "f_number": fnum,
+                      "N": N, "samples_per_step": N * N, "roi": M, "roi_pitch_m": lam * fnum / 8,
+                      "l2": "256 MiB buffer written between steps (flush)"},
+           "roofline": roof, "e2e": e2e, "gpu_launches": prof["kernel_launches"], "clocks": clocks,
+           "metrics_last_step": {k: m[k] for k in ("fwhm_x", "de_lobe", "mtf_half_cut")}}
+    if ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl)
+    _print(out)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

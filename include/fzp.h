@@ -176,6 +176,33 @@ FZP_API fzp_status fzp_intensity(fzp_plan_t plan, const void* d_field, void* d_i
  * (FZP_E_TIMEOUT). */
 FZP_API fzp_status fzp_metrics(fzp_plan_t plan, const void* d_field, void* stream, fzp_metrics_t* out);
 
+/* Binary aperture transmission T[j, i] of rows [row_begin, row_end), produced
+ * by the same device code that feeds the plan's row transform (Fig. 2 Stage 2:
+ * open where the paraxial zone index floor(r^2/(lambda f)) is odd and
+ * r <= R_eff), for inspection and testing.  The dense form's generator walks
+ * zone thresholds along each row; the Bluestein form's evaluates each sample.
+ *   d_mask  device uint8, (row_end - row_begin) * N, row-major, 0 or 1.
+ * Errors: FZP_E_INVALID (range outside [0, N], NULL). */
+FZP_API fzp_status fzp_aperture_mask(fzp_plan_t plan, int64_t row_begin, int64_t row_end, void* d_mask,
+                                     void* stream);
+
+/* Tracing of one plan (Sec. 5 of the paper times t_row / t_col with tic/toc;
+ * here CUDA events are recorded on the launching stream around every launch of
+ * the form's dominant kernel while profiling is enabled). */
+typedef struct fzp_profile_t {
+  double dominant_ms;        /* summed device time of the dominant kernel [ms]      */
+  int64_t dominant_launches; /* its launches since the last read                    */
+  int64_t kernel_launches;   /* all kernels this plan launched since the last read  */
+  char dominant_name[48];    /* kernel name                                         */
+} fzp_profile_t;
+
+/* Enable (1) or disable (0) event recording for `plan`. */
+FZP_API fzp_status fzp_profile_enable(fzp_plan_t plan, int enable);
+
+/* Synchronise on the recorded events, write the totals to *out (host) and
+ * reset them. */
+FZP_API fzp_status fzp_profile_read(fzp_plan_t plan, fzp_profile_t* out);
+
 /* Message of the calling thread's last failed call ("" if none). */
 FZP_API const char* fzp_last_error(void);
 

@@ -68,6 +68,11 @@ class Metrics(ctypes.Structure):
         return d
 
 
+class Profile(ctypes.Structure):
+    _fields_ = [("dominant_ms", ctypes.c_double), ("dominant_launches", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("dominant_name", ctypes.c_char * 48)]
+
+
 _lib = None
 
 
@@ -87,6 +92,9 @@ def lib() -> ctypes.CDLL:
             "fzp_propagate_roi": [vp, i64, i64, vp, i32, vp],
             "fzp_intensity": [vp, vp, vp, vp],
             "fzp_metrics": [vp, vp, vp, ctypes.POINTER(Metrics)],
+            "fzp_aperture_mask": [vp, i64, i64, vp, vp],
+            "fzp_profile_enable": [vp, i32],
+            "fzp_profile_read": [vp, ctypes.POINTER(Profile)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -161,6 +169,18 @@ class Plan:
         m = Metrics()
         _check(lib().fzp_metrics(self._h, _ptr(field), _stream(stream), ctypes.byref(m)))
         return m.as_dict()
+
+    def aperture_mask(self, row_begin: int, row_end: int, out, stream=None):
+        _check(lib().fzp_aperture_mask(self._h, row_begin, row_end, _ptr(out), _stream(stream)))
+
+    def profile(self, enable: bool = True):
+        _check(lib().fzp_profile_enable(self._h, int(enable)))
+
+    def profile_read(self) -> dict:
+        p = Profile()
+        _check(lib().fzp_profile_read(self._h, ctypes.byref(p)))
+        return {"dominant_ms": p.dominant_ms, "dominant_launches": p.dominant_launches,
+                "kernel_launches": p.kernel_launches, "dominant_name": p.dominant_name.decode()}
 
     def close(self):
         if getattr(self, "_h", None):

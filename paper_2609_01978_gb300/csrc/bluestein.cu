@@ -369,23 +369,45 @@ fzp_status rows_t(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
     a.rows = rb;
     if (b.L1 > 1) {
       k_f1<R><<<dim3((unsigned)(b.L2 / a.B), (unsigned)rb), 256, sizeof(C) * b.L1 * a.B, s>>>(a, 0);
+      prof_begin(P, s);
       k_f2<R><<<dim3((unsigned)b.L1, (unsigned)rb), 512, sizeof(C) * b.L2, s>>>(a, 0);
+      prof_end(P, s);
       k_f3<R><<<dim3((unsigned)(P.M / 32), (unsigned)((rb + 31) / 32)), 256, 0, s>>>(a);
+      P.launches += 3;
     } else {
+      prof_begin(P, s);
       k_f2<R><<<dim3(1, (unsigned)rb), 512, sizeof(C) * b.L2, s>>>(a, 0);
+      prof_end(P, s);
+      P.launches += 1;
     }
   }
   FZP_CUDA_TRY(cudaGetLastError());
   return FZP_OK;
 }
 
+__global__ void k_mask(MaskGeom mg, int64_t N, int64_t j0, int64_t rows, uint8_t* out) {
+  const int64_t total = rows * N;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / N, i = t % N;
+    out[t] = mask_open(j0 + r - mg.c, i - mg.c, mg) ? 1 : 0;
+  }
+}
+
 }  // namespace
+
+fzp_status bluestein_mask(Plan& P, int64_t j0, int64_t rows, uint8_t* out, cudaStream_t s) {
+  k_mask<<<1024, 256, 0, s>>>(P.mg, P.N, j0, rows, out);
+  P.launches += 1;
+  FZP_CUDA_TRY(cudaGetLastError());
+  return FZP_OK;
+}
 
 fzp_status bluestein_build_tables(Plan& P) {
   return P.precision == FZP_PREC_FP64 ? build_tables_t<double>(P) : build_tables_t<float>(P);
 }
 
 fzp_status bluestein_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream) {
+  P.dominant = P.precision == FZP_PREC_FP64 ? "bluestein_f2<double>" : "bluestein_f2<float>";
   return P.precision == FZP_PREC_FP64 ? rows_t<double>(P, j0, rows, stream) : rows_t<float>(P, j0, rows, stream);
 }
 

@@ -158,6 +158,7 @@ fzp_status column_pass(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
   dim3 grid((unsigned)(P.M / TM), (unsigned)(P.M / TN), (unsigned)((rows + JC - 1) / JC));
   if (P.precision == FZP_PREC_FP64) k_colpass<double><<<grid, 256, 0, s>>>(g, P.d_C1d, P.d_Uacc);
   else k_colpass<float><<<grid, 256, 0, s>>>(g, P.d_C1, P.d_Uacc);
+  P.launches += 1;
   FZP_CUDA_TRY(cudaGetLastError());
   return FZP_OK;
 }
@@ -167,6 +168,7 @@ fzp_status epilogue(Plan& P, void* d_field, int accumulate, cudaStream_t s) {
   const int count = P.M * P.M;
   k_epilogue<<<(count + 255) / 256, 256, 0, s>>>(P.M, P.p, lf, P.f / P.lambda, P.dx2 / lf, P.d_Uacc,
                                                  reinterpret_cast<double2*>(d_field), accumulate);
+  P.launches += 1;
   FZP_CUDA_TRY(cudaGetLastError());
   return FZP_OK;
 }
@@ -175,6 +177,7 @@ fzp_status intensity(Plan& P, const void* d_field, void* d_I, cudaStream_t s) {
   const int64_t count = (int64_t)P.M * P.M;
   k_intensity<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(count, reinterpret_cast<const double2*>(d_field),
                                                                reinterpret_cast<double*>(d_I));
+  P.launches += 1;
   FZP_CUDA_TRY(cudaGetLastError());
   return FZP_OK;
 }

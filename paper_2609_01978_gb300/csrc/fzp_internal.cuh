@@ -13,6 +13,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+#include <vector>
+
 #include "../../include/fzp.h"
 
 namespace fzp {
@@ -161,7 +164,18 @@ struct Plan {
   size_t device_bytes = 0;
   Bluestein bs;
   Dense dn;
+  // tracing: kernel launches issued, and CUDA events around the dominant
+  // kernel (recorded on the launching stream when profiling is enabled)
+  int64_t launches = 0;
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+  size_t prof_used = 0;
+  const char* dominant = "";
 };
+
+// Bracket one launch of the dominant kernel with events (no-op unless profiling).
+void prof_begin(Plan& P, cudaStream_t s);
+void prof_end(Plan& P, cudaStream_t s);
 
 // Launchers implemented in the .cu files.  All enqueue on `stream`.
 fzp_status bluestein_build_tables(Plan& P);
@@ -172,6 +186,8 @@ fzp_status column_pass(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream);
 fzp_status epilogue(Plan& P, void* d_field, int accumulate, cudaStream_t stream);
 fzp_status intensity(Plan& P, const void* d_field, void* d_I, cudaStream_t stream);
 fzp_status metrics(Plan& P, const void* d_field, cudaStream_t stream, fzp_metrics_t* out);
+fzp_status bluestein_mask(Plan& P, int64_t j0, int64_t rows, uint8_t* out, cudaStream_t stream);
+fzp_status dense_mask(Plan& P, int64_t j0, int64_t rows, uint8_t* out, cudaStream_t stream);
 
 // Row index into the C1 layout: kernel row tile t = m / 64 holds the real parts
 // of m = 64t..64t+63 in rows [0,64) and the imaginary parts in rows [64,128).

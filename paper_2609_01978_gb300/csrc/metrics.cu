@@ -214,6 +214,7 @@ fzp_status metrics(Plan& P, const void* d_field, cudaStream_t s, fzp_metrics_t* 
   k_fft_rows<<<M, 256, M * sizeof(double2), s>>>(M, logM, U, F);
   k_fft_cols<<<M, 256, M * sizeof(double2), s>>>(M, logM, F, scr);
   k_fwhm<<<2, 32, 0, s>>>(M, P.p, U, scr + S_FFT, scr);
+  P.launches += 5;
   FZP_CUDA_TRY(cudaGetLastError());
   double h[S_FFT];
   FZP_CUDA_TRY(cudaMemcpyAsync(h, scr, sizeof(h), cudaMemcpyDeviceToHost, s));

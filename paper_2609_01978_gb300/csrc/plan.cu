@@ -52,8 +52,32 @@ static void thresholds(double kappa, int64_t count, std::vector<int64_t>& S) {
   }
 }
 
+void prof_begin(Plan& P, cudaStream_t s) {
+  if (!P.profiling) return;
+  if (P.prof_used == P.prof_events.size()) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      if (a) cudaEventDestroy(a);
+      cudaGetLastError();
+      return;
+    }
+    P.prof_events.emplace_back(a, b);
+  }
+  cudaEventRecord(P.prof_events[P.prof_used].first, s);
+}
+
+void prof_end(Plan& P, cudaStream_t s) {
+  if (!P.profiling || P.prof_used >= P.prof_events.size()) return;
+  cudaEventRecord(P.prof_events[P.prof_used].second, s);
+  ++P.prof_used;
+}
+
 static void release(fzp_plan_s* P) {
   if (!P) return;
+  for (auto& e : P->prof_events) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
   void* ptrs[] = {P->d_thr, P->d_C1, P->d_C1d, P->d_Uacc, P->d_err, P->d_metrics,
                   P->bs.d_pre, P->bs.d_H, P->bs.d_Z, P->bs.d_G, P->bs.d_tab, P->dn.d_A};
   for (void* q : ptrs)
@@ -249,6 +273,42 @@ fzp_status fzp_propagate_roi(fzp_plan_t plan, int64_t row_begin, int64_t row_end
     if (st != FZP_OK) return st;
   }
   return epilogue(P, d_field, accumulate, s);
+}
+
+fzp_status fzp_aperture_mask(fzp_plan_t plan, int64_t row_begin, int64_t row_end, void* d_mask, void* stream) {
+  if (!plan || !d_mask) return set_error(FZP_E_INVALID, "NULL plan or mask");
+  Plan& P = *plan;
+  if (row_begin < 0 || row_end > P.N || row_begin > row_end)
+    return set_error(FZP_E_INVALID, "row range [%lld, %lld) outside [0, %lld]", (long long)row_begin,
+                     (long long)row_end, (long long)P.N);
+  if (row_end == row_begin) return FZP_OK;
+  uint8_t* out = reinterpret_cast<uint8_t*>(d_mask);
+  return P.form == FZP_FORM_DENSE ? dense_mask(P, row_begin, row_end - row_begin, out, (cudaStream_t)stream)
+                                  : bluestein_mask(P, row_begin, row_end - row_begin, out, (cudaStream_t)stream);
+}
+
+fzp_status fzp_profile_enable(fzp_plan_t plan, int enable) {
+  if (!plan) return set_error(FZP_E_INVALID, "NULL plan");
+  plan->profiling = enable != 0;
+  return FZP_OK;
+}
+
+fzp_status fzp_profile_read(fzp_plan_t plan, fzp_profile_t* out) {
+  if (!plan || !out) return set_error(FZP_E_INVALID, "NULL argument");
+  double total = 0;
+  for (size_t i = 0; i < plan->prof_used; ++i) {
+    FZP_CUDA_TRY(cudaEventSynchronize(plan->prof_events[i].second));
+    float ms = 0;
+    FZP_CUDA_TRY(cudaEventElapsedTime(&ms, plan->prof_events[i].first, plan->prof_events[i].second));
+    total += ms;
+  }
+  out->dominant_ms = total;
+  out->dominant_launches = (int64_t)plan->prof_used;
+  out->kernel_launches = plan->launches;
+  snprintf(out->dominant_name, sizeof(out->dominant_name), "%s", plan->dominant);
+  plan->prof_used = 0;
+  plan->launches = 0;
+  return FZP_OK;
 }
 
 fzp_status fzp_intensity(fzp_plan_t plan, const void* d_field, void* d_intensity, void* stream) {

@@ -1,0 +1,95 @@
+"""Form (b), the split-BF16 tcgen05 contraction U = K T K^T, against the CPU
+FP64 oracle through the C ABI (relative L2 of the ROI intensity <= 1e-4;
+FWHM within 0.01 %, DE within 0.01 percentage points)."""
+import numpy as np
+import pytest
+
+from gpu_util import rel_l2, run_plan
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    import paper_2609_01978_gb300 as fzp
+    return fzp, torch, oracle
+
+
+def _plan(fzp, g, prec=2):
+    return fzp.Plan(D=g.D, f=g.f, lam=g.lam, M=g.M, pitch=g.p, dx=g.dx, N=g.N, form=fzp.FORM_DENSE, precision=prec)
+
+
+def test_dense_config1(env):
+    fzp, torch, O = env
+    g = O.Geometry(D=4e-3, f=20e-3, lam=632.8e-9, M=256, p=0.2e-6)
+    Uref = O.field_czt(g)
+    mref = O.metrics(g, Uref)
+    with _plan(fzp, g) as plan:
+        U, I = run_plan(fzp, torch, plan, g.M, 0, g.N)
+        m = plan.metrics(torch.from_numpy(U).to("cuda:0"))
+    assert rel_l2(I, np.abs(Uref) ** 2) <= 1e-4
+    assert abs(m["fwhm_x"] / mref["fwhm_x"] - 1) < 1e-4
+    assert abs(m["de_lobe"] - mref["de_lobe"]) < 1e-4
+
+
+def test_dense_ragged_tiles(env):
+    """N = 9001 (last K block partial), M = 128 (two kernel tiles), row ranges
+    that cut stripes (partial 256-row tiles), accumulation over ranges."""
+    fzp, torch, O = env
+    g = O.Geometry(D=4e-3 * 9001 / 5057, f=20e-3 * 9001 / 5057, lam=632.8e-9, M=128, p=0.3e-6, N=9001)
+    with _plan(fzp, g) as plan:
+        for (j0, j1) in [(0, g.N), (4321, 4321 + 777), (g.c, g.c + 1)]:
+            _, I = run_plan(fzp, torch, plan, g.M, j0, j1)
+            assert rel_l2(I, np.abs(O.field_czt(g, j0, j1)) ** 2) <= 1e-4, (j0, j1)
+
+
+def test_dense_config2_sampled_stripes(env):
+    fzp, torch, O = env
+    lam = 632.8e-9
+    g = O.Geometry(D=0.25, f=1.25, lam=lam, M=512, p=lam * 5 / 8)
+    with _plan(fzp, g) as plan:
+        for j0 in [g.c - 512, 1000]:
+            _, I = run_plan(fzp, torch, plan, g.M, j0, j0 + 1024)
+            assert rel_l2(I, np.abs(O.field_czt(g, j0, j0 + 1024)) ** 2) <= 1e-4, j0
+
+
+def test_dense_vs_bluestein_full_config2(env):
+    """Full 0.25 m aperture: the split-BF16 dense form and the FP32 Bluestein form
+    agree, and both give the Airy FWHM and the binary-FZP efficiency."""
+    fzp, torch, O = env
+    lam = 632.8e-9
+    kw = dict(D=0.25, f=1.25, lam=lam, M=512, pitch=lam * 5 / 8)
+    with fzp.Plan(form=fzp.FORM_DENSE, precision=fzp.PREC_SPLIT_BF16, **kw) as pd, \
+            fzp.Plan(form=fzp.FORM_BLUESTEIN, precision=fzp.PREC_FP32, **kw) as pb:
+        N = pd.info["N"]
+        Ud, Id = run_plan(fzp, torch, pd, 512, 0, N)
+        Ub, Ib = run_plan(fzp, torch, pb, 512, 0, N)
+        md = pd.metrics(torch.from_numpy(Ud).to("cuda:0"))
+        mb = pb.metrics(torch.from_numpy(Ub).to("cuda:0"))
+    assert rel_l2(Id, Ib) <= 2e-4
+    assert abs(md["fwhm_x"] / mb["fwhm_x"] - 1) < 1e-4
+    assert abs(md["de_lobe"] - mb["de_lobe"]) < 1e-4
+    airy = O.airy_fwhm_factor() * lam * 5
+    assert abs(md["fwhm_x"] / airy - 1) < 1e-4
+    assert abs(md["de_lobe"] / (O.airy_encircled(O.AIRY_NULL) / np.pi ** 2) - 1) < 1e-3
+
+
+def test_dense_bf16_hi_only_is_less_accurate(env):
+    """The K_hi-only variant (one BF16 term) is measurably worse than split-BF16;
+    the test records both errors on config 1."""
+    fzp, torch, O = env
+    g = O.Geometry(D=4e-3, f=20e-3, lam=632.8e-9, M=256, p=0.2e-6)
+    Iref = np.abs(O.field_czt(g)) ** 2
+    errs = {}
+    for prec in (2, 3):
+        with _plan(fzp, g, prec) as plan:
+            _, I = run_plan(fzp, torch, plan, g.M, 0, g.N)
+        errs[prec] = rel_l2(I, Iref)
+    print("rel L2 split-BF16 %.3e  BF16 %.3e" % (errs[2], errs[3]))
+    assert errs[2] <= 1e-4 and errs[3] > errs[2]
