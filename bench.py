@@ -179,7 +179,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fzp-d0.25m", choices=sorted(WORKLOADS))
-    ap.add_argument("--form", default="bluestein", choices=["dense", "bluestein"])
+    ap.add_argument("--form", default="dense", choices=["dense", "bluestein"])
     ap.add_argument("--ref-rows", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -260,7 +260,10 @@ def main():
     peaks, peak_kind = _peaks()
     avg_ms = prof["dominant_ms"] / max(1, prof["dominant_launches"])
     if args.form == "dense":
-        flops_launch = prof.get("flops_per_launch", 0.0)
+        # algorithmic work of the contraction: 2 real rows (Re, Im) x M outputs x
+        # 2 flops x 2 split terms per aperture sample = 8 M flops per sample
+        launches = max(1, prof["dominant_launches"])
+        flops_launch = 8.0 * M * N * N * args.steps / launches
         achieved = flops_launch / (avg_ms / 1e3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
