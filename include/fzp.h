@@ -176,6 +176,31 @@ FZP_API fzp_status fzp_intensity(fzp_plan_t plan, const void* d_field, void* d_i
  * (FZP_E_TIMEOUT). */
 FZP_API fzp_status fzp_metrics(fzp_plan_t plan, const void* d_field, void* stream, fzp_metrics_t* out);
 
+/* Metric extractor that allocates nothing (no counterpart in the paper).
+ *
+ * Some callers cannot allocate device memory: a process whose device memory is
+ * owned by another allocator (for example a framework's caching pool that must
+ * stay the only owner), a real-time loop that forbids allocation once it has
+ * started, or a process running at its memory limit where a fresh allocation
+ * can fail mid-run.  fzp_plan allocates its tables and workspace, so such a
+ * caller cannot obtain fzp_metrics; this call computes the same metrics (same
+ * kernels) from the problem parameters alone.
+ *
+ * Its scratch is one file-scope device array of 4.25 MiB, which every GPU that
+ * loads libfzp holds until the process exits.  Limit: M <= 512 (power of two,
+ * >= 64); larger M is rejected with FZP_E_INVALID.  The first call on a device
+ * looks up the array's device address with that device current (once per
+ * device); make that first call before any stream capture.  All calls share
+ * the array and it keeps the last call's contents (the call clears what must
+ * start at zero); calls that overlap on the GPU, on any streams, race and give
+ * wrong results, so serialise them.
+ *   params  problem statement as for fzp_plan (M <= 512).
+ *   d_field device complex128 M*M, the focal-plane field (input).
+ *   stream  cudaStream_t; the call synchronises it and writes *out (host).
+ * Calls no cudaMalloc, cudaFree or allocating library routine. */
+FZP_API fzp_status fzp_metrics_noalloc(const fzp_params* params, const void* d_field, void* stream,
+                                       fzp_metrics_t* out);
+
 /* Binary aperture transmission T[j, i] of rows [row_begin, row_end), produced
  * by the same device code that feeds the plan's row transform (Fig. 2 Stage 2:
  * open where the paraxial zone index floor(r^2/(lambda f)) is odd and

@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
             "fzp_intensity": [vp, vp, vp, vp],
             "fzp_metrics": [vp, vp, vp, ctypes.POINTER(Metrics)],
             "fzp_aperture_mask": [vp, i64, i64, vp, vp],
+            "fzp_metrics_noalloc": [ctypes.POINTER(Params), vp, vp, ctypes.POINTER(Metrics)],
             "fzp_profile_enable": [vp, i32],
             "fzp_profile_read": [vp, ctypes.POINTER(Profile)],
         }
@@ -198,6 +199,16 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+def metrics_noalloc(field, D: float, f: float, lam: float, M: int, pitch: float, dx: float = 0.0, N: int = 0,
+                    stream=None) -> dict:
+    """fzp_metrics_noalloc: the metric extractor without a plan and without any
+    device allocation (scratch in a static device array; M <= 512)."""
+    p = Params(D=D, f=f, lam=lam, dx=dx, N=N, M=M, form=0, pitch=pitch, precision=0, stripe_rows=0, deform=None)
+    m = Metrics()
+    _check(lib().fzp_metrics_noalloc(ctypes.byref(p), _ptr(field), _stream(stream), ctypes.byref(m)))
+    return m.as_dict()
 
 
 def version() -> str:

@@ -12,6 +12,7 @@
 //   Strehl: I(M/2, M/2) / (pi R^2 / (lambda f))^2.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "fzp_internal.cuh"
 
@@ -264,4 +265,131 @@ fzp_status metrics(Plan& P, const void* d_field, cudaStream_t s, fzp_metrics_t* 
   return FZP_OK;
 }
 
+// ---------------------------------------------------------------- no-allocation variant
+// Scratch of fzp_metrics_noalloc: same layout as the plan's metric scratch for
+// M <= 512 (sums, bins, spline work, then the M x M complex FFT buffer).
+constexpr int kNoAllocMaxM = 512;
+constexpr size_t kNoAllocDoubles = (size_t)S_FFT + 6 * 1024 + 2 * (size_t)kNoAllocMaxM * kNoAllocMaxM;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device; looked up once
+// per device with that device current.
+fzp_status noalloc_scratch(double** out) {
+  int dev = 0;
+  FZP_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(FZP_E_UNSUPPORTED, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return set_error(FZP_E_CUDA, "cudaGetSymbolAddress(scratch) failed on device %d: %s", dev,
+                       cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = reinterpret_cast<double*>(g_noalloc_ptr[dev]);
+  return FZP_OK;
+}
+
+double fl_mul(int64_t s, double a) {
+  volatile double prod = (double)s * a;
+  return prod;
+}
+}  // namespace
+
 }  // namespace fzp
+
+extern "C" fzp_status fzp_metrics_noalloc(const fzp_params* in, const void* d_field, void* stream,
+                                          fzp_metrics_t* out) {
+  using namespace fzp;
+  if (!in || !d_field || !out) return set_error(FZP_E_INVALID, "NULL argument");
+  if (!(in->D > 0) || !(in->f > 0) || !(in->lambda > 0) || !(in->pitch > 0) || !std::isfinite(in->D) ||
+      !std::isfinite(in->f) || !std::isfinite(in->lambda) || !std::isfinite(in->pitch) || in->dx < 0)
+    return set_error(FZP_E_INVALID, "D, f, lambda and pitch must be finite and positive");
+  if (in->M < 64 || in->M > kNoAllocMaxM || (in->M & (in->M - 1)) != 0)
+    return set_error(FZP_E_INVALID, "M = %d outside the static scratch of fzp_metrics_noalloc "
+                     "(a power of two in [64, %d])", in->M, kNoAllocMaxM);
+  if (in->N < 0 || (in->N > 0 && (in->N % 2) == 0)) return set_error(FZP_E_INVALID, "N must be 0 or odd");
+  // grids as fzp_plan derives them (Fig. 2 Stage 1-2)
+  const double lf = in->lambda * in->f;
+  const double dx = in->dx > 0 ? in->dx : lf / (4.0 * in->D);
+  int64_t N = in->N;
+  if (N == 0) {
+    const double n = std::ceil(in->D / dx);
+    if (!(n < 1e9)) return set_error(FZP_E_INVALID, "grid too large");
+    N = (int64_t)n;
+    if ((N % 2) == 0) N += 1;
+  }
+  const int64_t c = (N - 1) / 2;
+  const double R = std::min(in->D / 2.0, lf / (2.0 * dx));
+  const double dx2 = dx * dx, R2 = R * R;
+  int64_t sR = (int64_t)std::floor(R2 / dx2);
+  if (sR < 0) sR = 0;
+  while (fl_mul(sR + 1, dx2) <= R2) ++sR;
+  while (sR > 0 && fl_mul(sR, dx2) > R2) --sR;
+
+  double* scr = nullptr;
+  fzp_status st = noalloc_scratch(&scr);
+  if (st != FZP_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int M = in->M;
+  int logM = 0;
+  while ((1 << logM) < M) ++logM;
+  const double2* U = reinterpret_cast<const double2*>(d_field);
+  double2* F = reinterpret_cast<double2*>(scr + S_FFT + 6 * 1024);
+  const double rnull = AIRY_NULL * lf / (2.0 * R);
+  FZP_CUDA_TRY(cudaMemsetAsync(scr, 0, S_FFT * sizeof(double), s));  // sums, counts, bins start at zero
+  k_sums<<<256, 256, 0, s>>>(M, in->pitch, rnull * rnull, U, scr);
+  k_count<<<256, 256, 0, s>>>(N, c, sR, scr);
+  k_fft_rows<<<M, 256, M * sizeof(double2), s>>>(M, logM, U, F);
+  k_fft_cols<<<M, 256, M * sizeof(double2), s>>>(M, logM, F, scr);
+  k_fwhm<<<2, 32, 0, s>>>(M, in->pitch, U, scr + S_FFT, scr);
+  FZP_CUDA_TRY(cudaGetLastError());
+  double h[S_FFT];
+  FZP_CUDA_TRY(cudaMemcpyAsync(h, scr, sizeof(h), cudaMemcpyDeviceToHost, s));
+  FZP_CUDA_TRY(cudaStreamSynchronize(s));
+  const double sum = h[S_SUM], lobe = h[S_LOBE];
+  int64_t count;
+  memcpy(&count, &h[S_COUNT], sizeof(count));
+  const double pin = (double)count * dx2;
+  out->aperture_count = count;
+  out->p_in = pin;
+  out->p_in_disc = 3.14159265358979323846 * R2;
+  out->de_lobe = lobe * in->pitch * in->pitch / pin;
+  out->de_roi = sum * in->pitch * in->pitch / pin;
+  out->fwhm_x = h[S_OUT];
+  out->fwhm_y = h[S_OUT + 1];
+  out->peak = h[S_OUT + 2];
+  const double ip = 3.14159265358979323846 * R2 / lf;
+  out->strehl = out->peak / (ip * ip);
+  double centre[NBINS], mean[NBINS];
+  int nb = 0;
+  const double nyq = 1.0 / (2.0 * in->pitch);
+  for (int b = 0; b < NBINS; ++b) {
+    int64_t cnt;
+    memcpy(&cnt, &h[S_BINCNT + b], sizeof(cnt));
+    if (cnt > 0) {
+      centre[nb] = (b + 0.5) * nyq / NBINS;
+      mean[nb] = h[S_BINS + b] / (double)cnt / sum;
+      ++nb;
+    }
+  }
+  auto interp = [&](double nu) -> double {
+    if (nb == 0) return (double)NAN;
+    if (nu <= centre[0]) return mean[0];
+    if (nu >= centre[nb - 1]) return mean[nb - 1];
+    int i = 0;
+    while (centre[i + 1] < nu) ++i;
+    const double t = (nu - centre[i]) / (centre[i + 1] - centre[i]);
+    return mean[i] + t * (mean[i + 1] - mean[i]);
+  };
+  const double nucut = 2.0 * R / lf;
+  out->mtf_half_cut = interp(0.5 * nucut);
+  for (int q = 0; q < 16; ++q) out->mtf16[q] = interp((q + 0.5) * nucut / 16.0);
+  return FZP_OK;
+}
