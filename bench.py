@@ -36,6 +36,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOADS = {
+    "fzp-d0.05m": dict(D=0.05, lam=632.8e-9, fnum=5.0, M=512),  # small case for profiler captures
     "fzp-d0.25m": dict(D=0.25, lam=632.8e-9, fnum=5.0, M=512),
     "fzp-d1m": dict(D=1.0, lam=632.8e-9, fnum=5.0, M=512),
 }

@@ -10,19 +10,23 @@
 // K_hi T^T + K_lo T^T is accumulated into the same accumulator, so the product
 // carries the ~16 significant bits of the split kernel.
 //
-// GB300 mapping (tcgen05, one CTA per SM, persistent):
-//   tile     : 128 kernel rows (64 m values, Re and Im) x 256 aperture rows,
-//              K step 64 per stage (one 128-byte swizzle atom of BF16)
-//   warp 4   : copies the A stage (hi and lo, pre-swizzled in HBM) with one
-//              cp.async.bulk per stage
-//   warps 6-13: generate the binary mask of the 256 aperture rows for the
-//              stage's 64 columns (exact zone rule, threshold walk), write it
-//              in the 128-byte-swizzled K-major layout
-//   warp 5   : allocates tensor memory and issues tcgen05.mma (M128 N256 K16)
-//   warps 0-3: epilogue; every `promote` K blocks the accumulator (double
-//              buffered in TMEM) is read with tcgen05.ld and added in FP32 to
-//              the C1 tile in global memory (bounds the growth of the tensor
-//              core's FP32 accumulation error).
+// GB300 mapping (tcgen05, one CTA per SM, persistent over items):
+//   item     : one stripe of 256 aperture rows x one pair of kernel tiles
+//              (2 x 128 kernel rows = 128 values of m, Re and Im); the mask
+//              tile generated for a stage feeds both tiles (hi and lo each)
+//   stage    : K step of 32 columns, 64-byte-swizzled K-major operands
+//              (A 32 KiB: [t0 hi][t1 hi][t0 lo][t1 lo]; B 16 KiB), 4 stages
+//   warp 8   : copies the A stage, pre-swizzled in HBM, with one cp.async.bulk
+//   warps 10-17: mask generators, one aperture row each; a walker carries the
+//              zone state along the row and yields the columns where the binary
+//              transmission toggles (exact integer thresholds)
+//   warp 9   : allocates 512 TMEM columns and issues tcgen05.mma (M128 N256 K16)
+//              into two FP32 accumulators (one per tile)
+//   warps 0-7: epilogue; every `promote` stages both accumulators are read with
+//              tcgen05.ld and added in FP32 to the C1 tiles in global memory.
+//              The tensor core's FP32 accumulation loses precision in proportion
+//              to the chunk length (measured: 8e-4 relative error of I over a
+//              0.25 m aperture without promotion, 8e-6 with 4096-sample chunks).
 // Every mbarrier wait is bounded in time; on expiry the kernel records an error
 // code, drains what it issued, frees tensor memory and returns.
 #include <cuda_bf16.h>
@@ -35,27 +39,32 @@
 namespace fzp {
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 3;
-constexpr int A_HALF = BM * BK * 2;  // 16 KiB: one of hi / lo
-constexpr int A_BYTES = 2 * A_HALF;  // 32 KiB
-constexpr int B_BYTES = BN * BK * 2; // 32 KiB
-constexpr int NUM_THREADS = 14 * 32;
-constexpr int GEN_WARP0 = 6;
-constexpr int TMEM_COLS = 512;
+constexpr int BM = 128;               // kernel rows per MMA (tcgen05 M)
+constexpr int TILES = 2;               // kernel tiles per item: 256 kernel rows share one mask tile
+constexpr int BN = 256;                // aperture rows per item (tcgen05 N)
+constexpr int BK = 32;                 // K per stage: one 64-byte swizzle row of BF16
+constexpr int STAGES = 4;
+constexpr int SUB = BM * BK * 2;       // 8 KiB: one (tile, hi|lo) operand image
+constexpr int A_BYTES = TILES * 2 * SUB;  // 32 KiB per stage: [t0 hi][t1 hi][t0 lo][t1 lo]
+constexpr int B_BYTES = BN * BK * 2;      // 16 KiB per stage
+constexpr int EPI_WARPS = 8;           // warps 0-7: epilogue (tile = warp / 4)
+constexpr int LOAD_WARP = 8, MMA_WARP = 9, GEN_WARP0 = 10;
+constexpr int NUM_THREADS = 18 * 32;
+constexpr int TMEM_COLS = 512;         // two 128 x 256 FP32 accumulators
 constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s per wait
 constexpr int ERR_TIMEOUT_BASE = 100;
 
 struct DenseArgs {
   MaskGeom mg;
   int64_t N;
-  int64_t kblocks;
+  int64_t kblocks;          // ceil(N / BK)
   int64_t j_begin, j_end;   // aperture rows of this launch [j_begin, j_end)
   int64_t n_stripes;        // ceil((j_end - j_begin) / BN)
-  int ntiles;               // 2M / 128
-  int promote;              // K blocks per accumulation chunk
+  int npairs;               // kernel tile pairs (items per stripe)
+  int promote;              // stages per accumulation chunk
   int hi_only;              // 1: BF16 kernel (hi) only
-  const uint8_t* A;         // pre-swizzled kernel tiles
-  float* C1;                // [2M][c1_stride], column = j - c1_j0
+  const uint8_t* A;         // pre-swizzled kernel tiles, [pair][kb][t0hi t1hi t0lo t1lo]
+  float* C1;                // [rows][c1_stride], column = j - c1_j0
   int64_t c1_stride, c1_j0;
   int* err;
 };
@@ -125,10 +134,11 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle (rows of 64 B,
+// 8-row groups 512 B apart), version 1.
 __device__ __forceinline__ uint64_t sdesc(const void* p) {
   const uint64_t a = smem_u32(p);
-  return ((a >> 4) & 0x3FFFull) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+  return ((a >> 4) & 0x3FFFull) | (1ull << 16) | ((uint64_t)(512 >> 4) << 32) | (1ull << 46) | (4ull << 61);
 }
 
 // Instruction descriptor: kind::f16, D = F32, A = B = BF16, K-major, N = 256, M = 128.
@@ -160,20 +170,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
-
-// ---------------------------------------------------------------- mask rows
-__device__ __forceinline__ uint64_t range_bits(int a, int b) {  // bits a..b inclusive, 0 <= a <= b <= 63
-  return (~0ull >> (63 - b)) & (~0ull << a);
-}
-
-__device__ __forceinline__ int64_t ceil_sqrt(int64_t t) {  // smallest a >= 0 with a^2 >= t
-  if (t <= 0) return 0;
-  int64_t a = (int64_t)sqrtf((float)t);
-  while (a * a < t) ++a;
-  while (a > 0 && (a - 1) * (a - 1) >= t) --a;
-  return a;
-}
-
+// ---------------------------------------------------------------- mask walker
 __device__ __forceinline__ int64_t isqrt_floor(int64_t t) {  // largest a with a^2 <= t (t >= 0)
   int64_t a = (int64_t)sqrtf((float)t);
   while (a * a > t) --a;
@@ -181,54 +178,111 @@ __device__ __forceinline__ int64_t isqrt_floor(int64_t t) {  // largest a with a
   return a;
 }
 
-// Open bits of row (dj2 = dj^2) for columns [ilo, ihi] inside the disc, relative
-// to i0.  The zone index is monotone in |i - c|; its parity flips at the
-// columns where dj^2 + (i - c)^2 crosses a threshold S_m.
-__device__ uint64_t row_bits(int64_t i0, int64_t ilo, int64_t ihi, int64_t c, int64_t dj2, const MaskGeom& g) {
-  uint64_t bits = 0;
-  const int64_t r0 = ilo > c ? ilo : c;
-  if (r0 <= ihi) {
-    const int64_t d0 = r0 - c, d1 = ihi - c;
-    const int64_t z0 = zone_of(dj2 + d0 * d0, g), z1 = zone_of(dj2 + d1 * d1, g);
-    uint64_t b = (z0 & 1) ? range_bits((int)(r0 - i0), (int)(ihi - i0)) : 0ull;
-    for (int64_t m = z0 + 1; m <= z1; ++m) {
-      const int64_t p = c + ceil_sqrt(__ldg(g.thr + (m - 1)) - dj2);
-      b ^= range_bits((int)(p - i0), (int)(ihi - i0));
+// Smallest a >= 0 with a^2 >= t, for 0 < t < 2^44: FP32 square root of a
+// 24-bit-accurate argument, then exact integer correction.
+__device__ __forceinline__ uint32_t ceil_sqrt44(int64_t t) {
+  const float tf = t < (1ll << 24) ? (float)(uint32_t)t : (float)(uint32_t)(t >> 12) * 4096.0f;
+  uint32_t a = (uint32_t)__fsqrt_rn(tf);
+  while ((int64_t)((uint64_t)a * a) < t) ++a;
+  while (a > 0 && (int64_t)((uint64_t)(a - 1) * (a - 1)) >= t) --a;
+  return a;
+}
+
+// Walks one aperture row from column 0 upwards and yields the columns where
+// the binary transmission toggles.  Along the row the zone index is a function
+// of d = |i - c|, non-decreasing in d, and steps at d = a_m = ceil(sqrt(S_m - dj^2));
+// the open state toggles at every step and at both ends of the disc chord.
+// Toggle columns in increasing order:
+//   c - bmax               (if the edge zone z_e is odd: the row enters open)
+//   c - a_m + 1, m = z_e .. z_c + 1   (zone drops below m, left half)
+//   c + a_m,     m = z_c + 1 .. z_e   (zone reaches m, right half)
+//   c + bmax + 1           (if z_e is odd: the row leaves the disc)
+struct Walker {
+  int64_t next;  // next toggle column (INT64_MAX: none)
+  int64_t m;     // threshold index of the pending boundary
+  int64_t dj2, c, bmax, zc, ze;
+  int phase;     // 0 start, 1 left, 2 right, 3 end, 4 done
+};
+
+__device__ __forceinline__ void walker_advance(Walker& w, const int64_t* __restrict__ thr) {
+  while (true) {
+    switch (w.phase) {
+      case 0:
+        w.phase = 1;
+        w.m = w.ze;
+        if (w.ze & 1) { w.next = w.c - w.bmax; return; }
+        break;
+      case 1:
+        if (w.m > w.zc) {
+          w.next = w.c - (int64_t)ceil_sqrt44(__ldg(thr + (w.m - 1)) - w.dj2) + 1;
+          --w.m;
+          return;
+        }
+        w.phase = 2;
+        w.m = w.zc + 1;
+        break;
+      case 2:
+        if (w.m <= w.ze) {
+          w.next = w.c + (int64_t)ceil_sqrt44(__ldg(thr + (w.m - 1)) - w.dj2);
+          ++w.m;
+          return;
+        }
+        w.phase = 3;
+        break;
+      case 3:
+        w.phase = 4;
+        if (w.ze & 1) { w.next = w.c + w.bmax + 1; return; }
+        break;
+      default:
+        w.next = INT64_MAX;
+        return;
     }
-    bits |= b;
   }
-  const int64_t l1 = ihi < c - 1 ? ihi : c - 1;
-  if (ilo <= l1) {
-    const int64_t dA = c - ilo, dB = c - l1;
-    const int64_t zA = zone_of(dj2 + dA * dA, g), zB = zone_of(dj2 + dB * dB, g);
-    uint64_t b = (zA & 1) ? range_bits((int)(ilo - i0), (int)(l1 - i0)) : 0ull;
-    for (int64_t m = zA; m > zB; --m) {
-      const int64_t p = c - ceil_sqrt(__ldg(g.thr + (m - 1)) - dj2) + 1;
-      b ^= range_bits((int)(p - i0), (int)(l1 - i0));
-    }
-    bits |= b;
+}
+
+__device__ __forceinline__ void walker_init(Walker& w, int64_t j, int64_t j_end, const MaskGeom& g) {
+  w.c = g.c;
+  w.phase = 4;
+  w.next = INT64_MAX;
+  const int64_t dj = j - g.c;
+  if (j >= j_end || dj * dj > g.sR) return;
+  w.dj2 = dj * dj;
+  w.bmax = isqrt_floor(g.sR - w.dj2);
+  w.zc = zone_of(w.dj2, g);
+  w.ze = zone_of(w.dj2 + w.bmax * w.bmax, g);
+  w.phase = 0;
+  walker_advance(w, g.thr);
+}
+
+// Open bits of columns [i0, i0 + 32) given the open state at i0; updates the state.
+__device__ __forceinline__ uint32_t walker_bits(Walker& w, int64_t i0, uint32_t& state, const int64_t* thr) {
+  uint32_t bits = state ? 0xFFFFFFFFu : 0u;
+  while (w.next < i0 + 32) {
+    bits ^= 0xFFFFFFFFu << (uint32_t)(w.next - i0);
+    state ^= 1u;
+    walker_advance(w, thr);
   }
   return bits;
 }
 
-__device__ __forceinline__ uint32_t pack2(uint32_t two_bits) {  // two samples -> two BF16 (1.0 or 0.0)
-  return (two_bits & 1u) * 0x3F80u + ((two_bits >> 1) & 1u) * 0x3F800000u;
+// Two samples -> two BF16 values (1.0 = 0x3F80 or 0.0).
+__device__ __forceinline__ uint32_t pack2(uint32_t x) {
+  return (x & 1u) * 0x3F80u + ((x >> 1) & 1u) * 0x3F800000u;
 }
 
 // ---------------------------------------------------------------- kernel
 __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  // 1024-byte alignment of the operand tiles (swizzle atoms)
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* sA = base;                       // STAGES x 32 KiB
-  uint8_t* sB = base + STAGES * A_BYTES;    // STAGES x 32 KiB
+  uint8_t* sA = base;                     // STAGES x 32 KiB
+  uint8_t* sB = base + STAGES * A_BYTES;  // STAGES x 16 KiB
   uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * B_BYTES);
   uint64_t* fullA = bars;
   uint64_t* fullB = bars + STAGES;
   uint64_t* empty = bars + 2 * STAGES;
   uint64_t* accFull = bars + 3 * STAGES;
-  uint64_t* accEmpty = accFull + 2;
-  uint64_t* drain = accEmpty + 2;
+  uint64_t* accEmpty = accFull + 1;
+  uint64_t* drain = accEmpty + 1;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(drain + 1);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 2);
 
@@ -239,15 +293,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
       mbar_init(&fullB[s], 8);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&accFull[b], 1);
-      mbar_init(&accEmpty[b], 4);
-    }
+    mbar_init(accFull, 1);
+    mbar_init(accEmpty, EPI_WARPS);
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 5) {
+  if (warp == MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(TMEM_COLS)
                  : "memory");
@@ -258,32 +310,32 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  const int64_t n_items = a.n_stripes * a.ntiles;
+  const int64_t n_items = a.n_stripes * a.npairs;
   const int64_t nkb = a.kblocks;
   const int64_t nchunk = (nkb + a.promote - 1) / a.promote;
-  const uint32_t a_bytes = a.hi_only ? A_HALF : A_BYTES;
+  const uint32_t a_bytes = a.hi_only ? A_BYTES / 2 : A_BYTES;
 
-  if (warp == 4) {
-    // ---------------- A loader
+  if (warp == LOAD_WARP) {
+    // ---------------- A loader: one bulk copy of 32 KiB (16 KiB hi only) per stage
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      int last[STAGES];  // parity of the last copy issued into each stage, -1: none
+      int last[STAGES];
 #pragma unroll
       for (int s2 = 0; s2 < STAGES; ++s2) last[s2] = -1;
       for (int64_t it = blockIdx.x; it < n_items && !*abort_flag; it += gridDim.x) {
-        const int t = (int)(it / a.n_stripes);
-        const uint8_t* At = a.A + (int64_t)t * nkb * A_BYTES;
+        const int64_t pr = it / a.n_stripes;
+        const uint8_t* Ap = a.A + pr * nkb * A_BYTES;
         for (int64_t kb = 0; kb < nkb; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 1)) break;
           mbar_arrive_tx(&fullA[stage], a_bytes);
-          bulk_g2s(sA + stage * A_BYTES, At + kb * A_BYTES, a_bytes, &fullA[stage]);
+          bulk_g2s(sA + stage * A_BYTES, Ap + kb * A_BYTES, a_bytes, &fullA[stage]);
           last[stage] = (int)phase;
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
         }
       }
       if (*abort_flag) {
-        // the copies already issued must land before shared memory is released
+        // copies already issued must land before shared memory is released
 #pragma unroll
         for (int s2 = 0; s2 < STAGES; ++s2) {
           if (last[s2] < 0) continue;
@@ -293,19 +345,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
         }
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == MMA_WARP) {
     // ---------------- MMA issuer
     if (lane == 0) {
       int stage = 0;
-      uint32_t phase = 0;
-      int buf = 0;
-      uint32_t accph = 0;
+      uint32_t phase = 0, accph = 0;
       bool ok = true;
       for (int64_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
         for (int64_t ch = 0; ch < nchunk && ok; ++ch) {
-          if (!mbar_wait(&accEmpty[buf], accph ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 2)) { ok = false; break; }
+          // the epilogue has drained both accumulators of the previous chunk
+          if (!mbar_wait(accEmpty, accph ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 2)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t dt = tmem + (uint32_t)(buf * BN);
           const int64_t kb0 = ch * a.promote, kb1 = kb0 + a.promote < nkb ? kb0 + a.promote : nkb;
           for (int64_t kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait(&fullA[stage], phase, abort_flag, a.err, ERR_TIMEOUT_BASE + 3) ||
@@ -317,21 +367,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
             const uint64_t bdesc = sdesc(sB + stage * B_BYTES);
             const uint64_t adesc = sdesc(sA + stage * A_BYTES);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              if (h == 1 && a.hi_only) break;
+            for (int ks = 0; ks < BK / 16; ++ks) {
 #pragma unroll
-              for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint64_t ad = adesc + (uint64_t)((h * A_HALF + kk * 32) >> 4);
-                const uint64_t bd = bdesc + (uint64_t)((kk * 32) >> 4);
-                mma_bf16(dt, ad, bd, (kb > kb0 || h > 0 || kk > 0) ? 1u : 0u);
+              for (int q = 0; q < TILES; ++q) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  if (h == 1 && a.hi_only) continue;
+                  const uint64_t ad = adesc + (uint64_t)(((h * TILES + q) * SUB + ks * 32) >> 4);
+                  const uint64_t bd = bdesc + (uint64_t)((ks * 32) >> 4);
+                  mma_bf16(tmem + (uint32_t)(q * BN), ad, bd, (kb > kb0 || ks > 0 || h > 0) ? 1u : 0u);
+                }
               }
             }
             mma_commit(&empty[stage]);
             if (++stage == STAGES) { stage = 0; phase ^= 1; }
           }
           if (!ok) break;
-          mma_commit(&accFull[buf]);
-          if (++buf == 2) { buf = 0; accph ^= 1; }
+          mma_commit(accFull);
+          accph ^= 1;
         }
       }
       // all issued MMAs complete before tensor memory is released
@@ -341,35 +394,27 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
       }
     }
   } else if (warp >= GEN_WARP0) {
-    // ---------------- mask generators: one thread per aperture row of the tile
+    // ---------------- mask generators: thread g owns aperture row j_tile + g
     const int g = threadIdx.x - GEN_WARP0 * 32;  // 0..255
     int stage = 0;
     uint32_t phase = 0;
-    const int64_t c = a.mg.c;
-    uint8_t* rowbase0 = sB + (g >> 3) * 1024 + (g & 7) * 128;
-    const int sw = g & 7;
+    // 64-byte swizzle, K-major: row g at (g/8)*512 + (g%8)*64, 16-byte chunk q at q ^ ((g%8)/2)
+    uint8_t* rowbase0 = sB + (g >> 3) * 512 + (g & 7) * 64;
+    const int sw = (g & 7) >> 1;
     for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
       if (__shfl_sync(0xffffffffu, *abort_flag, 0)) break;
       const int64_t s = it % a.n_stripes;
-      const int64_t j = a.j_begin + s * BN + g;
-      const int64_t dj = j - c;
-      int64_t bmax = -1;
-      if (j < a.j_end && dj * dj <= a.mg.sR) bmax = isqrt_floor(a.mg.sR - dj * dj);
-      const int64_t dj2 = dj * dj;
+      Walker w;
+      walker_init(w, a.j_begin + s * BN + g, a.j_end, a.mg);
+      uint32_t state = 0;
+      bool ok = true;
       for (int64_t kb = 0; kb < nkb; ++kb) {
-        if (!warp_wait(&empty[stage], phase ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 5)) break;
-        const int64_t i0 = kb * BK;
-        uint64_t bits = 0;
-        if (bmax >= 0) {
-          int64_t ilo = c - bmax > i0 ? c - bmax : i0;
-          int64_t ihi = c + bmax < i0 + BK - 1 ? c + bmax : i0 + BK - 1;
-          if (ihi > a.N - 1) ihi = a.N - 1;
-          if (ilo <= ihi) bits = row_bits(i0, ilo, ihi, c, dj2, a.mg);
-        }
+        if (!warp_wait(&empty[stage], phase ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 5)) { ok = false; break; }
+        const uint32_t bits = walker_bits(w, kb * BK, state, a.mg.thr);
         uint8_t* rowp = rowbase0 + stage * B_BYTES;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const uint32_t byte = (uint32_t)(bits >> (8 * q)) & 0xFFu;
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t byte = (bits >> (8 * q)) & 0xFFu;
           uint4 v;
           v.x = pack2(byte);
           v.y = pack2(byte >> 2);
@@ -382,21 +427,22 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
         if (lane == 0) mbar_arrive(&fullB[stage]);
         if (++stage == STAGES) { stage = 0; phase ^= 1; }
       }
+      if (!ok) break;
     }
   } else {
-    // ---------------- epilogue: warps 0-3 own TMEM lanes 32w..32w+31
-    const int r = warp * 32 + lane;  // kernel row within the tile
-    int buf = 0;
+    // ---------------- epilogue: warp w drains tile w/4, TMEM lanes 32(w%4)..+31
+    const int q = warp >> 2;
+    const int r = (warp & 3) * 32 + lane;  // kernel row within the tile
     uint32_t accph = 0;
     bool ok = true;
     for (int64_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
-      const int t = (int)(it / a.n_stripes);
+      const int64_t pr = it / a.n_stripes;
       const int64_t s = it % a.n_stripes;
-      float* crow = a.C1 + (int64_t)(t * BM + r) * a.c1_stride + (a.j_begin + s * BN - a.c1_j0);
+      float* crow = a.C1 + ((pr * TILES + q) * BM + r) * a.c1_stride + (a.j_begin + s * BN - a.c1_j0);
       for (int64_t ch = 0; ch < nchunk; ++ch) {
-        if (!warp_wait(&accFull[buf], accph, abort_flag, a.err, ERR_TIMEOUT_BASE + 6)) { ok = false; break; }
+        if (!warp_wait(accFull, accph, abort_flag, a.err, ERR_TIMEOUT_BASE + 6)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * BN);
+        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(q * BN);
 #pragma unroll 1
         for (int col = 0; col < BN; col += 32) {
           float v[32];
@@ -404,78 +450,91 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
           float4* dst = reinterpret_cast<float4*>(crow + col);
           if (ch == 0) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            for (int k = 0; k < 8; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
           } else {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              float4 o = dst[q];
-              o.x += v[4 * q]; o.y += v[4 * q + 1]; o.z += v[4 * q + 2]; o.w += v[4 * q + 3];
-              dst[q] = o;
+            for (int k = 0; k < 8; ++k) {
+              float4 o = dst[k];
+              o.x += v[4 * k]; o.y += v[4 * k + 1]; o.z += v[4 * k + 2]; o.w += v[4 * k + 3];
+              dst[k] = o;
             }
           }
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&accEmpty[buf]);
-        if (++buf == 2) { buf = 0; accph ^= 1; }
+        if (lane == 0) mbar_arrive(accEmpty);
+        accph ^= 1;
       }
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 5) {
+  if (warp == MMA_WARP) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
 }
 
 // ---------------------------------------------------------------- kernel table
-// A image of tile t, K block kb, part h (0 hi, 1 lo): 128 rows x 64 columns,
-// K-major, 128-byte swizzle: element (r, k) at byte
-//   (r/8)*1024 + (r%8)*128 + ((k/8) ^ (r%8))*16 + (k%8)*2.
-__global__ void k_build_A(int M, int64_t N, int64_t kblocks, int64_t c, double kappa, double delta, uint8_t* A) {
-  const int64_t total = (int64_t)(2 * M) * kblocks * BK;  // (row, column) pairs
+// Block (pair p, K block kb) = 32 KiB: [tile 2p hi][tile 2p+1 hi][tile 2p lo][tile 2p+1 lo],
+// each 128 rows x 32 BF16, K-major, 64-byte swizzle: element (r, k) at byte
+//   (r/8)*512 + (r%8)*64 + ((k/8) ^ ((r%8)/2))*16 + (k%8)*2.
+// Tile t holds Re K for m = 64t + r (r < 64) and Im K for m = 64t + r - 64 (r >= 64);
+// tiles with 64t >= M are zero (padding to an even count).
+__global__ void k_build_A(int M, int64_t N, int64_t kblocks, int npairs, int64_t c, double kappa, double delta,
+                          uint8_t* A) {
+  const int64_t K = kblocks * BK;
+  const int64_t total = (int64_t)npairs * TILES * BM * (K / 8);  // one thread per 8 consecutive k
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
-    const int64_t i = e % (kblocks * BK);
-    const int rg = (int)(e / (kblocks * BK));  // global kernel row 0..2M-1
-    const int t = rg / BM, r = rg % BM;
+    const int64_t k8 = e % (K / 8);
+    const int64_t rg = e / (K / 8);  // kernel row over all tiles
+    const int t = (int)(rg / BM), r = (int)(rg % BM);
     const int m = t * 64 + (r & 63);
     const bool im = r >= 64;
-    float v = 0.f;
-    if (i < N) {
-      const double di = (double)(i - c);
-      const double th = di * di * (0.5 * kappa) - (double)(m - M / 2) * di * delta;
-      const float2 k = cis_turns_f(th);
-      v = im ? k.y : k.x;
+    const int p = t / TILES, q = t % TILES;
+    const int64_t i0 = k8 * 8;
+    const int64_t kb = i0 / BK;
+    const int k = (int)(i0 % BK);
+    uint32_t hw[4], lw[4];
+#pragma unroll
+    for (int u = 0; u < 8; u += 2) {
+      float v2[2];
+#pragma unroll
+      for (int z = 0; z < 2; ++z) {
+        const int64_t i = i0 + u + z;
+        float v = 0.f;
+        if (i < N && m < M) {
+          const double di = (double)(i - c);
+          const double th = di * di * (0.5 * kappa) - (double)(m - M / 2) * di * delta;
+          const float2 kk = cis_turns_f(th);
+          v = im ? kk.y : kk.x;
+        }
+        v2[z] = v;
+      }
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(v2[0]), h1 = __float2bfloat16_rn(v2[1]);
+      const __nv_bfloat16 l0 = __float2bfloat16_rn(v2[0] - __bfloat162float(h0));
+      const __nv_bfloat16 l1 = __float2bfloat16_rn(v2[1] - __bfloat162float(h1));
+      hw[u / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+      lw[u / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
     }
-    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-    const int64_t kb = i / BK;
-    const int k = (int)(i % BK);
-    const int64_t blk = ((int64_t)t * kblocks + kb) * A_BYTES;
-    const int off = (r >> 3) * 1024 + (r & 7) * 128 + (((k >> 3) ^ (r & 7)) << 4) + (k & 7) * 2;
-    *reinterpret_cast<__nv_bfloat16*>(A + blk + off) = hi;
-    *reinterpret_cast<__nv_bfloat16*>(A + blk + A_HALF + off) = lo;
+    const int64_t blk = ((int64_t)p * kblocks + kb) * A_BYTES;
+    const int off = (r >> 3) * 512 + (r & 7) * 64 + (((k >> 3) ^ ((r & 7) >> 1)) << 4);
+    *reinterpret_cast<uint4*>(A + blk + (0 * TILES + q) * SUB + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4*>(A + blk + (1 * TILES + q) * SUB + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
   }
 }
 
-// The generator of k_dense, one (row, 64-column block) per thread, to bytes.
-__global__ void k_mask_rows(MaskGeom mg, int64_t N, int64_t j0, int64_t rows, int64_t kblocks, uint8_t* out) {
-  const int64_t total = rows * kblocks;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = t / kblocks, kb = t % kblocks;
-    const int64_t j = j0 + r, c = mg.c, dj = j - c;
-    const int64_t i0 = kb * BK;
-    uint64_t bits = 0;
-    if (dj * dj <= mg.sR) {
-      const int64_t bmax = isqrt_floor(mg.sR - dj * dj);
-      int64_t ilo = c - bmax > i0 ? c - bmax : i0;
-      int64_t ihi = c + bmax < i0 + BK - 1 ? c + bmax : i0 + BK - 1;
-      if (ihi > N - 1) ihi = N - 1;
-      if (ilo <= ihi) bits = row_bits(i0, ilo, ihi, c, dj * dj, mg);
+// The generator of k_dense (walker), one row per thread, to bytes.
+__global__ void k_mask_rows(MaskGeom mg, int64_t N, int64_t j0, int64_t rows, uint8_t* out) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+    Walker w;
+    walker_init(w, j0 + r, INT64_MAX, mg);
+    uint32_t state = 0;
+    for (int64_t i0 = 0; i0 < N; i0 += 32) {
+      const uint32_t bits = walker_bits(w, i0, state, mg.thr);
+      for (int k = 0; k < 32 && i0 + k < N; ++k) out[r * N + i0 + k] = (uint8_t)((bits >> k) & 1u);
     }
-    for (int k = 0; k < BK && i0 + k < N; ++k) out[r * N + i0 + k] = (uint8_t)((bits >> k) & 1);
   }
 }
 
@@ -487,22 +546,24 @@ fzp_status dense_build_tables(Plan& P) {
   Dense& d = P.dn;
   d.kblocks = (P.N + BK - 1) / BK;
   d.ntiles = 2 * P.M / BM;
-  d.promote_kblocks = 16;
+  const int npairs = (d.ntiles + TILES - 1) / TILES;
+  d.promote_kblocks = 128;  // 4096 samples per TMEM accumulation chunk
   if (const char* e = getenv("FZP_DENSE_PROMOTE")) d.promote_kblocks = std::max(1, atoi(e));
   int dev = 0;
   FZP_CUDA_TRY(cudaGetDevice(&dev));
   FZP_CUDA_TRY(cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev));
-  const size_t bytes = (size_t)d.ntiles * (size_t)d.kblocks * A_BYTES;
+  const size_t bytes = (size_t)npairs * (size_t)d.kblocks * A_BYTES;
   FZP_CUDA_TRY(cudaMalloc(&d.d_A, bytes));
   P.device_bytes += bytes;
-  k_build_A<<<4 * d.num_sms, 256>>>(P.M, P.N, d.kblocks, P.c, P.kappa, P.delta, reinterpret_cast<uint8_t*>(d.d_A));
+  k_build_A<<<8 * d.num_sms, 256>>>(P.M, P.N, d.kblocks, npairs, P.c, P.kappa, P.delta,
+                                    reinterpret_cast<uint8_t*>(d.d_A));
   FZP_CUDA_TRY(cudaGetLastError());
   FZP_CUDA_TRY(cudaFuncSetAttribute(k_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem_bytes()));
   return FZP_OK;
 }
 
 fzp_status dense_mask(Plan& P, int64_t j0, int64_t rows, uint8_t* out, cudaStream_t s) {
-  k_mask_rows<<<1024, 256, 0, s>>>(P.mg, P.N, j0, rows, P.dn.kblocks, out);
+  k_mask_rows<<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(P.mg, P.N, j0, rows, out);
   P.launches += 1;
   FZP_CUDA_TRY(cudaGetLastError());
   return FZP_OK;
@@ -517,7 +578,7 @@ fzp_status dense_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
   a.j_begin = j0;
   a.j_end = j0 + rows;
   a.n_stripes = (rows + BN - 1) / BN;
-  a.ntiles = d.ntiles;
+  a.npairs = (d.ntiles + TILES - 1) / TILES;
   a.promote = d.promote_kblocks;
   a.hi_only = P.precision == FZP_PREC_BF16 ? 1 : 0;
   a.A = reinterpret_cast<const uint8_t*>(d.d_A);
@@ -525,7 +586,7 @@ fzp_status dense_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
   a.c1_stride = P.chunk_rows;
   a.c1_j0 = j0;
   a.err = P.d_err;
-  const int64_t items = a.n_stripes * a.ntiles;
+  const int64_t items = a.n_stripes * a.npairs;
   const int grid = (int)std::min<int64_t>(items, d.num_sms);
   P.dominant = "dense_tcgen05";
   prof_begin(P, s);

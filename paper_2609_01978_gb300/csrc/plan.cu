@@ -199,7 +199,8 @@ fzp_status fzp_plan(const fzp_params* params, fzp_plan_t* out) {
   g_errmsg[0] = 0;
   st = build_mask_tables(*P);
   if (st == FZP_OK) {
-    const int64_t M2 = 2 * (int64_t)P->M;
+    // rows of C1: 2M kernel rows, rounded up to whole pairs of 128-row tiles (dense form)
+    const int64_t M2 = (2 * (int64_t)P->M + 255) / 256 * 256;
     // Row intermediate for a chunk of rows; the default budget keeps it <= 8 GiB.
     const int64_t budget_rows = (int64_t)((8ull << 30) / (uint64_t)(M2 * (P->precision == FZP_PREC_FP64 ? 8 : 4)));
     int64_t rows = std::min<int64_t>(P->N, budget_rows);
