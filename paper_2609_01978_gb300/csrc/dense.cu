@@ -178,71 +178,51 @@ __device__ __forceinline__ int64_t isqrt_floor(int64_t t) {  // largest a with a
   return a;
 }
 
-// Smallest a >= 0 with a^2 >= t, for 0 < t < 2^44: FP32 square root of a
-// 24-bit-accurate argument, then exact integer correction.
+// Smallest a >= 0 with a^2 >= t, for 0 < t < 2^44.  The hardware square root
+// of a float within 2^-12 of t (low bits dropped for t >= 2^24) lands within
+// [a - 3, a + 1]; exact integer corrections follow, without branches.
 __device__ __forceinline__ uint32_t ceil_sqrt44(int64_t t) {
   const float tf = t < (1ll << 24) ? (float)(uint32_t)t : (float)(uint32_t)(t >> 12) * 4096.0f;
-  uint32_t a = (uint32_t)__fsqrt_rn(tf);
-  while ((int64_t)((uint64_t)a * a) < t) ++a;
-  while (a > 0 && (int64_t)((uint64_t)(a - 1) * (a - 1)) >= t) --a;
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(tf));
+  uint32_t a = (uint32_t)r;
+  a += ((int64_t)((uint64_t)a * a) < t) ? 1u : 0u;
+  a += ((int64_t)((uint64_t)a * a) < t) ? 1u : 0u;
+  a += ((int64_t)((uint64_t)a * a) < t) ? 1u : 0u;
+  a -= (a > 0 && (int64_t)((uint64_t)(a - 1) * (a - 1)) >= t) ? 1u : 0u;
   return a;
 }
 
 // Walks one aperture row from column 0 upwards and yields the columns where
 // the binary transmission toggles.  Along the row the zone index is a function
-// of d = |i - c|, non-decreasing in d, and steps at d = a_m = ceil(sqrt(S_m - dj^2));
+// of d = |i - c|, non-decreasing in d, stepping at d = a_m = ceil(sqrt(S_m - dj^2));
 // the open state toggles at every step and at both ends of the disc chord.
-// Toggle columns in increasing order:
-//   c - bmax               (if the edge zone z_e is odd: the row enters open)
-//   c - a_m + 1, m = z_e .. z_c + 1   (zone drops below m, left half)
-//   c + a_m,     m = z_c + 1 .. z_e   (zone reaches m, right half)
-//   c + bmax + 1           (if z_e is odd: the row leaves the disc)
+// Toggle columns, numbered by the event index e (L = z_e - z_c boundaries per half):
+//   c - bmax                       start of the chord (only if the edge zone z_e is odd)
+//   c - a_m + 1, m = z_e .. z_c+1  zone drops below m (left half)
+//   c + a_m,     m = z_c+1 .. z_e  zone reaches m (right half)
+//   c + bmax + 1                   end of the chord (only if z_e is odd)
 struct Walker {
-  int64_t next;  // next toggle column (INT64_MAX: none)
-  int64_t m;     // threshold index of the pending boundary
+  int64_t next;  // column of event e (INT64_MAX: none left)
   int64_t dj2, c, bmax, zc, ze;
-  int phase;     // 0 start, 1 left, 2 right, 3 end, 4 done
+  int32_t e, ne, L, odd;
 };
 
-__device__ __forceinline__ void walker_advance(Walker& w, const int64_t* __restrict__ thr) {
-  while (true) {
-    switch (w.phase) {
-      case 0:
-        w.phase = 1;
-        w.m = w.ze;
-        if (w.ze & 1) { w.next = w.c - w.bmax; return; }
-        break;
-      case 1:
-        if (w.m > w.zc) {
-          w.next = w.c - (int64_t)ceil_sqrt44(__ldg(thr + (w.m - 1)) - w.dj2) + 1;
-          --w.m;
-          return;
-        }
-        w.phase = 2;
-        w.m = w.zc + 1;
-        break;
-      case 2:
-        if (w.m <= w.ze) {
-          w.next = w.c + (int64_t)ceil_sqrt44(__ldg(thr + (w.m - 1)) - w.dj2);
-          ++w.m;
-          return;
-        }
-        w.phase = 3;
-        break;
-      case 3:
-        w.phase = 4;
-        if (w.ze & 1) { w.next = w.c + w.bmax + 1; return; }
-        break;
-      default:
-        w.next = INT64_MAX;
-        return;
-    }
-  }
+__device__ __forceinline__ int64_t walker_event(const Walker& w, int32_t e, const int64_t* __restrict__ thr) {
+  if (e >= w.ne) return INT64_MAX;
+  const int32_t b = e - w.odd;  // boundary index, -1 = chord start, 2L = chord end
+  if (b < 0) return w.c - w.bmax;
+  if (b >= 2 * w.L) return w.c + w.bmax + 1;
+  const bool left = b < w.L;
+  const int64_t m = left ? w.ze - b : w.zc + 1 + (b - w.L);
+  const int64_t a = (int64_t)ceil_sqrt44(__ldg(thr + (m - 1)) - w.dj2);
+  return left ? w.c - a + 1 : w.c + a;
 }
 
 __device__ __forceinline__ void walker_init(Walker& w, int64_t j, int64_t j_end, const MaskGeom& g) {
   w.c = g.c;
-  w.phase = 4;
+  w.e = 0;
+  w.ne = 0;
   w.next = INT64_MAX;
   const int64_t dj = j - g.c;
   if (j >= j_end || dj * dj > g.sR) return;
@@ -250,24 +230,43 @@ __device__ __forceinline__ void walker_init(Walker& w, int64_t j, int64_t j_end,
   w.bmax = isqrt_floor(g.sR - w.dj2);
   w.zc = zone_of(w.dj2, g);
   w.ze = zone_of(w.dj2 + w.bmax * w.bmax, g);
-  w.phase = 0;
-  walker_advance(w, g.thr);
+  w.L = (int32_t)(w.ze - w.zc);
+  w.odd = (int32_t)(w.ze & 1);
+  w.ne = 2 * w.L + 2 * w.odd;
+  w.next = walker_event(w, 0, g.thr);
 }
 
 // Open bits of columns [i0, i0 + 32) given the open state at i0; updates the state.
 __device__ __forceinline__ uint32_t walker_bits(Walker& w, int64_t i0, uint32_t& state, const int64_t* thr) {
-  uint32_t bits = state ? 0xFFFFFFFFu : 0u;
+  uint32_t bits = 0u - state;
   while (w.next < i0 + 32) {
     bits ^= 0xFFFFFFFFu << (uint32_t)(w.next - i0);
     state ^= 1u;
-    walker_advance(w, thr);
+    w.next = walker_event(w, ++w.e, thr);
   }
   return bits;
 }
 
-// Two samples -> two BF16 values (1.0 = 0x3F80 or 0.0).
-__device__ __forceinline__ uint32_t pack2(uint32_t x) {
-  return (x & 1u) * 0x3F80u + ((x >> 1) & 1u) * 0x3F800000u;
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+  uint32_t d;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+  return d;
+}
+
+// 32 mask bits -> 32 BF16 values (1.0 = 0x3F80, 0.0) in 16 words.  y_j = bits
+// << (7 - j) puts sample 8q + j in the sign bit of byte q; prmt with the
+// sign-replicate selector expands two such bytes to 0x00/0xFF per output byte,
+// and the AND keeps 0x3F80 in each half-word.
+__device__ __forceinline__ void expand_bits(uint32_t bits, uint32_t (&w)[16]) {
+  uint32_t y[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) y[j] = bits << (7 - j);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int q = k >> 2, j = 2 * (k & 3);  // samples 2k = 8q + j and 8q + j + 1
+    const uint32_t sel = (uint32_t)((8 | q) | ((8 | q) << 4) | ((8 | (4 + q)) << 8) | ((8 | (4 + q)) << 12));
+    w[k] = prmt(y[j], y[j + 1], sel) & 0x3F803F80u;
+  }
 }
 
 // ---------------------------------------------------------------- kernel
@@ -412,16 +411,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
         if (!warp_wait(&empty[stage], phase ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 5)) { ok = false; break; }
         const uint32_t bits = walker_bits(w, kb * BK, state, a.mg.thr);
         uint8_t* rowp = rowbase0 + stage * B_BYTES;
+        uint32_t wd[16];
+        expand_bits(bits, wd);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const uint32_t byte = (bits >> (8 * q)) & 0xFFu;
-          uint4 v;
-          v.x = pack2(byte);
-          v.y = pack2(byte >> 2);
-          v.z = pack2(byte >> 4);
-          v.w = pack2(byte >> 6);
-          *reinterpret_cast<uint4*>(rowp + ((q ^ sw) << 4)) = v;
-        }
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<uint4*>(rowp + ((q ^ sw) << 4)) = make_uint4(wd[4 * q], wd[4 * q + 1], wd[4 * q + 2], wd[4 * q + 3]);
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(&fullB[stage]);
