@@ -23,7 +23,8 @@
 //   warp 9   : allocates 512 TMEM columns and issues tcgen05.mma (M128 N256 K16)
 //              into two FP32 accumulators (one per tile)
 //   warps 0-7: epilogue; every `promote` stages both accumulators are read with
-//              tcgen05.ld and added in FP32 to the C1 tiles in global memory.
+//              tcgen05.ld and added in FP32 to the C1 tiles in global memory
+//              (stored for the first chunk, red.global.add afterwards).
 //              The tensor core's FP32 accumulation loses precision in proportion
 //              to the chunk length (measured: 8e-4 relative error of I over a
 //              0.25 m aperture without promotion, 8e-6 with 4096-sample chunks).
@@ -89,12 +90,14 @@ __device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t tx) {
                "r"(tx)
                : "memory");
 }
+// try_wait with a suspend-time hint: the waiting thread sleeps in hardware
+// (up to 20 us per call) until the phase completes, instead of spinning.
 __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
       : "memory");
   return ok != 0;
 }
@@ -446,12 +449,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
 #pragma unroll
             for (int k = 0; k < 8; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
           } else {
+            // fire-and-forget FP32 adds in L2: the accumulator is released without
+            // waiting for a read of the partial sums
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              float4 o = dst[k];
-              o.x += v[4 * k]; o.y += v[4 * k + 1]; o.z += v[4 * k + 2]; o.w += v[4 * k + 3];
-              dst[k] = o;
-            }
+            for (int k = 0; k < 8; ++k)
+              asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + k), "f"(v[4 * k]),
+                           "f"(v[4 * k + 1]), "f"(v[4 * k + 2]), "f"(v[4 * k + 3])
+                           : "memory");
           }
         }
         tc_fence_before();
