@@ -69,7 +69,10 @@ typedef enum {
   FZP_PREC_FP64 = 0,       /* Bluestein in FP64 throughout                          */
   FZP_PREC_FP32 = 1,       /* Bluestein in FP32 (complex64)                          */
   FZP_PREC_SPLIT_BF16 = 2, /* dense: K = K_hi + K_lo in BF16, T exact, FP32 accumulate */
-  FZP_PREC_BF16 = 3        /* dense: K_hi only (reduced accuracy, for error studies)   */
+  FZP_PREC_BF16 = 3,       /* dense: K_hi only (reduced accuracy, for error studies)   */
+  FZP_PREC_AUTO_1E4 = 4    /* any arithmetic whose ROI-intensity error is <= 1e-4: the
+                              autotuner measures split-BF16 dense and FP32 Bluestein
+                              (and their knobs) on a probe stripe and keeps the faster */
 } fzp_precision;
 
 /* Membrane deformation w(u,v) [m]; phase phi = (4 pi / lambda) w:
@@ -98,8 +101,14 @@ typedef struct fzp_params {
   int32_t form;        /* fzp_form                                                     */
   double pitch;        /* ROI pitch p [m], > 0                                         */
   int32_t precision;   /* fzp_precision                                                */
-  int32_t stripe_rows; /* aperture rows per stripe; 0 -> library default              */
+  int32_t stripe_rows; /* aperture rows per row-pass chunk (multiple of 256); 0 ->
+                          as many as an 8 GiB row intermediate holds               */
   const fzp_deform* deform; /* NULL: flat membrane.  Copied by fzp_plan.               */
+  int32_t promote;     /* dense: 32-column K blocks accumulated in tensor memory before
+                          promotion to FP32 global sums; 0 -> 128 (error ~8e-6 at
+                          D = 0.25 m; it grows in proportion to this length)       */
+  int32_t row_batch;   /* Bluestein: aperture rows per FFT pass launch; 0 -> rows of a
+                          1 GiB transform workspace                               */
 } fzp_params;
 
 /* Opaque plan: geometry, zone-threshold table, chirp / kernel tables and the
@@ -122,7 +131,10 @@ typedef struct fzp_plan_info {
   int32_t precision;     /* fzp_precision                                          */
   int32_t stripe_rows;   /* resolved stripe height                                 */
   int64_t fft_length;    /* Bluestein length L = 2^ceil(log2(N + M - 1)) (Sec. 2.6) */
-  size_t device_bytes;   /* device memory owned by the plan                        */
+  size_t device_bytes;   /* device memory owned by the plan (batch: by the batch)  */
+  int32_t promote;       /* dense: K blocks per tensor-memory accumulation chunk   */
+  int32_t row_batch;     /* Bluestein: aperture rows per FFT pass launch           */
+  int64_t chunk_rows;    /* aperture rows per row-pass chunk                       */
 } fzp_plan_info;
 
 /* Metrics of Fig. 2 Stage 4 / Fig. 18 Stage 5. */
@@ -175,6 +187,39 @@ FZP_API fzp_status fzp_intensity(fzp_plan_t plan, const void* d_field, void* d_i
  * Also reports any device-side timeout recorded by earlier calls on this plan
  * (FZP_E_TIMEOUT). */
 FZP_API fzp_status fzp_metrics(fzp_plan_t plan, const void* d_field, void* stream, fzp_metrics_t* out);
+
+/* ---- Batches: many apertures in one CUDA graph ----------------------------
+ *
+ * A batch holds n problems (different D, lambda, deformation, ROI) that share
+ * one set of device buffers sized for the largest.  Each instance's form
+ * tables are regenerated inside the batch, and its work -- tables, row passes
+ * (the dense form as one persistent launch), column pass and epilogue -- is
+ * captured with all other instances into one CUDA graph that
+ * fzp_batch_propagate replays with a single launch.  Instances with
+ * precision FZP_PREC_AUTO_1E4 are autotuned first (see fzp_precision).
+ * The per-instance stages follow Fig. 18 (tables, row stage, column stage,
+ * output chirp); the batching itself has no counterpart in the paper. */
+typedef struct fzp_batch_s* fzp_batch_t;
+
+/* Plan a batch of n >= 1 problems.  params[i] as for fzp_plan.  Errors as
+ * fzp_plan; the message names the failing instance. */
+FZP_API fzp_status fzp_batch_plan(const fzp_params* params, int n, fzp_batch_t* out);
+
+/* Full-aperture field of every instance: d_fields[i] is a device complex128
+ * M_i*M_i buffer (caller-owned), overwritten.  The first call (and any call
+ * with different field pointers) captures the graph; later calls replay it.
+ * Asynchronous on `stream`. */
+FZP_API fzp_status fzp_batch_propagate(fzp_batch_t batch, void* const* d_fields, void* stream);
+
+/* Plan description of instance `index` (the form and knobs chosen for it). */
+FZP_API fzp_status fzp_batch_info(fzp_batch_t batch, int index, fzp_plan_info* out);
+
+/* Metric extractor for instance `index` (as fzp_metrics). */
+FZP_API fzp_status fzp_batch_metrics(fzp_batch_t batch, int index, const void* d_field, void* stream,
+                                     fzp_metrics_t* out);
+
+/* Release the batch.  NULL is accepted.  Synchronises the device. */
+FZP_API fzp_status fzp_batch_destroy(fzp_batch_t batch);
 
 /* Metric extractor that allocates nothing (no counterpart in the paper).
  *

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libfzp.so")
 
 FZP_OK, FZP_E_INVALID, FZP_E_OOM, FZP_E_CUDA, FZP_E_TIMEOUT, FZP_E_UNSUPPORTED = range(6)
 FORM_AUTO, FORM_BLUESTEIN, FORM_DENSE = 0, 1, 2
-PREC_FP64, PREC_FP32, PREC_SPLIT_BF16, PREC_BF16 = 0, 1, 2, 3
+PREC_FP64, PREC_FP32, PREC_SPLIT_BF16, PREC_BF16, PREC_AUTO_1E4 = 0, 1, 2, 3, 4
 
 _STATUS = {0: "FZP_OK", 1: "FZP_E_INVALID", 2: "FZP_E_OOM", 3: "FZP_E_CUDA", 4: "FZP_E_TIMEOUT",
            5: "FZP_E_UNSUPPORTED"}
@@ -45,7 +45,8 @@ class Params(ctypes.Structure):
     _fields_ = [("D", ctypes.c_double), ("f", ctypes.c_double), ("lam", ctypes.c_double),
                 ("dx", ctypes.c_double), ("N", ctypes.c_int64), ("M", ctypes.c_int32),
                 ("form", ctypes.c_int32), ("pitch", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("stripe_rows", ctypes.c_int32), ("deform", ctypes.POINTER(Deform))]
+                ("stripe_rows", ctypes.c_int32), ("deform", ctypes.POINTER(Deform)),
+                ("promote", ctypes.c_int32), ("row_batch", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -53,7 +54,8 @@ class PlanInfo(ctypes.Structure):
                 ("n_thresholds", ctypes.c_int64), ("dx", ctypes.c_double), ("R", ctypes.c_double),
                 ("kappa", ctypes.c_double), ("x0", ctypes.c_double), ("M", ctypes.c_int32),
                 ("form", ctypes.c_int32), ("precision", ctypes.c_int32), ("stripe_rows", ctypes.c_int32),
-                ("fft_length", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
+                ("fft_length", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
+                ("promote", ctypes.c_int32), ("row_batch", ctypes.c_int32), ("chunk_rows", ctypes.c_int64)]
 
 
 class Metrics(ctypes.Structure):
@@ -95,6 +97,11 @@ def lib() -> ctypes.CDLL:
             "fzp_aperture_mask": [vp, i64, i64, vp, vp],
             "fzp_metrics_noalloc": [ctypes.POINTER(Params), vp, vp, ctypes.POINTER(Metrics)],
             "fzp_profile_enable": [vp, i32],
+            "fzp_batch_plan": [ctypes.POINTER(Params), i32, ctypes.POINTER(vp)],
+            "fzp_batch_propagate": [vp, ctypes.POINTER(vp), vp],
+            "fzp_batch_info": [vp, i32, ctypes.POINTER(PlanInfo)],
+            "fzp_batch_metrics": [vp, i32, vp, vp, ctypes.POINTER(Metrics)],
+            "fzp_batch_destroy": [vp],
             "fzp_profile_read": [vp, ctypes.POINTER(Profile)],
         }
         for name, args in sig.items():
@@ -145,10 +152,11 @@ class Plan:
 
     def __init__(self, D: float, f: float, lam: float, M: int, pitch: float, dx: float = 0.0, N: int = 0,
                  form: int = FORM_AUTO, precision: int = PREC_FP32, stripe_rows: int = 0,
-                 deform: Optional[Deform] = None):
+                 deform: Optional[Deform] = None, promote: int = 0, row_batch: int = 0):
         self._deform = deform
         p = Params(D=D, f=f, lam=lam, dx=dx, N=N, M=M, form=form, pitch=pitch, precision=precision,
-                   stripe_rows=stripe_rows, deform=ctypes.pointer(deform) if deform is not None else None)
+                   stripe_rows=stripe_rows, deform=ctypes.pointer(deform) if deform is not None else None,
+                   promote=promote, row_batch=row_batch)
         h = ctypes.c_void_p()
         _check(lib().fzp_plan(ctypes.byref(p), ctypes.byref(h)))
         self._h = h
@@ -199,6 +207,54 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Batch:
+    """fzp_batch_plan / fzp_batch_propagate: many apertures replayed as one CUDA graph.
+
+    `problems` is a list of dicts with the keyword arguments of Plan."""
+
+    def __init__(self, problems):
+        n = len(problems)
+        arr = (Params * n)()
+        self._keep = []
+        for k, pr in enumerate(problems):
+            d = pr.get("deform")
+            self._keep.append(d)
+            arr[k] = Params(D=pr["D"], f=pr["f"], lam=pr["lam"], dx=pr.get("dx", 0.0), N=pr.get("N", 0), M=pr["M"],
+                            form=pr.get("form", FORM_AUTO), pitch=pr["pitch"],
+                            precision=pr.get("precision", PREC_AUTO_1E4), stripe_rows=pr.get("stripe_rows", 0),
+                            deform=ctypes.pointer(d) if d is not None else None, promote=pr.get("promote", 0),
+                            row_batch=pr.get("row_batch", 0))
+        h = ctypes.c_void_p()
+        _check(lib().fzp_batch_plan(arr, n, ctypes.byref(h)))
+        self._h = h
+        self.n = n
+
+    def info(self, i: int) -> dict:
+        inf = PlanInfo()
+        _check(lib().fzp_batch_info(self._h, i, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in inf._fields_}
+
+    def propagate(self, fields, stream=None):
+        ptrs = (ctypes.c_void_p * self.n)(*[_ptr(f) for f in fields])
+        _check(lib().fzp_batch_propagate(self._h, ptrs, _stream(stream)))
+
+    def metrics(self, i: int, field, stream=None) -> dict:
+        m = Metrics()
+        _check(lib().fzp_batch_metrics(self._h, i, _ptr(field), _stream(stream), ctypes.byref(m)))
+        return m.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fzp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def metrics_noalloc(field, D: float, f: float, lam: float, M: int, pitch: float, dx: float = 0.0, N: int = 0,

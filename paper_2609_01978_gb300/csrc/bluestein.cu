@@ -308,7 +308,7 @@ static RowArgs make_args(const Plan& P) {
 }
 
 template <typename R>
-fzp_status build_tables_t(Plan& P) {
+fzp_status layout_t(Plan& P, FormSizes* out) {
   using C = typename Cplx<R>::T;
   Bluestein& b = P.bs;
   b.L = 1;
@@ -316,45 +316,61 @@ fzp_status build_tables_t(Plan& P) {
   b.L2 = b.L < Traits<R>::L2MAX ? b.L : Traits<R>::L2MAX;
   b.L1 = b.L / b.L2;
   if (P.M > b.L2) return set_error(FZP_E_UNSUPPORTED, "M larger than the inner FFT length");
-  const int twN = (int)b.L2;
-  // row batch: Z workspace of about 1 GiB
+  // rows per pass: requested, else a transform workspace of about 1 GiB
   const int64_t zbytes = (int64_t)sizeof(C) * b.L;
-  b.rows = b.L1 > 1 ? std::max<int64_t>(1, std::min<int64_t>(P.chunk_rows, (1ll << 30) / zbytes)) : P.chunk_rows;
-  if (b.rows > 65535) b.rows = 65535;
-  FZP_CUDA_TRY(cudaMalloc(&b.d_pre, sizeof(C) * P.N));
-  FZP_CUDA_TRY(cudaMalloc(&b.d_H, sizeof(C) * b.L));
-  FZP_CUDA_TRY(cudaMalloc(&b.d_tab, sizeof(C) * (b.L + twN / 2 + P.M)));
+  int64_t rows = P.row_batch_req > 0 ? P.row_batch_req : (1ll << 30) / zbytes;
+  if (b.L1 == 1) rows = P.row_batch_req > 0 ? P.row_batch_req : P.chunk_rows;
+  b.rows = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(rows, P.chunk_rows), 65535));
+  const int twN = (int)b.L2;
+  out->pre = sizeof(C) * P.N;
+  out->H = sizeof(C) * b.L;
+  out->tab = sizeof(C) * (b.L + twN / 2 + P.M);
+  out->Z = sizeof(C) * b.L * (b.L1 > 1 ? b.rows : 1);  // row 0 also serves the table build
+  out->G = b.L1 > 1 ? sizeof(C) * b.L1 * P.M * b.rows : 0;
+  static bool attrs = false;
+  if (!attrs) {
+    FZP_CUDA_TRY(cudaFuncSetAttribute(k_f1<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+    FZP_CUDA_TRY(cudaFuncSetAttribute(k_f2<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(C) * Traits<R>::L2MAX)));
+    attrs = true;
+  }
+  return FZP_OK;
+}
+
+template <typename R>
+fzp_status fill_tables_t(Plan& P, cudaStream_t s) {
+  using C = typename Cplx<R>::T;
+  Bluestein& b = P.bs;
+  const int twN = (int)b.L2;
   b.d_tw = reinterpret_cast<C*>(b.d_tab) + b.L;
   b.d_post = reinterpret_cast<C*>(b.d_tw) + twN / 2;
-  const int64_t zrows = b.L1 > 1 ? b.rows : 1;
-  FZP_CUDA_TRY(cudaMalloc(&b.d_Z, sizeof(C) * b.L * zrows));
-  if (b.L1 > 1) FZP_CUDA_TRY(cudaMalloc(&b.d_G, sizeof(C) * b.L1 * P.M * b.rows));
-  P.device_bytes += sizeof(C) * (P.N + b.L + b.L + twN / 2 + P.M + b.L * zrows) +
-                    (b.L1 > 1 ? sizeof(C) * b.L1 * P.M * b.rows : 0);
-  k_tables<R><<<1024, 256>>>(P.N, P.M, b.L, P.c, P.kappa, P.delta, b.d_pre, b.d_post, b.d_tab, b.d_tw, twN);
+  k_tables<R><<<1024, 256, 0, s>>>(P.N, P.M, b.L, P.c, P.kappa, P.delta, b.d_pre, b.d_post, b.d_tab, b.d_tw, twN);
   FZP_CUDA_TRY(cudaGetLastError());
-  // H = FFT_L(v) in the [k1][k2] order: F1 (table mode) + F2 (forward only) into Z, then copy.
+  // H = FFT_L(v) in the [k1][k2] order: F1 (table mode) + F2 (forward only) into Z row 0, then copy.
   RowArgs a = make_args(P);
   a.j0 = 0;
   a.rows = 1;
-  if (b.L1 > 1) {
-    const size_t sm = sizeof(C) * b.L1 * a.B;
-    FZP_CUDA_TRY(cudaFuncSetAttribute(k_f1<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_f1<R><<<dim3((unsigned)(b.L2 / a.B), 1), 256, sm>>>(a, 1);
-    FZP_CUDA_TRY(cudaGetLastError());
-  }
-  {
-    const size_t sm = sizeof(C) * b.L2;
-    FZP_CUDA_TRY(cudaFuncSetAttribute(k_f2<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_f2<R><<<dim3((unsigned)b.L1, 1), 512, sm>>>(a, 1);
-    FZP_CUDA_TRY(cudaGetLastError());
-  }
-  FZP_CUDA_TRY(cudaMemcpy(b.d_H, b.d_Z, sizeof(C) * b.L, cudaMemcpyDeviceToDevice));
-  if (b.L1 == 1) {  // Z only served the table build
-    FZP_CUDA_TRY(cudaFree(b.d_Z));
-    b.d_Z = nullptr;
-  }
+  if (b.L1 > 1) k_f1<R><<<dim3((unsigned)(b.L2 / a.B), 1), 256, sizeof(C) * b.L1 * a.B, s>>>(a, 1);
+  k_f2<R><<<dim3((unsigned)b.L1, 1), 512, sizeof(C) * b.L2, s>>>(a, 1);
+  FZP_CUDA_TRY(cudaGetLastError());
+  FZP_CUDA_TRY(cudaMemcpyAsync(b.d_H, b.d_Z, sizeof(C) * b.L, cudaMemcpyDeviceToDevice, s));
+  P.launches += b.L1 > 1 ? 3 : 2;
   return FZP_OK;
+}
+
+template <typename R>
+fzp_status build_tables_t(Plan& P) {
+  Bluestein& b = P.bs;
+  FormSizes z;
+  fzp_status st = layout_t<R>(P, &z);
+  if (st != FZP_OK) return st;
+  FZP_CUDA_TRY(cudaMalloc(&b.d_pre, z.pre));
+  FZP_CUDA_TRY(cudaMalloc(&b.d_H, z.H));
+  FZP_CUDA_TRY(cudaMalloc(&b.d_tab, z.tab));
+  FZP_CUDA_TRY(cudaMalloc(&b.d_Z, z.Z));
+  if (z.G) FZP_CUDA_TRY(cudaMalloc(&b.d_G, z.G));
+  P.device_bytes += z.pre + z.H + z.tab + z.Z + z.G;
+  return fill_tables_t<R>(P, 0);
 }
 
 template <typename R>
@@ -404,6 +420,14 @@ fzp_status bluestein_mask(Plan& P, int64_t j0, int64_t rows, uint8_t* out, cudaS
 
 fzp_status bluestein_build_tables(Plan& P) {
   return P.precision == FZP_PREC_FP64 ? build_tables_t<double>(P) : build_tables_t<float>(P);
+}
+
+fzp_status bluestein_layout(Plan& P, FormSizes* out) {
+  return P.precision == FZP_PREC_FP64 ? layout_t<double>(P, out) : layout_t<float>(P, out);
+}
+
+fzp_status bluestein_fill_tables(Plan& P, cudaStream_t s) {
+  return P.precision == FZP_PREC_FP64 ? fill_tables_t<double>(P, s) : fill_tables_t<float>(P, s);
 }
 
 fzp_status bluestein_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream) {

@@ -540,24 +540,41 @@ size_t dense_smem_bytes() { return 1024 + STAGES * (A_BYTES + B_BYTES) + 256; }
 
 }  // namespace
 
-fzp_status dense_build_tables(Plan& P) {
+fzp_status dense_layout(Plan& P, FormSizes* out) {
   Dense& d = P.dn;
   d.kblocks = (P.N + BK - 1) / BK;
   d.ntiles = 2 * P.M / BM;
   const int npairs = (d.ntiles + TILES - 1) / TILES;
-  d.promote_kblocks = 128;  // 4096 samples per TMEM accumulation chunk
-  if (const char* e = getenv("FZP_DENSE_PROMOTE")) d.promote_kblocks = std::max(1, atoi(e));
+  d.promote_kblocks = P.promote_req > 0 ? P.promote_req : 128;  // 4096 samples per TMEM chunk
   int dev = 0;
   FZP_CUDA_TRY(cudaGetDevice(&dev));
   FZP_CUDA_TRY(cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev));
-  const size_t bytes = (size_t)npairs * (size_t)d.kblocks * A_BYTES;
-  FZP_CUDA_TRY(cudaMalloc(&d.d_A, bytes));
-  P.device_bytes += bytes;
-  k_build_A<<<8 * d.num_sms, 256>>>(P.M, P.N, d.kblocks, npairs, P.c, P.kappa, P.delta,
-                                    reinterpret_cast<uint8_t*>(d.d_A));
-  FZP_CUDA_TRY(cudaGetLastError());
-  FZP_CUDA_TRY(cudaFuncSetAttribute(k_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem_bytes()));
+  out->A = (size_t)npairs * (size_t)d.kblocks * A_BYTES;
+  static bool attrs = false;
+  if (!attrs) {
+    FZP_CUDA_TRY(cudaFuncSetAttribute(k_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem_bytes()));
+    attrs = true;
+  }
   return FZP_OK;
+}
+
+fzp_status dense_fill_tables(Plan& P, cudaStream_t s) {
+  Dense& d = P.dn;
+  const int npairs = (d.ntiles + TILES - 1) / TILES;
+  k_build_A<<<8 * d.num_sms, 256, 0, s>>>(P.M, P.N, d.kblocks, npairs, P.c, P.kappa, P.delta,
+                                          reinterpret_cast<uint8_t*>(d.d_A));
+  P.launches += 1;
+  FZP_CUDA_TRY(cudaGetLastError());
+  return FZP_OK;
+}
+
+fzp_status dense_build_tables(Plan& P) {
+  FormSizes z;
+  fzp_status st = dense_layout(P, &z);
+  if (st != FZP_OK) return st;
+  FZP_CUDA_TRY(cudaMalloc(&P.dn.d_A, z.A));
+  P.device_bytes += z.A;
+  return dense_fill_tables(P, 0);
 }
 
 fzp_status dense_mask(Plan& P, int64_t j0, int64_t rows, uint8_t* out, cudaStream_t s) {

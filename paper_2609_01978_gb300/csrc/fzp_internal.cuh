@@ -147,6 +147,8 @@ struct Plan {
   int64_t N, c;
   int M;
   int form, precision, stripe_rows;
+  int promote_req = 0, row_batch_req = 0;  // tuning knobs as requested (0: default)
+  bool owns_buffers = true;  // false: tables and workspace belong to a batch
   // derived
   double kappa, delta, dx2, R2;
   int64_t total_zones;
@@ -178,8 +180,17 @@ void prof_begin(Plan& P, cudaStream_t s);
 void prof_end(Plan& P, cudaStream_t s);
 
 // Launchers implemented in the .cu files.  All enqueue on `stream`.
-fzp_status bluestein_build_tables(Plan& P);
+// Form layouts: sizes in bytes of the form's tables and transform workspace.
+struct FormSizes {
+  size_t pre = 0, H = 0, tab = 0, Z = 0, G = 0;  // Bluestein
+  size_t A = 0;                                  // dense
+};
+fzp_status bluestein_layout(Plan& P, FormSizes* out);
+fzp_status bluestein_fill_tables(Plan& P, cudaStream_t s);  // buffers already assigned
+fzp_status bluestein_build_tables(Plan& P);                 // layout + allocate + fill
 fzp_status bluestein_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream);
+fzp_status dense_layout(Plan& P, FormSizes* out);
+fzp_status dense_fill_tables(Plan& P, cudaStream_t s);
 fzp_status dense_build_tables(Plan& P);
 fzp_status dense_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream);
 fzp_status column_pass(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream);
@@ -198,3 +209,7 @@ __host__ __device__ __forceinline__ int c1_row_im(int m) { return (m >> 6) * 128
 
 // The opaque handle of the C ABI is the plan itself.
 struct fzp_plan_s : public fzp::Plan {};
+
+namespace fzp {
+fzp_status autotune(const fzp_params* in, fzp_params* chosen, fzp_plan_t* keep);
+}

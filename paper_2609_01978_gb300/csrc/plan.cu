@@ -72,20 +72,28 @@ void prof_end(Plan& P, cudaStream_t s) {
   ++P.prof_used;
 }
 
-static void release(fzp_plan_s* P) {
+void release_plan(Plan* P) {
   if (!P) return;
   for (auto& e : P->prof_events) {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);
   }
-  void* ptrs[] = {P->d_thr, P->d_C1, P->d_C1d, P->d_Uacc, P->d_err, P->d_metrics,
-                  P->bs.d_pre, P->bs.d_H, P->bs.d_Z, P->bs.d_G, P->bs.d_tab, P->dn.d_A};
-  for (void* q : ptrs)
-    if (q) cudaFree(q);
+  if (P->d_thr) cudaFree(P->d_thr);
+  if (P->owns_buffers) {
+    void* ptrs[] = {P->d_C1, P->d_C1d, P->d_Uacc, P->d_err, P->d_metrics,
+                    P->bs.d_pre, P->bs.d_H, P->bs.d_Z, P->bs.d_G, P->bs.d_tab, P->dn.d_A};
+    for (void* q : ptrs)
+      if (q) cudaFree(q);
+  }
+}
+
+static void release(fzp_plan_s* P) {
+  if (!P) return;
+  release_plan(P);
   delete P;
 }
 
-static fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
+fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
   if (!(in->D > 0) || !(in->f > 0) || !(in->lambda > 0) || !(in->pitch > 0) || !std::isfinite(in->D) ||
       !std::isfinite(in->f) || !std::isfinite(in->lambda) || !std::isfinite(in->pitch))
     return set_error(FZP_E_INVALID, "D, f, lambda and pitch must be finite and positive");
@@ -94,9 +102,11 @@ static fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
     return set_error(FZP_E_INVALID, "M must be a power of two in [64, 1024] (got %d)", in->M);
   if (in->N < 0 || (in->N > 0 && (in->N % 2) == 0))
     return set_error(FZP_E_INVALID, "N must be 0 (derive) or odd (got %lld)", (long long)in->N);
-  if (in->stripe_rows < 0) return set_error(FZP_E_INVALID, "stripe_rows must be >= 0");
+  if (in->stripe_rows < 0 || (in->stripe_rows % 256) != 0)
+    return set_error(FZP_E_INVALID, "stripe_rows must be 0 or a positive multiple of 256");
+  if (in->promote < 0 || in->row_batch < 0) return set_error(FZP_E_INVALID, "promote and row_batch must be >= 0");
   if (in->form < FZP_FORM_AUTO || in->form > FZP_FORM_DENSE) return set_error(FZP_E_INVALID, "unknown form");
-  if (in->precision < FZP_PREC_FP64 || in->precision > FZP_PREC_BF16)
+  if (in->precision < FZP_PREC_FP64 || in->precision > FZP_PREC_AUTO_1E4)
     return set_error(FZP_E_INVALID, "unknown precision");
   if (in->deform && (in->deform->n_ridges < 0 || in->deform->n_ridges > 3))
     return set_error(FZP_E_INVALID, "deform.n_ridges must be in [0, 3]");
@@ -143,10 +153,12 @@ static fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
     P.deform = *in->deform;
   }
   P.stripe_rows = in->stripe_rows;
+  P.promote_req = in->promote;
+  P.row_batch_req = in->row_batch;
   return FZP_OK;
 }
 
-static fzp_status build_mask_tables(Plan& P) {
+fzp_status build_mask_tables(Plan& P) {
   P.mg.c = P.c;
   P.mg.sR = disc_limit(P.dx2, P.R2);
   const int64_t zmax = zone_host(P.mg.sR, P.kappa);
@@ -167,8 +179,18 @@ static fzp_status build_mask_tables(Plan& P) {
   return FZP_OK;
 }
 
+// Rows per row-pass chunk: requested (multiple of 256), else as many as an
+// 8 GiB row intermediate holds; never more than the grid (rounded to 256).
+int64_t chunk_rows_for(const Plan& P) {
+  const int64_t M2 = (2 * (int64_t)P.M + 255) / 256 * 256;
+  const int64_t budget_rows = (int64_t)((8ull << 30) / (uint64_t)(M2 * (P.precision == FZP_PREC_FP64 ? 8 : 4)));
+  int64_t rows = P.stripe_rows > 0 ? (int64_t)P.stripe_rows : budget_rows;
+  rows = std::min<int64_t>(rows, P.N);
+  return (rows + 255) / 256 * 256;
+}
+
 // Rows of [0, N) that intersect the aperture disc: dj^2 <= s_R.
-static void disc_rows(const Plan& P, int64_t& jlo, int64_t& jhi) {
+void disc_rows(const Plan& P, int64_t& jlo, int64_t& jhi) {
   int64_t b = (int64_t)std::floor(std::sqrt((double)P.mg.sR));
   while ((b + 1) * (b + 1) <= P.mg.sR) ++b;
   while (b * b > P.mg.sR) --b;
@@ -192,6 +214,10 @@ fzp_status fzp_plan(const fzp_params* params, fzp_plan_t* out) {
   if (!out) return set_error(FZP_E_INVALID, "out is NULL");
   *out = nullptr;
   if (!params) return set_error(FZP_E_INVALID, "params is NULL");
+  if (params->precision == FZP_PREC_AUTO_1E4) {
+    fzp_params chosen;
+    return autotune(params, &chosen, out);
+  }
   fzp_plan_s* P = new (std::nothrow) fzp_plan_s();
   if (!P) return set_error(FZP_E_OOM, "host allocation failed");
   fzp_status st = validate_and_derive(params, *P);
@@ -201,11 +227,8 @@ fzp_status fzp_plan(const fzp_params* params, fzp_plan_t* out) {
   if (st == FZP_OK) {
     // rows of C1: 2M kernel rows, rounded up to whole pairs of 128-row tiles (dense form)
     const int64_t M2 = (2 * (int64_t)P->M + 255) / 256 * 256;
-    // Row intermediate for a chunk of rows; the default budget keeps it <= 8 GiB.
-    const int64_t budget_rows = (int64_t)((8ull << 30) / (uint64_t)(M2 * (P->precision == FZP_PREC_FP64 ? 8 : 4)));
-    int64_t rows = std::min<int64_t>(P->N, budget_rows);
-    rows = (rows + 255) / 256 * 256;
-    P->chunk_rows = rows;
+    P->chunk_rows = chunk_rows_for(*P);
+    const int64_t rows = P->chunk_rows;
     cudaError_t e = cudaSuccess;
     if (P->precision == FZP_PREC_FP64) e = cudaMalloc(&P->d_C1d, (size_t)(M2 * rows) * sizeof(double));
     else e = cudaMalloc(&P->d_C1, (size_t)(M2 * rows) * sizeof(float));
@@ -243,6 +266,9 @@ fzp_status fzp_plan_info_get(fzp_plan_t plan, fzp_plan_info* out) {
   out->M = P.M; out->form = P.form; out->precision = P.precision;
   out->stripe_rows = P.stripe_rows;
   out->fft_length = P.bs.L;
+  out->promote = P.form == FZP_FORM_DENSE ? P.dn.promote_kblocks : 0;
+  out->row_batch = P.form == FZP_FORM_BLUESTEIN ? (int32_t)P.bs.rows : 0;
+  out->chunk_rows = P.chunk_rows;
   out->device_bytes = P.device_bytes;
   return FZP_OK;
 }
