@@ -221,6 +221,48 @@ FZP_API fzp_status fzp_batch_metrics(fzp_batch_t batch, int index, const void* d
 /* Release the batch.  NULL is accepted.  Synchronises the device. */
 FZP_API fzp_status fzp_batch_destroy(fzp_batch_t batch);
 
+/* ---- Learned surrogate (no counterpart in the paper) ------------------------
+ *
+ * A multilayer perceptron n_in -> hidden (x n_hidden_layers, SiLU) -> n_out
+ * (linear), trained with mean squared error and AdamW (decoupled weight decay
+ * on weights), by kernels in this library: every matrix product takes BF16
+ * operands and accumulates in FP32 on the tensor cores (tcgen05); master
+ * weights, optimiser state and gradients are FP32.  It learns the map from
+ * membrane-deformation parameters to the PSF and metrics that this library's
+ * propagation computes; the propagation stays the reference that judges it.
+ * Parameters are one flat FP32 vector: for each layer W (n_out x n_in,
+ * row-major) then b (n_out). */
+typedef struct fzp_surrogate_s* fzp_surrogate_t;
+
+/* Create with weights ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from `seed`, biases 0.
+ * All sizes in [1, 65536]; max_batch bounds every later batch. */
+FZP_API fzp_status fzp_surrogate_create(int n_in, int hidden, int n_hidden_layers, int n_out, int max_batch,
+                                        uint64_t seed, fzp_surrogate_t* out);
+
+/* Number of FP32 parameters (0 for NULL). */
+FZP_API size_t fzp_surrogate_param_count(fzp_surrogate_t s);
+
+/* Copy the master parameters to (set = 0) or from (set = 1) host memory;
+ * count must equal fzp_surrogate_param_count.  Synchronous. */
+FZP_API fzp_status fzp_surrogate_params(fzp_surrogate_t s, float* h_params, size_t count, int set);
+
+/* y = network(x): d_x device FP32 [batch][n_in], d_y device FP32 [batch][n_out],
+ * 1 <= batch <= max_batch.  Asynchronous on `stream`. */
+FZP_API fzp_status fzp_surrogate_infer(fzp_surrogate_t s, const float* d_x, int batch, float* d_y, void* stream);
+
+/* Loss (mean squared error, written to d_loss, device FP32 scalar, optional)
+ * and its gradient (d_grad, device FP32 [param_count], optional) for a batch
+ * (multiple of 8, <= max_batch) of inputs d_x and targets d_y [batch][n_out]. */
+FZP_API fzp_status fzp_surrogate_grad(fzp_surrogate_t s, const float* d_x, const float* d_y, int batch,
+                                      float* d_grad, float* d_loss, void* stream);
+
+/* One AdamW step (beta1 0.9, beta2 0.999, eps 1e-8) on a batch (multiple of 8). */
+FZP_API fzp_status fzp_surrogate_train_step(fzp_surrogate_t s, const float* d_x, const float* d_y, int batch,
+                                            float lr, float weight_decay, float* d_loss, void* stream);
+
+/* Release.  NULL is accepted. */
+FZP_API fzp_status fzp_surrogate_destroy(fzp_surrogate_t s);
+
 /* Metric extractor that allocates nothing (no counterpart in the paper).
  *
  * Some callers cannot allocate device memory: a process whose device memory is

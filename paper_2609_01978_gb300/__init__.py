@@ -102,6 +102,12 @@ def lib() -> ctypes.CDLL:
             "fzp_batch_info": [vp, i32, ctypes.POINTER(PlanInfo)],
             "fzp_batch_metrics": [vp, i32, vp, vp, ctypes.POINTER(Metrics)],
             "fzp_batch_destroy": [vp],
+            "fzp_surrogate_create": [i32, i32, i32, i32, i32, ctypes.c_uint64, ctypes.POINTER(vp)],
+            "fzp_surrogate_params": [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t, i32],
+            "fzp_surrogate_infer": [vp, vp, i32, vp, vp],
+            "fzp_surrogate_grad": [vp, vp, vp, i32, vp, vp, vp],
+            "fzp_surrogate_train_step": [vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, vp, vp],
+            "fzp_surrogate_destroy": [vp],
             "fzp_profile_read": [vp, ctypes.POINTER(Profile)],
         }
         for name, args in sig.items():
@@ -110,6 +116,8 @@ def lib() -> ctypes.CDLL:
             fn.restype = ctypes.c_int
         L.fzp_last_error.restype = ctypes.c_char_p
         L.fzp_last_error.argtypes = []
+        L.fzp_surrogate_param_count.argtypes = [vp]
+        L.fzp_surrogate_param_count.restype = ctypes.c_size_t
         L.fzp_version.restype = ctypes.c_char_p
         L.fzp_version.argtypes = []
         _lib = L
@@ -248,6 +256,56 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             lib().fzp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SurrogateNet:
+    """fzp_surrogate_*: MLP n_in -> hidden x layers (SiLU) -> n_out, BF16 tensor-core
+    products with FP32 accumulation, FP32 masters, AdamW -- all in libfzp kernels."""
+
+    def __init__(self, n_in=8, hidden=512, layers=3, n_out=4114, max_batch=256, seed=0):
+        h = ctypes.c_void_p()
+        _check(lib().fzp_surrogate_create(n_in, hidden, layers, n_out, max_batch, seed, ctypes.byref(h)))
+        self._h = h
+        self.n_in, self.n_out, self.max_batch = n_in, n_out, max_batch
+        self.sizes = [n_in] + [hidden] * layers + [n_out]
+
+    @property
+    def param_count(self) -> int:
+        return int(lib().fzp_surrogate_param_count(self._h))
+
+    def get_params(self):
+        import numpy as np
+        buf = np.zeros(self.param_count, dtype=np.float32)
+        _check(lib().fzp_surrogate_params(self._h, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), buf.size, 0))
+        return buf
+
+    def set_params(self, vec):
+        import numpy as np
+        buf = np.ascontiguousarray(vec, dtype=np.float32)
+        assert buf.size == self.param_count
+        _check(lib().fzp_surrogate_params(self._h, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), buf.size, 1))
+
+    def infer(self, x, y, stream=None):
+        _check(lib().fzp_surrogate_infer(self._h, _ptr(x), x.shape[0], _ptr(y), _stream(stream)))
+
+    def grad(self, x, y, grad_out=None, loss_out=None, stream=None):
+        _check(lib().fzp_surrogate_grad(self._h, _ptr(x), _ptr(y), x.shape[0], _ptr(grad_out), _ptr(loss_out),
+                                        _stream(stream)))
+
+    def train_step(self, x, y, lr, weight_decay=0.0, loss_out=None, stream=None):
+        _check(lib().fzp_surrogate_train_step(self._h, _ptr(x), _ptr(y), x.shape[0], lr, weight_decay,
+                                              _ptr(loss_out), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fzp_surrogate_destroy(self._h)
             self._h = None
 
     def __del__(self):
