@@ -184,6 +184,7 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 Bluestein form")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     ws, rank, local = _dist()
@@ -306,6 +307,23 @@ def main():
            "note": "fzp_plan + fzp_propagate_roi + field to pinned host + fzp_metrics + fzp_plan_destroy"}
     plan.close()
 
+    # the plain FP32 Bluestein form on the same workload (the metric compares
+    # the split-BF16 dense form with it): one warm and one timed step
+    plain = None
+    if args.form == "dense" and not args.no_plain:
+        with fzp.Plan(**dict(params, form=fzp.FORM_BLUESTEIN, precision=fzp.PREC_FP32)) as pb:
+            pb.propagate_roi(0, N, U, stream=stream)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pb.propagate_roi(0, N, U, stream=stream)
+            mb = pb.metrics(U, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            pms = e0.elapsed_time(e1)
+        plain = {"form": "bluestein", "dtype": "f32", "value": N * N / (pms / 1e3) / 1e9, "unit": UNIT,
+                 "ms_per_step": pms, "fwhm_x": mb["fwhm_x"], "de_lobe": mb["de_lobe"]}
+
     if rank != 0:
         if pg:
             pg.destroy_process_group()
@@ -318,6 +336,9 @@ def main():
                       "l2": "256 MiB buffer written between steps (flush)"},
            "roofline": roof, "e2e": e2e, "gpu_launches": prof["kernel_launches"], "clocks": clocks,
            "metrics_last_step": {k: m[k] for k in ("fwhm_x", "de_lobe", "mtf_half_cut")}}
+    if plain:
+        out["plain_fp32"] = plain
+        out["speedup_vs_plain_fp32"] = value / plain["value"]
     if ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
     _print(out)

@@ -3,8 +3,8 @@
 // Autotuner: for FZP_PREC_AUTO_1E4 (any arithmetic whose ROI-intensity error is
 // <= 1e-4) it builds the candidate plans -- the split-BF16 dense form with two
 // accumulation-chunk lengths, and the FP32 Bluestein form -- times each on a
-// probe stripe of 512 central aperture rows (the rows with the most zone
-// boundaries), and keeps the fastest.  Deformed membranes have complex
+// probe stripe of central aperture rows sized to fill the GPU twice with dense
+// work items, and keeps the fastest.  Deformed membranes have complex
 // transmission, which only the Bluestein form supports.  Results are cached
 // per (N, M, deformed) for the process and, when FZP_TUNE_CACHE names a file,
 // in that file (one "key value..." line per problem).
@@ -94,7 +94,15 @@ static fzp_plan_t probe_candidate(const fzp_params& base, const Choice& c, doubl
             cudaEventCreate(&e1) == cudaSuccess;
   fzp_plan_info info;
   fzp_plan_info_get(plan, &info);
-  const int64_t j0 = std::max<int64_t>(0, info.c - 256), j1 = std::min<int64_t>(info.N, info.c + 256);
+  // probe stripe: enough rows for two full waves of dense work items (one item =
+  // 256 rows x one pair of 128-row kernel tiles) so that neither form is timed
+  // on an under-filled GPU; centred rows carry the most zone boundaries
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t pairs = std::max<int64_t>(1, (2 * (int64_t)p.M / 128 + 1) / 2);
+  const int64_t half = 128 * ((2 * sms + pairs - 1) / pairs);
+  const int64_t j0 = std::max<int64_t>(0, info.c - half), j1 = std::min<int64_t>(info.N, info.c + half);
   float t = 0;
   if (ok) ok = fzp_propagate_roi(plan, j0, j1, field, 0, nullptr) == FZP_OK;  // warm
   if (ok) {

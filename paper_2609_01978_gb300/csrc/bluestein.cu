@@ -31,7 +31,7 @@ namespace fzp {
 namespace {
 
 template <typename R> struct Traits;
-template <> struct Traits<float> { static constexpr int L2MAX = 8192; };
+template <> struct Traits<float> { static constexpr int L2MAX = 4096; };  // radix-16 pass kernel
 template <> struct Traits<double> { static constexpr int L2MAX = 4096; };
 
 __host__ __device__ inline int ilog2(int64_t v) { int r = 0; while ((1ll << r) < v) ++r; return r; }
@@ -96,7 +96,7 @@ struct RowArgs {
   void* Z;           // [rows][L1][L2]
   void* G;           // [rows][L1][M]
   const void* post;  // M, includes 1/L
-  const void* tw;    // twN/2 entries
+  const void* tw;    // twN entries: e^{-2 pi i t / twN}
   int twN;
   void* C1;          // [2M][c1_stride]
   int64_t c1_stride; // row length of C1
@@ -220,6 +220,162 @@ __global__ void __launch_bounds__(512) k_f2(RowArgs a, int mode) {
   }
 }
 
+// ---------------------------------------------------------------- FP32 pass F2, radix 16
+// L2 = 4096 = 16^3 points, 256 threads x 16 values in registers, Stockham
+// order (pass s, Ns = 16^s: x_r = in[j + 256 r] times W_{16 Ns}^{r k},
+// k = j mod Ns, 16-point DFT, y_q -> out[(j / Ns) 16 Ns + q Ns + k]).  The
+// 16-point DFT is 4 x 4 (two radix-4 layers with W_16^{ac} between); shared
+// memory is padded by one element per 16 against bank conflicts.
+constexpr int RL = 4096, RT = 256;
+__device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
+
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3, bool inv) {
+  const float2 s02 = make_float2(a0.x + a2.x, a0.y + a2.y), d02 = make_float2(a0.x - a2.x, a0.y - a2.y);
+  const float2 s13 = make_float2(a1.x + a3.x, a1.y + a3.y), d13 = make_float2(a1.x - a3.x, a1.y - a3.y);
+  const float2 t = inv ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);  // (+/-i) d13
+  a0 = make_float2(s02.x + s13.x, s02.y + s13.y);
+  a2 = make_float2(s02.x - s13.x, s02.y - s13.y);
+  a1 = make_float2(d02.x + t.x, d02.y + t.y);
+  a3 = make_float2(d02.x - t.x, d02.y - t.y);
+}
+
+// In place; afterwards y_q sits in v[4 (q % 4) + q / 4].
+__device__ __forceinline__ void dft16(float2 (&v)[16], bool inv) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a) dft4(v[a], v[a + 4], v[a + 8], v[a + 12], inv);
+  // W_16^{a c}, a, c in 1..3: cos / sin of 2 pi k / 16 for k = 1, 2, 3, 4, 6, 9
+  const float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f, c2 = 0.70710678118654752f;
+#pragma unroll
+  for (int a = 1; a < 4; ++a)
+#pragma unroll
+    for (int c = 1; c < 4; ++c) {
+      const int k = a * c;
+      float cs, sn;
+      switch (k) {
+        case 1: cs = c1; sn = s1; break;
+        case 2: cs = c2; sn = c2; break;
+        case 3: cs = s1; sn = c1; break;
+        case 4: cs = 0.f; sn = 1.f; break;
+        case 6: cs = -c2; sn = c2; break;
+        default: cs = -c1; sn = -s1; break;  // k = 9
+      }
+      if (!inv) sn = -sn;
+      float2& x = v[a + 4 * c];
+      x = make_float2(x.x * cs - x.y * sn, x.x * sn + x.y * cs);
+    }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) dft4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3], inv);
+}
+
+__device__ __forceinline__ float2 y_of(const float2 (&v)[16], int q) { return v[4 * (q & 3) + (q >> 2)]; }
+
+__device__ __forceinline__ void twiddle16(float2 (&v)[16], int k, int step, const float2* __restrict__ tw, bool inv) {
+#pragma unroll
+  for (int r = 1; r < 16; ++r) {
+    float2 w = __ldg(tw + r * k * step);
+    if (inv) w.y = -w.y;
+    v[r] = make_float2(v[r].x * w.x - v[r].y * w.y, v[r].x * w.y + v[r].y * w.x);
+  }
+}
+
+// mode 0: row transform; mode 1: forward FFT only, natural order -> Z row (table build).
+__global__ void __launch_bounds__(RT) k_f2_r16(RowArgs a, int mode) {
+  __shared__ float2 sm[RL + RL / 16];
+  const int j = threadIdx.x;
+  const int64_t k1 = blockIdx.x, r = blockIdx.y, row = a.j0 + r;
+  const float2* tw = reinterpret_cast<const float2*>(a.tw);
+  float2 v[16];
+  if (a.L1 == 1) {
+    const float2* pre = reinterpret_cast<const float2*>(a.pre);
+    const float2* vin = reinterpret_cast<const float2*>(a.vin);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int n = j + RT * q;
+      if (mode == 0) {
+        float2 x = aperture<float>(a, row, n);
+        if (x.x != 0.f || x.y != 0.f) x = cmul(x, pre[n]);
+        v[q] = x;
+      } else {
+        v[q] = vin[n];
+      }
+    }
+  } else {
+    const float2* Z = reinterpret_cast<const float2*>(a.Z) + r * a.L + k1 * RL;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = Z[j + RT * q];
+  }
+  // forward: passes Ns = 1, 16, 256
+  dft16(v, false);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) sm[pidx(j * 16 + q)] = y_of(v, q);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = sm[pidx(j + RT * q)];
+  __syncthreads();
+  twiddle16(v, j & 15, 16, tw, false);
+  dft16(v, false);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) sm[pidx((j >> 4) * 256 + q * 16 + (j & 15))] = y_of(v, q);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = sm[pidx(j + RT * q)];
+  __syncthreads();
+  twiddle16(v, j, 1, tw, false);
+  dft16(v, false);
+  if (mode == 1) {
+    float2* out = reinterpret_cast<float2*>(a.Z) + r * a.L + k1 * RL;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) out[q * 256 + j] = y_of(v, q);
+    return;
+  }
+  const float2* H = reinterpret_cast<const float2*>(a.H) + k1 * RL;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) sm[pidx(q * 256 + j)] = cmul(y_of(v, q), H[q * 256 + j]);
+  __syncthreads();
+  // inverse: same passes with conjugate twiddles
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = sm[pidx(j + RT * q)];
+  __syncthreads();
+  dft16(v, true);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) sm[pidx(j * 16 + q)] = y_of(v, q);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = sm[pidx(j + RT * q)];
+  __syncthreads();
+  twiddle16(v, j & 15, 16, tw, true);
+  dft16(v, true);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) sm[pidx((j >> 4) * 256 + q * 16 + (j & 15))] = y_of(v, q);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = sm[pidx(j + RT * q)];
+  twiddle16(v, j, 1, tw, true);
+  dft16(v, true);
+  // outputs m = q * 256 + j < M
+  if (a.L1 == 1) {
+    const float2* post = reinterpret_cast<const float2*>(a.post);
+    float* C1 = reinterpret_cast<float*>(a.C1);
+    const int64_t jl = row - a.c1_j0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int m = q * 256 + j;
+      if (m < a.M) {
+        const float2 z = cmul(y_of(v, q), post[m]);
+        C1[(int64_t)c1_row_re(m) * a.c1_stride + jl] = z.x;
+        C1[(int64_t)c1_row_im(m) * a.c1_stride + jl] = z.y;
+      }
+    }
+    return;
+  }
+  float2* G = reinterpret_cast<float2*>(a.G) + (r * a.L1 + k1) * a.M;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int m = q * 256 + j;
+    if (m < a.M) G[m] = cmul(y_of(v, q), twiddle<float>((k1 * m) & (a.L - 1), a.L, 1.0f));
+  }
+}
+
 // Sum over k1; tile of 32 rows x 32 m; writes C1 coalesced along rows.
 template <typename R>
 __global__ void __launch_bounds__(256) k_f3(RowArgs a) {
@@ -280,7 +436,7 @@ __global__ void k_tables(int64_t N, int M, int64_t L, int64_t c, double kappa, d
       h = cis_turns<R>(0.5 * delta * kk * kk);
     }
     reinterpret_cast<C*>(v)[t] = h;
-    if (t < twN / 2) reinterpret_cast<C*>(tw)[t] = twiddle<R>(t, twN, -1.0f);
+    if (t < twN) reinterpret_cast<C*>(tw)[t] = twiddle<R>(t, twN, -1.0f);
   }
 }
 
@@ -324,7 +480,7 @@ fzp_status layout_t(Plan& P, FormSizes* out) {
   const int twN = (int)b.L2;
   out->pre = sizeof(C) * P.N;
   out->H = sizeof(C) * b.L;
-  out->tab = sizeof(C) * (b.L + twN / 2 + P.M);
+  out->tab = sizeof(C) * (b.L + twN + P.M);
   out->Z = sizeof(C) * b.L * (b.L1 > 1 ? b.rows : 1);  // row 0 also serves the table build
   out->G = b.L1 > 1 ? sizeof(C) * b.L1 * P.M * b.rows : 0;
   static bool attrs = false;
@@ -343,7 +499,7 @@ fzp_status fill_tables_t(Plan& P, cudaStream_t s) {
   Bluestein& b = P.bs;
   const int twN = (int)b.L2;
   b.d_tw = reinterpret_cast<C*>(b.d_tab) + b.L;
-  b.d_post = reinterpret_cast<C*>(b.d_tw) + twN / 2;
+  b.d_post = reinterpret_cast<C*>(b.d_tw) + twN;
   k_tables<R><<<1024, 256, 0, s>>>(P.N, P.M, b.L, P.c, P.kappa, P.delta, b.d_pre, b.d_post, b.d_tab, b.d_tw, twN);
   FZP_CUDA_TRY(cudaGetLastError());
   // H = FFT_L(v) in the [k1][k2] order: F1 (table mode) + F2 (forward only) into Z row 0, then copy.
@@ -351,7 +507,8 @@ fzp_status fill_tables_t(Plan& P, cudaStream_t s) {
   a.j0 = 0;
   a.rows = 1;
   if (b.L1 > 1) k_f1<R><<<dim3((unsigned)(b.L2 / a.B), 1), 256, sizeof(C) * b.L1 * a.B, s>>>(a, 1);
-  k_f2<R><<<dim3((unsigned)b.L1, 1), 512, sizeof(C) * b.L2, s>>>(a, 1);
+  if (sizeof(R) == 4 && b.L2 == RL) k_f2_r16<<<dim3((unsigned)b.L1, 1), RT, 0, s>>>(a, 1);
+  else k_f2<R><<<dim3((unsigned)b.L1, 1), 512, sizeof(C) * b.L2, s>>>(a, 1);
   FZP_CUDA_TRY(cudaGetLastError());
   FZP_CUDA_TRY(cudaMemcpyAsync(b.d_H, b.d_Z, sizeof(C) * b.L, cudaMemcpyDeviceToDevice, s));
   P.launches += b.L1 > 1 ? 3 : 2;
@@ -386,13 +543,15 @@ fzp_status rows_t(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
     if (b.L1 > 1) {
       k_f1<R><<<dim3((unsigned)(b.L2 / a.B), (unsigned)rb), 256, sizeof(C) * b.L1 * a.B, s>>>(a, 0);
       prof_begin(P, s);
-      k_f2<R><<<dim3((unsigned)b.L1, (unsigned)rb), 512, sizeof(C) * b.L2, s>>>(a, 0);
+      if (sizeof(R) == 4 && b.L2 == RL) k_f2_r16<<<dim3((unsigned)b.L1, (unsigned)rb), RT, 0, s>>>(a, 0);
+      else k_f2<R><<<dim3((unsigned)b.L1, (unsigned)rb), 512, sizeof(C) * b.L2, s>>>(a, 0);
       prof_end(P, s);
       k_f3<R><<<dim3((unsigned)(P.M / 32), (unsigned)((rb + 31) / 32)), 256, 0, s>>>(a);
       P.launches += 3;
     } else {
       prof_begin(P, s);
-      k_f2<R><<<dim3(1, (unsigned)rb), 512, sizeof(C) * b.L2, s>>>(a, 0);
+      if (sizeof(R) == 4 && b.L2 == RL) k_f2_r16<<<dim3(1, (unsigned)rb), RT, 0, s>>>(a, 0);
+      else k_f2<R><<<dim3(1, (unsigned)rb), 512, sizeof(C) * b.L2, s>>>(a, 0);
       prof_end(P, s);
       P.launches += 1;
     }
