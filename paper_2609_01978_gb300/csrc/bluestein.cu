@@ -40,11 +40,11 @@ __device__ __forceinline__ int brev(int v, int bits) { return (int)(__brev((unsi
 
 template <typename C> __device__ __forceinline__ C conjc(C a) { a.y = -a.y; return a; }
 
-// Batched in-place radix-2 DIT: `batch` transforms of length n = 2^logn stored
-// contiguously; input in bit-reversed order, output natural; forward sign.
+// Batched in-place radix-2 DIT: `batch` transforms of length n = 2^logn, column
+// c at x + c * colstride; input in bit-reversed order, output natural; forward sign.
 // tw[t] = e^{-2 pi i t / twN}.
 template <typename C>
-__device__ void dit(C* x, int logn, int batch, const C* __restrict__ tw, int twN) {
+__device__ void dit(C* x, int logn, int batch, const C* __restrict__ tw, int twN, int colstride) {
   const int n = 1 << logn, nb = (n >> 1) * batch;
   for (int s = 1; s <= logn; ++s) {
     const int half = 1 << (s - 1);
@@ -52,7 +52,7 @@ __device__ void dit(C* x, int logn, int batch, const C* __restrict__ tw, int twN
     for (int t = threadIdx.x; t < nb; t += blockDim.x) {
       const int col = t >> (logn - 1), b = t & ((n >> 1) - 1);
       const int k = b & (half - 1);
-      const int i0 = col * n + ((b >> (s - 1)) << s) + k, i1 = i0 + half;
+      const int i0 = col * colstride + ((b >> (s - 1)) << s) + k, i1 = i0 + half;
       const C w = tw[k * stride];
       const C a = x[i0], v = cmul(x[i1], w);
       x[i0] = cadd(a, v);
@@ -97,6 +97,7 @@ struct RowArgs {
   void* G;           // [rows][L1][M]
   const void* post;  // M, includes 1/L
   const void* tw;    // twN entries: e^{-2 pi i t / twN}
+  const void* twL;   // 4096 entries: e^{-2 pi i t / L}
   int twN;
   void* C1;          // [2M][c1_stride]
   int64_t c1_stride; // row length of C1
@@ -125,6 +126,24 @@ __device__ __forceinline__ typename Cplx<R>::T aperture(const RowArgs& a, int64_
   return cis_turns<R>(2.0 * wz * a.inv_lambda);  // phi / (2 pi) = 2 w / lambda
 }
 
+// e^{sign 2 pi i t / L} for 0 <= t < L = L1 * L2 from two tables:
+// t = th * 4096 + tl, W_L^t = W_{L1}^{th} W_L^{tl}, W_{L1}^{th} = tw[th * (twN / L1)].
+template <typename R>
+__device__ __forceinline__ typename Cplx<R>::T twiddle_L(const RowArgs& a, int64_t t, bool conj) {
+  using C = typename Cplx<R>::T;
+  if (a.L <= 4096) {
+    C w = reinterpret_cast<const C*>(a.twL)[t];
+    if (conj) w.y = -w.y;
+    return w;
+  }
+  const int64_t th = t >> 12, tl = t & 4095;
+  C w1 = reinterpret_cast<const C*>(a.tw)[th * (a.twN / a.L1)];
+  C w2 = reinterpret_cast<const C*>(a.twL)[tl];
+  C w = cmul(w1, w2);
+  if (conj) w.y = -w.y;
+  return w;
+}
+
 // mode 0: generate y = aperture * pre; mode 1: read the table input `vin`.
 template <typename R>
 __global__ void __launch_bounds__(256) k_f1(RowArgs a, int mode) {
@@ -149,16 +168,16 @@ __global__ void __launch_bounds__(256) k_f1(RowArgs a, int mode) {
     } else {
       x = vin[n];
     }
-    sm[b * L1 + brev(n1, a.logL1)] = x;
+    sm[b * (L1 + 1) + brev(n1, a.logL1)] = x;  // odd column stride: no bank conflicts across columns
   }
   __syncthreads();
-  dit(sm, a.logL1, B, reinterpret_cast<const C*>(a.tw), a.twN);
+  dit(sm, a.logL1, B, reinterpret_cast<const C*>(a.tw), a.twN, L1 + 1);
   C* Z = reinterpret_cast<C*>(a.Z) + r * a.L;
   for (int t = threadIdx.x; t < L1 * B; t += blockDim.x) {
     const int k1 = t / B, b = t % B;
     const int64_t n2 = n2_0 + b;
-    const C w = twiddle<R>((n2 * k1) & (a.L - 1), a.L, -1.0f);
-    Z[(int64_t)k1 * a.L2 + n2] = cmul(sm[b * L1 + k1], w);
+    const C w = twiddle_L<R>(a, n2 * k1, false);
+    Z[(int64_t)k1 * a.L2 + n2] = cmul(sm[b * (L1 + 1) + k1], w);
   }
 }
 
@@ -191,7 +210,7 @@ __global__ void __launch_bounds__(512) k_f2(RowArgs a, int mode) {
     for (int n = threadIdx.x; n < L2; n += blockDim.x) sm[brev(n, a.logL2)] = Z[n];
   }
   __syncthreads();
-  dit(sm, a.logL2, 1, tw, a.twN);
+  dit(sm, a.logL2, 1, tw, a.twN, (int)a.L2);
   if (mode == 1) {
     C* out = reinterpret_cast<C*>(a.Z) + r * a.L + k1 * a.L2;
     for (int k = threadIdx.x; k < L2; k += blockDim.x) out[k] = sm[k];
@@ -215,8 +234,7 @@ __global__ void __launch_bounds__(512) k_f2(RowArgs a, int mode) {
   }
   C* G = reinterpret_cast<C*>(a.G) + (r * a.L1 + k1) * a.M;
   for (int m = threadIdx.x; m < a.M; m += blockDim.x) {
-    const C w = twiddle<R>((k1 * m) & (a.L - 1), a.L, 1.0f);
-    G[m] = cmul(sm[brev(m, a.logL2)], w);
+    G[m] = cmul(sm[brev(m, a.logL2)], twiddle_L<R>(a, (k1 * m) & (a.L - 1), true));
   }
 }
 
@@ -372,7 +390,7 @@ __global__ void __launch_bounds__(RT) k_f2_r16(RowArgs a, int mode) {
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
     const int m = q * 256 + j;
-    if (m < a.M) G[m] = cmul(y_of(v, q), twiddle<float>((k1 * m) & (a.L - 1), a.L, 1.0f));
+    if (m < a.M) G[m] = cmul(y_of(v, q), twiddle_L<float>(a, (k1 * m) & (a.L - 1), true));
   }
 }
 
@@ -409,7 +427,7 @@ __global__ void __launch_bounds__(256) k_f3(RowArgs a) {
 // Tables: pre(i), post(m)/L, convolution chirp v (length L), twiddles.
 template <typename R>
 __global__ void k_tables(int64_t N, int M, int64_t L, int64_t c, double kappa, double delta, void* pre, void* post,
-                         void* v, void* tw, int twN) {
+                         void* v, void* tw, int twN, void* twL) {
   using C = typename Cplx<R>::T;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < L; t += stride) {
@@ -437,6 +455,7 @@ __global__ void k_tables(int64_t N, int M, int64_t L, int64_t c, double kappa, d
     }
     reinterpret_cast<C*>(v)[t] = h;
     if (t < twN) reinterpret_cast<C*>(tw)[t] = twiddle<R>(t, twN, -1.0f);
+    if (t < 4096) reinterpret_cast<C*>(twL)[t] = twiddle<R>(t, L, -1.0f);
   }
 }
 
@@ -449,7 +468,7 @@ static RowArgs make_args(const Plan& P) {
   {
     const int64_t csz = P.precision == FZP_PREC_FP64 ? 16 : 8;
     int64_t B = 16;
-    while (B > 1 && B * b.L1 * csz > 65536) B >>= 1;
+    while (B > 1 && B * (b.L1 + 1) * csz > 65536) B >>= 1;
     a.B = (int)std::min<int64_t>(B, b.L2);
   }
   a.has_deform = P.has_deform ? 1 : 0;
@@ -457,6 +476,7 @@ static RowArgs make_args(const Plan& P) {
   a.dx = P.dx; a.R = P.R; a.inv_lambda = 1.0 / P.lambda;
   a.pre = b.d_pre; a.H = b.d_H; a.Z = b.d_Z; a.G = b.d_G; a.post = b.d_post; a.tw = b.d_tw;
   a.twN = (int)b.L2;
+  a.twL = b.d_twL;
   a.c1_stride = P.chunk_rows;
   a.C1 = P.precision == FZP_PREC_FP64 ? (void*)P.d_C1d : (void*)P.d_C1;
   a.vin = b.d_tab;
@@ -480,7 +500,7 @@ fzp_status layout_t(Plan& P, FormSizes* out) {
   const int twN = (int)b.L2;
   out->pre = sizeof(C) * P.N;
   out->H = sizeof(C) * b.L;
-  out->tab = sizeof(C) * (b.L + twN + P.M);
+  out->tab = sizeof(C) * (b.L + twN + P.M + 4096);
   out->Z = sizeof(C) * b.L * (b.L1 > 1 ? b.rows : 1);  // row 0 also serves the table build
   out->G = b.L1 > 1 ? sizeof(C) * b.L1 * P.M * b.rows : 0;
   static bool attrs = false;
@@ -500,13 +520,15 @@ fzp_status fill_tables_t(Plan& P, cudaStream_t s) {
   const int twN = (int)b.L2;
   b.d_tw = reinterpret_cast<C*>(b.d_tab) + b.L;
   b.d_post = reinterpret_cast<C*>(b.d_tw) + twN;
-  k_tables<R><<<1024, 256, 0, s>>>(P.N, P.M, b.L, P.c, P.kappa, P.delta, b.d_pre, b.d_post, b.d_tab, b.d_tw, twN);
+  b.d_twL = reinterpret_cast<C*>(b.d_post) + P.M;
+  k_tables<R><<<1024, 256, 0, s>>>(P.N, P.M, b.L, P.c, P.kappa, P.delta, b.d_pre, b.d_post, b.d_tab, b.d_tw, twN,
+                                   b.d_twL);
   FZP_CUDA_TRY(cudaGetLastError());
   // H = FFT_L(v) in the [k1][k2] order: F1 (table mode) + F2 (forward only) into Z row 0, then copy.
   RowArgs a = make_args(P);
   a.j0 = 0;
   a.rows = 1;
-  if (b.L1 > 1) k_f1<R><<<dim3((unsigned)(b.L2 / a.B), 1), 256, sizeof(C) * b.L1 * a.B, s>>>(a, 1);
+  if (b.L1 > 1) k_f1<R><<<dim3((unsigned)(b.L2 / a.B), 1), 256, sizeof(C) * (b.L1 + 1) * a.B, s>>>(a, 1);
   if (sizeof(R) == 4 && b.L2 == RL) k_f2_r16<<<dim3((unsigned)b.L1, 1), RT, 0, s>>>(a, 1);
   else k_f2<R><<<dim3((unsigned)b.L1, 1), 512, sizeof(C) * b.L2, s>>>(a, 1);
   FZP_CUDA_TRY(cudaGetLastError());
@@ -541,7 +563,7 @@ fzp_status rows_t(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
     a.j0 = j0 + r0;
     a.rows = rb;
     if (b.L1 > 1) {
-      k_f1<R><<<dim3((unsigned)(b.L2 / a.B), (unsigned)rb), 256, sizeof(C) * b.L1 * a.B, s>>>(a, 0);
+      k_f1<R><<<dim3((unsigned)(b.L2 / a.B), (unsigned)rb), 256, sizeof(C) * (b.L1 + 1) * a.B, s>>>(a, 0);
       prof_begin(P, s);
       if (sizeof(R) == 4 && b.L2 == RL) k_f2_r16<<<dim3((unsigned)b.L1, (unsigned)rb), RT, 0, s>>>(a, 0);
       else k_f2<R><<<dim3((unsigned)b.L1, (unsigned)rb), 512, sizeof(C) * b.L2, s>>>(a, 0);

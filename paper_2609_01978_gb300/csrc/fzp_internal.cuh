@@ -130,6 +130,7 @@ struct Bluestein {
   void* d_tab = nullptr;  // table block: chirp v (L) | twiddles (L2/2) | post (M)
   void* d_tw = nullptr;   // into d_tab
   void* d_post = nullptr; // into d_tab
+  void* d_twL = nullptr;  // into d_tab: e^{-2 pi i t / L}, t < 4096
   int64_t rows = 0;       // rows per batch of the workspace
 };
 
