@@ -109,6 +109,10 @@ typedef struct fzp_params {
                           D = 0.25 m; it grows in proportion to this length)       */
   int32_t row_batch;   /* Bluestein: aperture rows per FFT pass launch; 0 -> rows of a
                           1 GiB transform workspace                               */
+  int32_t cluster;     /* dense: CTAs of a thread-block cluster that share each
+                          generated mask tile through distributed shared memory,
+                          each generating its share of the rows (1 or 2; 0 -> 1:
+                          at D = 0.25 m, 2 measured 20 % slower)                  */
 } fzp_params;
 
 /* Opaque plan: geometry, zone-threshold table, chirp / kernel tables and the
@@ -135,6 +139,8 @@ typedef struct fzp_plan_info {
   int32_t promote;       /* dense: K blocks per tensor-memory accumulation chunk   */
   int32_t row_batch;     /* Bluestein: aperture rows per FFT pass launch           */
   int64_t chunk_rows;    /* aperture rows per row-pass chunk                       */
+  int32_t cluster;       /* dense: CTAs per cluster sharing each mask tile         */
+  int32_t reserved;
 } fzp_plan_info;
 
 /* Metrics of Fig. 2 Stage 4 / Fig. 18 Stage 5. */

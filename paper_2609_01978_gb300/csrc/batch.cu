@@ -39,7 +39,7 @@ void release_plan(Plan* P);
 namespace {
 
 struct Choice {
-  int form, precision, promote, row_batch;
+  int form, precision, promote, row_batch, cluster;
   double ms_probe;
 };
 
@@ -62,7 +62,8 @@ void tune_load() {
   if (!fh) return;
   char key[96];
   Choice c;
-  while (fscanf(fh, "%95s %d %d %d %d %lf", key, &c.form, &c.precision, &c.promote, &c.row_batch, &c.ms_probe) == 6)
+  while (fscanf(fh, "%95s %d %d %d %d %d %lf", key, &c.form, &c.precision, &c.promote, &c.row_batch, &c.cluster,
+                &c.ms_probe) == 7)
     g_tune[key] = c;
   fclose(fh);
 }
@@ -73,7 +74,8 @@ void tune_store(const std::string& key, const Choice& c) {
   if (!path) return;
   FILE* fh = fopen(path, "a");
   if (!fh) return;
-  fprintf(fh, "%s %d %d %d %d %.6f\n", key.c_str(), c.form, c.precision, c.promote, c.row_batch, c.ms_probe);
+  fprintf(fh, "%s %d %d %d %d %d %.6f\n", key.c_str(), c.form, c.precision, c.promote, c.row_batch, c.cluster,
+          c.ms_probe);
   fclose(fh);
 }
 
@@ -86,6 +88,7 @@ static fzp_plan_t probe_candidate(const fzp_params& base, const Choice& c, doubl
   p.precision = c.precision;
   p.promote = c.promote;
   p.row_batch = c.row_batch;
+  p.cluster = c.cluster;
   fzp_plan_t plan = nullptr;
   if (fzp_plan(&p, &plan) != FZP_OK) return nullptr;
   void* field = nullptr;
@@ -143,15 +146,17 @@ fzp_status autotune(const fzp_params* in, fzp_params* chosen, fzp_plan_t* keep) 
     chosen->precision = hit->second.precision;
     chosen->promote = hit->second.promote;
     chosen->row_batch = hit->second.row_batch;
+    chosen->cluster = hit->second.cluster;
     if (keep) return fzp_plan(chosen, keep);
     return FZP_OK;
   }
   std::vector<Choice> cands;
   if (!deformed) {
-    cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 128, 0, 0});
-    cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 256, 0, 0});
+    cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 128, 0, 1, 0});
+    cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 256, 0, 1, 0});
+    cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 128, 0, 2, 0});
   }
-  cands.push_back({FZP_FORM_BLUESTEIN, FZP_PREC_FP32, 0, 0, 0});
+  cands.push_back({FZP_FORM_BLUESTEIN, FZP_PREC_FP32, 0, 0, 0, 0});
   fzp_plan_t best = nullptr;
   Choice bc{};
   double bms = 1e300;
@@ -175,6 +180,7 @@ fzp_status autotune(const fzp_params* in, fzp_params* chosen, fzp_plan_t* keep) 
   chosen->precision = bc.precision;
   chosen->promote = bc.promote;
   chosen->row_batch = bc.row_batch;
+  chosen->cluster = bc.cluster;
   if (keep) *keep = best;
   else fzp_plan_destroy(best);
   return FZP_OK;
@@ -243,7 +249,7 @@ fzp_status fzp_batch_plan(const fzp_params* params, int n, fzp_batch_t* out) {
     if (st != FZP_OK) { batch_release(b); return st; }
     mx.pre = std::max(mx.pre, z.pre); mx.H = std::max(mx.H, z.H); mx.tab = std::max(mx.tab, z.tab);
     mx.Z = std::max(mx.Z, z.Z); mx.G = std::max(mx.G, z.G); mx.A = std::max(mx.A, z.A);
-    const size_t rowsC1 = (size_t)((2 * (int64_t)P->M + 255) / 256 * 256) * (size_t)P->chunk_rows;
+    const size_t rowsC1 = (size_t)((2 * (int64_t)P->M + 511) / 512 * 512) * (size_t)P->chunk_rows;
     if (P->precision == FZP_PREC_FP64) c1d = std::max(c1d, rowsC1 * 8);
     else c1 = std::max(c1, rowsC1 * 4);
     uacc = std::max(uacc, (size_t)P->M * P->M * sizeof(double2));

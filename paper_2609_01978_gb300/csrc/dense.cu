@@ -51,7 +51,9 @@ constexpr int A_BYTES = TILES * 2 * SUB;  // 32 KiB per stage: [t0 hi][t1 hi][t0
 constexpr int B_BYTES = BN * BK * 2;      // 16 KiB per stage
 constexpr int EPI_WARPS = 8;           // warps 0-7: epilogue (tile = warp / 4)
 constexpr int LOAD_WARP = 8, MMA_WARP = 9, GEN_WARP0 = 10;
-constexpr int NUM_THREADS = 18 * 32;
+// CTAs per cluster sharing each generated mask tile: each generates BN / CL rows
+template <int CL> constexpr int gen_warps() { return 8 / CL; }
+template <int CL> constexpr int num_threads() { return (GEN_WARP0 + gen_warps<CL>()) * 32; }
 constexpr int TMEM_COLS = 512;         // two 128 x 256 FP32 accumulators
 constexpr int ERR_TIMEOUT_BASE = 100;
 
@@ -61,7 +63,7 @@ struct DenseArgs {
   int64_t kblocks;          // ceil(N / BK)
   int64_t j_begin, j_end;   // aperture rows of this launch [j_begin, j_end)
   int64_t n_stripes;        // ceil((j_end - j_begin) / BN)
-  int npairs;               // kernel tile pairs (items per stripe)
+  int npairs;               // kernel tile pairs (items per stripe; a multiple of the cluster size)
   int promote;              // stages per accumulation chunk
   int hi_only;              // 1: BF16 kernel (hi) only
   const uint8_t* A;         // pre-swizzled kernel tiles, [pair][kb][t0hi t1hi t0lo t1lo]
@@ -190,7 +192,13 @@ __device__ __forceinline__ void expand_bits(uint32_t bits, uint32_t (&w)[16]) {
 }
 
 // ---------------------------------------------------------------- kernel
-__global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
+// Work units: unit u = (tile-pair group pu = u / n_stripes, stripe s = u % n_stripes);
+// CTA rank rk of a cluster of CL takes pair pu * CL + rk.  With CL = 2 both CTAs
+// of a cluster work on the same stripe and each generates half of its mask rows;
+// each half is copied to the peer's shared memory (distributed shared memory) by
+// one bulk copy per stage.
+template <int CL>
+__global__ void __launch_bounds__(num_threads<CL>(), 1) k_dense(DenseArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = base;                     // STAGES x 32 KiB
@@ -204,13 +212,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
   uint64_t* drain = accEmpty + 1;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(drain + 1);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 2);
+  volatile int* gen_ok = reinterpret_cast<volatile int*>(drain + 3);  // generator warps' common decision
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&fullA[s], 1);
-      mbar_init(&fullB[s], 8);
-      mbar_init(&empty[s], 1);
+      // mask rows: 8 local generator warps (CL = 1), or 4 local warps + the
+      // expect-tx arrival for the peer's half, delivered by a bulk copy (CL = 2)
+      mbar_init(&fullB[s], CL > 1 ? 5 : 8);
+      mbar_init(&empty[s], CL);  // MMA completion of every CTA that reads rows this CTA writes
     }
     mbar_init(accFull, 1);
     mbar_init(accEmpty, EPI_WARPS);
@@ -228,8 +239,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  const uint32_t rk = CL > 1 ? cluster_rank() : 0u;
+  if (CL > 1) cluster_sync();  // peers' barriers are initialised before any remote arrive
 
-  const int64_t n_items = a.n_stripes * a.npairs;
+  const int64_t n_items = a.n_stripes * (a.npairs / CL);  // units of this cluster
+  const int64_t u0 = blockIdx.x / CL, ustep = gridDim.x / CL;
   const int64_t nkb = a.kblocks;
   const int64_t nchunk = (nkb + a.promote - 1) / a.promote;
   const uint32_t a_bytes = a.hi_only ? A_BYTES / 2 : A_BYTES;
@@ -242,11 +256,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
       int last[STAGES];
 #pragma unroll
       for (int s2 = 0; s2 < STAGES; ++s2) last[s2] = -1;
-      for (int64_t it = blockIdx.x; it < n_items && !*abort_flag; it += gridDim.x) {
-        const int64_t pr = it / a.n_stripes;
+      for (int64_t it = u0; it < n_items && !*abort_flag; it += ustep) {
+        const int64_t pr = (it / a.n_stripes) * CL + rk;
         const uint8_t* Ap = a.A + pr * nkb * A_BYTES;
         for (int64_t kb = 0; kb < nkb; ++kb) {
-          if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 1)) break;
+          if (!(CL > 1 ? mbar_wait_cl(&empty[stage], phase ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 1)
+                       : mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 1)))
+            break;
           mbar_arrive_tx(&fullA[stage], a_bytes);
           bulk_g2s(sA + stage * A_BYTES, Ap + kb * A_BYTES, a_bytes, &fullA[stage]);
           last[stage] = (int)phase;
@@ -270,7 +286,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
       int stage = 0;
       uint32_t phase = 0, accph = 0;
       bool ok = true;
-      for (int64_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+      for (int64_t it = u0; it < n_items && ok; it += ustep) {
         for (int64_t ch = 0; ch < nchunk && ok; ++ch) {
           // the epilogue has drained both accumulators of the previous chunk
           if (!mbar_wait(accEmpty, accph ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 2)) { ok = false; break; }
@@ -278,7 +294,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
           const int64_t kb0 = ch * a.promote, kb1 = kb0 + a.promote < nkb ? kb0 + a.promote : nkb;
           for (int64_t kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait(&fullA[stage], phase, abort_flag, a.err, ERR_TIMEOUT_BASE + 3) ||
-                !mbar_wait(&fullB[stage], phase, abort_flag, a.err, ERR_TIMEOUT_BASE + 4)) {
+                !(CL > 1 ? mbar_wait_cl(&fullB[stage], phase, abort_flag, a.err, ERR_TIMEOUT_BASE + 4)
+                         : mbar_wait(&fullB[stage], phase, abort_flag, a.err, ERR_TIMEOUT_BASE + 4))) {
               ok = false;
               break;
             }
@@ -298,7 +315,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
                 }
               }
             }
-            mma_commit(&empty[stage]);
+            if (CL > 1) mma_commit_mc(&empty[stage], (uint16_t)((1u << CL) - 1u));
+            else mma_commit(&empty[stage]);
             if (++stage == STAGES) { stage = 0; phase ^= 1; }
           }
           if (!ok) break;
@@ -313,35 +331,89 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
       }
     }
   } else if (warp >= GEN_WARP0) {
-    // ---------------- mask generators: thread g owns aperture row j_tile + g
-    const int g = threadIdx.x - GEN_WARP0 * 32;  // 0..255
+    // ---------------- mask generators: row (rk * BN/CL + g) of the unit's stripe
+    const int g = threadIdx.x - GEN_WARP0 * 32;  // 0 .. BN/CL - 1
+    const int row = (int)rk * (BN / CL) + g;
     int stage = 0;
     uint32_t phase = 0;
-    // 64-byte swizzle, K-major: row g at (g/8)*512 + (g%8)*64, 16-byte chunk q at q ^ ((g%8)/2)
-    uint8_t* rowbase0 = sB + (g >> 3) * 512 + (g & 7) * 64;
-    const int sw = (g & 7) >> 1;
-    for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-      if (__shfl_sync(0xffffffffu, *abort_flag, 0)) break;
-      const int64_t s = it % a.n_stripes;
-      Walker w;
-      walker_init(w, a.j_begin + s * BN + g, a.j_end, a.mg);
-      uint32_t state = 0;
-      bool ok = true;
-      for (int64_t kb = 0; kb < nkb; ++kb) {
-        if (!warp_wait(&empty[stage], phase ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 5)) { ok = false; break; }
-        const uint32_t bits = walker_bits(w, kb * BK, state, a.mg.thr);
-        uint8_t* rowp = rowbase0 + stage * B_BYTES;
-        uint32_t wd[16];
-        expand_bits(bits, wd);
+    // 64-byte swizzle, K-major: row at (row/8)*512 + (row%8)*64, 16-byte chunk q at q ^ ((row%8)/2)
+    uint8_t* rowbase0 = sB + (row >> 3) * 512 + (row & 7) * 64;
+    const int sw = (row & 7) >> 1;
+    if constexpr (CL == 1) {
+      for (int64_t it = u0; it < n_items; it += ustep) {
+        if (__shfl_sync(0xffffffffu, *abort_flag, 0)) break;
+        const int64_t s = it % a.n_stripes;
+        Walker w;
+        walker_init(w, a.j_begin + s * BN + row, a.j_end, a.mg);
+        uint32_t state = 0;
+        bool ok = true;
+        for (int64_t kb = 0; kb < nkb; ++kb) {
+          if (!warp_wait(&empty[stage], phase ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 5)) { ok = false; break; }
+          const uint32_t bits = walker_bits(w, kb * BK, state, a.mg.thr);
+          uint8_t* rowp = rowbase0 + stage * B_BYTES;
+          uint32_t wd[16];
+          expand_bits(bits, wd);
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          *reinterpret_cast<uint4*>(rowp + ((q ^ sw) << 4)) = make_uint4(wd[4 * q], wd[4 * q + 1], wd[4 * q + 2], wd[4 * q + 3]);
-        fence_proxy_async();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&fullB[stage]);
-        if (++stage == STAGES) { stage = 0; phase ^= 1; }
+          for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4*>(rowp + ((q ^ sw) << 4)) = make_uint4(wd[4 * q], wd[4 * q + 1], wd[4 * q + 2], wd[4 * q + 3]);
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&fullB[stage]);
+          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+        }
+        if (!ok) break;
       }
-      if (!ok) break;
+    } else {
+      // The 4 generator warps act together (named barrier 1): thread g = 0 waits
+      // for the stage and publishes the decision, all rows are written to this
+      // CTA's half of the tile (8 KiB, contiguous), then g = 0 sends the half to
+      // the peer with one bulk copy that completes on the peer's fullB barrier.
+      constexpr int GT = BN / CL;  // generator threads
+      constexpr uint32_t HALF = B_BYTES / CL;
+      bool ok = true;
+      int last[STAGES];  // phase of the last peer copy expected on each stage (thread g = 0)
+#pragma unroll
+      for (int s2 = 0; s2 < STAGES; ++s2) last[s2] = -1;
+      for (int64_t it = u0; it < n_items && ok; it += ustep) {
+        const int64_t s = it % a.n_stripes;
+        Walker w;
+        walker_init(w, a.j_begin + s * BN + row, a.j_end, a.mg);
+        uint32_t state = 0;
+        for (int64_t kb = 0; kb < nkb; ++kb) {
+          if (g == 0) *gen_ok = mbar_wait_cl(&empty[stage], phase ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 5) ? 1 : 0;
+          named_bar_sync(1, GT);
+          ok = *gen_ok != 0;
+          if (!ok) break;
+          const uint32_t bits = walker_bits(w, kb * BK, state, a.mg.thr);
+          uint8_t* rowp = rowbase0 + stage * B_BYTES;
+          uint32_t wd[16];
+          expand_bits(bits, wd);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4*>(rowp + ((q ^ sw) << 4)) = make_uint4(wd[4 * q], wd[4 * q + 1], wd[4 * q + 2], wd[4 * q + 3]);
+          fence_proxy_async();
+          named_bar_sync(1, GT);
+          if (g == 0) {
+            uint8_t* half = sB + stage * B_BYTES + rk * HALF;
+            mbar_arrive_tx(&fullB[stage], HALF);  // the peer's half lands here
+            bulk_s2peer(mapa(smem_u32(half), rk ^ 1u), half, HALF, mapa(smem_u32(&fullB[stage]), rk ^ 1u));
+            last[stage] = (int)phase;
+          }
+          if (lane == 0) mbar_arrive(&fullB[stage]);
+          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+        }
+      }
+      if (g == 0 && *abort_flag) {
+        // after an abort the peer's copies already issued must land before this
+        // CTA's shared memory is released (bounded: the peer may have stopped first)
+#pragma unroll
+        for (int s2 = 0; s2 < STAGES; ++s2) {
+          if (last[s2] < 0) continue;
+          const uint64_t t0 = gtimer();
+          while (!mbar_try(&fullB[s2], (uint32_t)last[s2]) && gtimer() - t0 < WAIT_NS) {
+          }
+        }
+      }
     }
   } else {
     // ---------------- epilogue: warp w drains tile w/4, TMEM lanes 32(w%4)..+31
@@ -349,8 +421,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
     const int r = (warp & 3) * 32 + lane;  // kernel row within the tile
     uint32_t accph = 0;
     bool ok = true;
-    for (int64_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
-      const int64_t pr = it / a.n_stripes;
+    for (int64_t it = u0; it < n_items && ok; it += ustep) {
+      const int64_t pr = (it / a.n_stripes) * CL + rk;
       const int64_t s = it % a.n_stripes;
       float* crow = a.C1 + ((pr * TILES + q) * BM + r) * a.c1_stride + (a.j_begin + s * BN - a.c1_j0);
       for (int64_t ch = 0; ch < nchunk; ++ch) {
@@ -388,6 +460,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
+  // no CTA leaves while its peer may still write its shared memory or arrive on
+  // its barriers (every wait above is bounded, so both CTAs get here)
+  if (CL > 1) cluster_sync();
 }
 
 // ---------------------------------------------------------------- kernel table
@@ -461,15 +536,17 @@ fzp_status dense_layout(Plan& P, FormSizes* out) {
   Dense& d = P.dn;
   d.kblocks = (P.N + BK - 1) / BK;
   d.ntiles = 2 * P.M / BM;
-  const int npairs = (d.ntiles + TILES - 1) / TILES;
+  d.npairs = ((d.ntiles + TILES - 1) / TILES + 1) / 2 * 2;  // padded to an even count (zero pair)
   d.promote_kblocks = P.promote_req > 0 ? P.promote_req : 128;  // 4096 samples per TMEM chunk
+  d.cluster = P.cluster_req == 2 ? 2 : 1;
   int dev = 0;
   FZP_CUDA_TRY(cudaGetDevice(&dev));
   FZP_CUDA_TRY(cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev));
-  out->A = (size_t)npairs * (size_t)d.kblocks * A_BYTES;
+  out->A = (size_t)d.npairs * (size_t)d.kblocks * A_BYTES;
   static bool attrs = false;
   if (!attrs) {
-    FZP_CUDA_TRY(cudaFuncSetAttribute(k_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem_bytes()));
+    FZP_CUDA_TRY(cudaFuncSetAttribute(k_dense<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem_bytes()));
+    FZP_CUDA_TRY(cudaFuncSetAttribute(k_dense<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem_bytes()));
     attrs = true;
   }
   return FZP_OK;
@@ -477,8 +554,7 @@ fzp_status dense_layout(Plan& P, FormSizes* out) {
 
 fzp_status dense_fill_tables(Plan& P, cudaStream_t s) {
   Dense& d = P.dn;
-  const int npairs = (d.ntiles + TILES - 1) / TILES;
-  k_build_A<<<8 * d.num_sms, 256, 0, s>>>(P.M, P.N, d.kblocks, npairs, P.c, P.kappa, P.delta,
+  k_build_A<<<8 * d.num_sms, 256, 0, s>>>(P.M, P.N, d.kblocks, d.npairs, P.c, P.kappa, P.delta,
                                           reinterpret_cast<uint8_t*>(d.d_A));
   P.launches += 1;
   FZP_CUDA_TRY(cudaGetLastError());
@@ -510,7 +586,9 @@ fzp_status dense_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
   a.j_begin = j0;
   a.j_end = j0 + rows;
   a.n_stripes = (rows + BN - 1) / BN;
-  a.npairs = (d.ntiles + TILES - 1) / TILES;
+  const int CL = d.cluster;
+  const int used_pairs = (d.ntiles + TILES - 1) / TILES;
+  a.npairs = CL == 2 ? d.npairs : used_pairs;
   a.promote = d.promote_kblocks;
   a.hi_only = P.precision == FZP_PREC_BF16 ? 1 : 0;
   a.A = reinterpret_cast<const uint8_t*>(d.d_A);
@@ -518,11 +596,28 @@ fzp_status dense_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
   a.c1_stride = P.chunk_rows;
   a.c1_j0 = j0;
   a.err = P.d_err;
-  const int64_t items = a.n_stripes * a.npairs;
-  const int grid = (int)std::min<int64_t>(items, d.num_sms);
+  const int64_t units = a.n_stripes * (a.npairs / CL);
+  const int64_t max_ctas = d.num_sms / CL * CL;
+  const int grid = (int)std::min<int64_t>(units * CL, max_ctas);
   P.dominant = "dense_tcgen05";
   prof_begin(P, s);
-  k_dense<<<grid, NUM_THREADS, dense_smem_bytes(), s>>>(a);
+  if (CL == 2) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)num_threads<2>());
+    cfg.dynamicSmemBytes = dense_smem_bytes();
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<2>, a));
+  } else {
+    k_dense<1><<<grid, num_threads<1>(), dense_smem_bytes(), s>>>(a);
+  }
   prof_end(P, s);
   P.launches += 1;
   FZP_CUDA_TRY(cudaGetLastError());

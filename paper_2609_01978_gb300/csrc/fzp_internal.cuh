@@ -139,6 +139,8 @@ struct Dense {
   int64_t kblocks = 0;     // ceil(N / 64)
   int ntiles = 0;          // 2M / 128 row tiles of the kernel matrix
   int promote_kblocks = 0; // K blocks per TMEM accumulation chunk
+  int npairs = 0;          // kernel tile pairs, padded to an even count
+  int cluster = 2;         // CTAs per cluster sharing each mask tile
   int num_sms = 0;
 };
 
@@ -148,7 +150,7 @@ struct Plan {
   int64_t N, c;
   int M;
   int form, precision, stripe_rows;
-  int promote_req = 0, row_batch_req = 0;  // tuning knobs as requested (0: default)
+  int promote_req = 0, row_batch_req = 0, cluster_req = 0;  // tuning knobs as requested (0: default)
   bool owns_buffers = true;  // false: tables and workspace belong to a batch
   // derived
   double kappa, delta, dx2, R2;

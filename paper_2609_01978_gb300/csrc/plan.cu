@@ -155,6 +155,8 @@ fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
   P.stripe_rows = in->stripe_rows;
   P.promote_req = in->promote;
   P.row_batch_req = in->row_batch;
+  if (in->cluster < 0 || in->cluster > 2) return set_error(FZP_E_INVALID, "cluster must be 0, 1 or 2");
+  P.cluster_req = in->cluster;
   return FZP_OK;
 }
 
@@ -182,7 +184,7 @@ fzp_status build_mask_tables(Plan& P) {
 // Rows per row-pass chunk: requested (multiple of 256), else as many as an
 // 8 GiB row intermediate holds; never more than the grid (rounded to 256).
 int64_t chunk_rows_for(const Plan& P) {
-  const int64_t M2 = (2 * (int64_t)P.M + 255) / 256 * 256;
+  const int64_t M2 = (2 * (int64_t)P.M + 511) / 512 * 512;
   const int64_t budget_rows = (int64_t)((8ull << 30) / (uint64_t)(M2 * (P.precision == FZP_PREC_FP64 ? 8 : 4)));
   int64_t rows = P.stripe_rows > 0 ? (int64_t)P.stripe_rows : budget_rows;
   rows = std::min<int64_t>(rows, P.N);
@@ -225,8 +227,8 @@ fzp_status fzp_plan(const fzp_params* params, fzp_plan_t* out) {
   g_errmsg[0] = 0;
   st = build_mask_tables(*P);
   if (st == FZP_OK) {
-    // rows of C1: 2M kernel rows, rounded up to whole pairs of 128-row tiles (dense form)
-    const int64_t M2 = (2 * (int64_t)P->M + 255) / 256 * 256;
+    // rows of C1: 2M kernel rows, rounded up to whole couples of 2 x 128-row tile pairs (dense form)
+    const int64_t M2 = (2 * (int64_t)P->M + 511) / 512 * 512;
     P->chunk_rows = chunk_rows_for(*P);
     const int64_t rows = P->chunk_rows;
     cudaError_t e = cudaSuccess;
@@ -269,6 +271,7 @@ fzp_status fzp_plan_info_get(fzp_plan_t plan, fzp_plan_info* out) {
   out->promote = P.form == FZP_FORM_DENSE ? P.dn.promote_kblocks : 0;
   out->row_batch = P.form == FZP_FORM_BLUESTEIN ? (int32_t)P.bs.rows : 0;
   out->chunk_rows = P.chunk_rows;
+  out->cluster = P.form == FZP_FORM_DENSE ? P.dn.cluster : 0;
   out->device_bytes = P.device_bytes;
   return FZP_OK;
 }

@@ -21,8 +21,9 @@ def env():
     return fzp, torch, oracle
 
 
-def _plan(fzp, g, prec=2):
-    return fzp.Plan(D=g.D, f=g.f, lam=g.lam, M=g.M, pitch=g.p, dx=g.dx, N=g.N, form=fzp.FORM_DENSE, precision=prec)
+def _plan(fzp, g, prec=2, cluster=0):
+    return fzp.Plan(D=g.D, f=g.f, lam=g.lam, M=g.M, pitch=g.p, dx=g.dx, N=g.N, form=fzp.FORM_DENSE, precision=prec,
+                    cluster=cluster)
 
 
 def test_dense_config1(env):
@@ -38,12 +39,15 @@ def test_dense_config1(env):
     assert abs(m["de_lobe"] - mref["de_lobe"]) < 1e-4
 
 
-def test_dense_ragged_tiles(env):
-    """N = 9001 (last K block partial), M = 128 (two kernel tiles), row ranges
-    that cut stripes (partial 256-row tiles), accumulation over ranges."""
+@pytest.mark.parametrize("cluster", [1, 2])
+def test_dense_ragged_tiles(env, cluster):
+    """N = 9001 (last K block partial), M = 128 (one pair of kernel tiles, padded
+    to a couple for the 2-CTA cluster), row ranges that cut stripes (partial
+    256-row tiles); both the single-CTA and the cluster variant."""
     fzp, torch, O = env
     g = O.Geometry(D=4e-3 * 9001 / 5057, f=20e-3 * 9001 / 5057, lam=632.8e-9, M=128, p=0.3e-6, N=9001)
-    with _plan(fzp, g) as plan:
+    with _plan(fzp, g, cluster=cluster) as plan:
+        assert plan.info["cluster"] == cluster
         for (j0, j1) in [(0, g.N), (4321, 4321 + 777), (g.c, g.c + 1)]:
             _, I = run_plan(fzp, torch, plan, g.M, j0, j1)
             assert rel_l2(I, np.abs(O.field_czt(g, j0, j1)) ** 2) <= 1e-4, (j0, j1)
