@@ -14,7 +14,12 @@ lambda = 632.8 nm, f/# = 5 (f = 1.25 m), 4 samples per outermost zone width
 lambda f/# / 8 = 0.3955 um, centred on the focus.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--form dense|bluestein]
-                  [--impl ours|reference] [--workload fzp-d0.25m|fzp-d1m]
+                  [--impl ours|reference] [--workload fzp-d0.25m|fzp-d1m|...|fzp-d5m]
+                  [--plain-rows R] [--e2e-steps E]
+
+--plain-rows R times the plain FP32 form on the R aperture rows around the
+centre instead of all N (its cost per row does not depend on the row), for
+the large-D workloads; --e2e-steps 0 leaves out the end-to-end leg.
 
 Under torchrun (N > 1) every rank propagates its own copy of the aperture
 (independent problems: weak scaling, no collective on the data path); rank 0
@@ -38,7 +43,27 @@ if ROOT not in sys.path:
 WORKLOADS = {
     "fzp-d0.05m": dict(D=0.05, lam=632.8e-9, fnum=5.0, M=512),  # small case for profiler captures
     "fzp-d0.25m": dict(D=0.25, lam=632.8e-9, fnum=5.0, M=512),
-    "fzp-d1m": dict(D=1.0, lam=632.8e-9, fnum=5.0, M=512),
+    "fzp-d1m": dict(D=1.0, lam=632.8e-9, fnum=5.0, M=512),  # the D sweep at f/# = 5 (N up to 6.3e6)
+    "fzp-d2m": dict(D=2.0, lam=632.8e-9, fnum=5.0, M=512),
+    "fzp-d3m": dict(D=3.0, lam=632.8e-9, fnum=5.0, M=512),
+    "fzp-d4m": dict(D=4.0, lam=632.8e-9, fnum=5.0, M=512),
+    "fzp-d5m": dict(D=5.0, lam=632.8e-9, fnum=5.0, M=512),
+    # batched deformed membranes (D ~ U[0.05, 0.30] m, 450/550/650 nm, ROI 256^2,
+    # seed 0): the first --instances of the 256 draws, one CUDA graph per step
+    "membranes": dict(D=0.0, lam=0.0, fnum=5.0, M=256),
+}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the dominant kernel, from a one-pass ncu capture of this workload; reported
+# only while the kernel's sources hash to what was captured (null otherwise).
+# Summaries and commands: profiles/dense_splitbf16_fzp-d0.25m_launches.md and
+# profiles/bluestein_fp32_fzp-d0.25m_launches.md.
+KERNEL_SOURCES = {
+    "dense": ["dense.cu", "tc_ptx.cuh", "fzp_internal.cuh"],
+    "bluestein": ["bluestein.cu", "fzp_internal.cuh"],
+}
+TRAFFIC = {
+    ("fzp-d0.25m", "dense"): (644.87e9 + 97.88e9,
+                              "d44e0f4ab3e79f3bfda013c442dbf81b02d733b83e831b2ebfca46241936b19f"),
 }
 METRIC = "aperture Gsamples/s into 512² ROI, split-BF16 vs FP32 CZT at ≤1e-4 PSF error"
 UNIT = "Gsamples/s"
@@ -54,6 +79,20 @@ def _peaks():
         return d, "measured"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _traffic(workload, form):
+    """Captured per-launch DRAM bytes of the dominant kernel, or None when the
+    kernel has changed since the capture."""
+    import hashlib
+    hit = TRAFFIC.get((workload, form))
+    if hit is None:
+        return None
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[form]:
+        with open(os.path.join(ROOT, "paper_2609_01978_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return hit[0] if h.hexdigest() == hit[1] else None
 
 
 class ClockSampler:
@@ -124,10 +163,80 @@ def bluestein_f2_flops(info: dict, rows: int) -> float:
     product with H, inverse L2-point FFT) for `rows` aperture rows: per row and
     per inner transform 2 x 5 L2 log2 L2 + 6 L2, L1 inner transforms per row."""
     L = info["fft_length"]
-    L2 = min(L, 8192)
+    L2 = info["fft_inner"]
     L1 = L // L2
     lg = L2.bit_length() - 1
     return rows * L1 * (10.0 * L2 * lg + 6.0 * L2)
+
+
+def run_membranes(args, fzp, torch, dev, ws, pg, rank, local):
+    """Config 4: a batch of deformed membranes (autotuned form per instance), the
+    whole batch replayed as one CUDA graph, metrics of every instance per step."""
+    import fzp_inputs
+    wl = WORKLOADS["membranes"]
+    fnum, M = wl["fnum"], wl["M"]
+    mem = fzp_inputs.batch_draws(256, seed=0)[:args.instances]
+    probs = [dict(D=m.D, f=fnum * m.D, lam=m.lam, M=M, pitch=m.lam * fnum / 8, precision=fzp.PREC_AUTO_1E4,
+                  deform=fzp.make_deform(m.amp, m.period, m.theta, m.taper, m.ridges)) for m in mem]
+    stream = torch.cuda.current_stream(dev)
+    b = fzp.Batch(probs)
+    infos = [b.info(i) for i in range(len(probs))]
+    samples = sum(inf["N"] ** 2 for inf in infos)
+    fields = [torch.empty((M, M), dtype=torch.complex128, device=dev) for _ in probs]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        flush.fill_(1.0)
+        b.propagate(fields, stream=stream)
+        return [b.metrics(i, fields[i], stream=stream) for i in range(len(probs))]
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        mets = step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clocks = sampler.stop() if sampler else None
+    if pg:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    b.close()
+    forms = {}
+    for inf in infos:
+        k = ("dense" if inf["form"] == fzp.FORM_DENSE else "bluestein") + "/" + \
+            {0: "f64", 1: "f32", 2: "split-bf16", 3: "bf16"}[inf["precision"]]
+        forms[k] = forms.get(k, 0) + 1
+    return {"metric": METRIC, "value": ws * args.steps * samples / (ms / 1e3) / 1e9, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "mixed (autotuned per instance)",
+            "data": "synthetic (seeded deformed membranes)",
+            "config": {"workload": "membranes", "instances": len(probs), "of": 256, "seed": 0, "roi": M,
+                       "f_number": fnum, "samples_per_step": samples, "forms": forms,
+                       "l2": "256 MiB buffer written between steps (flush)"},
+            "roofline": None, "e2e": None, "gpu_launches": None, "clocks": clocks,
+            "per_instance_ms": ms / args.steps / len(probs),
+            "de_lobe_range": [min(m["de_lobe"] for m in mets), max(m["de_lobe"] for m in mets)]}
+
+
+def _config(args, wl, N):
+    """The workload description shared by both arms' JSON lines."""
+    return {"workload": args.workload, "form": args.form, "D_m": wl["D"], "lambda_m": wl["lam"],
+            "f_number": wl["fnum"], "N": N, "samples_per_step": N * N, "roi": wl["M"],
+            "roi_pitch_m": wl["lam"] * wl["fnum"] / 8, "l2": "256 MiB buffer written between steps (flush)"}
 
 
 def run_reference(args, wl):
@@ -150,7 +259,7 @@ def run_reference(args, wl):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (procedural zone plate)",
-            "config": {"workload": args.workload, "N": g.N, "M": g.M, "rows_per_step": rows},
+            "config": dict(_config(args, wl, g.N), rows_per_step=rows),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -158,16 +267,17 @@ def run_reference(args, wl):
 def cpu_baseline(wl, budget_s: float = 15.0) -> dict:
     import oracle as O
     g = O.Geometry(D=wl["D"], f=wl["D"] * wl["fnum"], lam=wl["lam"], M=wl["M"], p=wl["lam"] * wl["fnum"] / 8)
+    # grow the sample until one evaluation takes at least half the budget (small
+    # samples carry fixed costs, so one extrapolation undershoots)
     rows = 16
-    j0 = g.c - rows // 2
-    t0 = time.perf_counter()
-    O.field_czt(g, j0, j0 + rows)
-    dt = time.perf_counter() - t0
-    rows = max(16, min(g.N, int(rows * budget_s / max(dt, 1e-3))))
-    j0 = g.c - rows // 2
-    t0 = time.perf_counter()
-    O.field_czt(g, j0, j0 + rows)
-    dt = time.perf_counter() - t0
+    while True:
+        j0 = g.c - rows // 2
+        t0 = time.perf_counter()
+        O.field_czt(g, j0, j0 + rows)
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * budget_s or rows >= g.N:
+            break
+        rows = min(g.N, max(2 * rows, int(rows * budget_s / max(dt, 1e-3))))
     return {"value": rows * g.N / dt / 1e9, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
             "sample": f"{rows} central aperture rows of N = {g.N} (row + column CZT, FP64), {dt:.1f} s",
             "seconds": dt}
@@ -185,6 +295,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 Bluestein form")
+    ap.add_argument("--plain-rows", type=int, default=0, help="rows of the plain form's timed sample (0: all)")
+    ap.add_argument("--instances", type=int, default=16, help="membranes workload: instances per batch")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     ws, rank, local = _dist()
@@ -210,6 +322,13 @@ def main():
         if rank != 0:
             __graft_entry__.build()  # already built by rank 0; loads the library
         dist.barrier()
+    if args.workload == "membranes":
+        out = run_membranes(args, fzp, torch, dev, ws, pg, rank, local)
+        if rank == 0:
+            _print(out)
+        if pg:
+            pg.destroy_process_group()
+        return
     D, lam, fnum, M = wl["D"], wl["lam"], wl["fnum"], wl["M"]
     if args.form == "dense":
         form, prec, dtype = fzp.FORM_DENSE, fzp.PREC_SPLIT_BF16, "bf16x2"
@@ -269,7 +388,7 @@ def main():
         achieved = flops_launch / (avg_ms / 1e3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": prof["dominant_name"], "peak_source": peak_kind + " bf16 sustained"}
+                "traffic": _traffic(args.workload, "dense"), "kernel": prof["dominant_name"], "peak_source": peak_kind + " bf16 sustained"}
     else:
         launches = max(1, prof["dominant_launches"])
         rows_per_launch = N * args.steps / launches
@@ -277,52 +396,57 @@ def main():
         achieved = flops_launch / (avg_ms / 1e3) / 1e12
         peak = SM_COUNT * 128 * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12  # FP32 FMA lanes x clock
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": prof["dominant_name"],
+                "traffic": _traffic(args.workload, "bluestein"), "kernel": prof["dominant_name"],
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
 
     # end to end through the public API with host buffers: plan from host
     # parameters (zone-threshold table uploaded), propagate, copy the ROI field
     # to pinned host memory, metrics to host, destroy.
-    host = torch.empty((M, M), dtype=torch.complex128, pin_memory=True)
-    e2e_steps = max(1, args.e2e_steps)
-    torch.cuda.synchronize(dev)
-    if pg:
-        pg.barrier()
-    t0 = time.perf_counter()
-    h2d = 0
-    for _ in range(e2e_steps):
-        with fzp.Plan(**params) as p2:
-            h2d = 8 * p2.info["n_thresholds"] + 96
-            p2.propagate_roi(0, N, U, stream=stream)
-            host.copy_(U, non_blocking=True)
-            p2.metrics(U, stream=stream)
-            torch.cuda.synchronize(dev)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if pg:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": ws * N * N / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": M * M * 16 + 8 * 28,
-           "note": "fzp_plan + fzp_propagate_roi + field to pinned host + fzp_metrics + fzp_plan_destroy"}
+    e2e = None
+    if args.e2e_steps > 0:
+        host = torch.empty((M, M), dtype=torch.complex128, pin_memory=True)
+        torch.cuda.synchronize(dev)
+        if pg:
+            pg.barrier()
+        t0 = time.perf_counter()
+        h2d = 0
+        for _ in range(args.e2e_steps):
+            with fzp.Plan(**params) as p2:
+                h2d = 8 * p2.info["n_thresholds"] + 96
+                p2.propagate_roi(0, N, U, stream=stream)
+                host.copy_(U, non_blocking=True)
+                p2.metrics(U, stream=stream)
+                torch.cuda.synchronize(dev)
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        if pg:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": ws * N * N / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": M * M * 16 + 8 * 28,
+               "note": "fzp_plan + fzp_propagate_roi + field to pinned host + fzp_metrics + fzp_plan_destroy"}
     plan.close()
 
     # the plain FP32 Bluestein form on the same workload (the metric compares
     # the split-BF16 dense form with it): one warm and one timed step
     plain = None
     if args.form == "dense" and not args.no_plain:
+        rows = N if args.plain_rows <= 0 else min(N, args.plain_rows)
+        r0 = (N - rows) // 2
         with fzp.Plan(**dict(params, form=fzp.FORM_BLUESTEIN, precision=fzp.PREC_FP32)) as pb:
-            pb.propagate_roi(0, N, U, stream=stream)
+            pb.propagate_roi(r0, r0 + rows, U, stream=stream)
             torch.cuda.synchronize(dev)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            pb.propagate_roi(0, N, U, stream=stream)
+            pb.propagate_roi(r0, r0 + rows, U, stream=stream)
             mb = pb.metrics(U, stream=stream)
             e1.record(stream)
             torch.cuda.synchronize(dev)
             pms = e0.elapsed_time(e1)
-        plain = {"form": "bluestein", "dtype": "f32", "value": N * N / (pms / 1e3) / 1e9, "unit": UNIT,
-                 "ms_per_step": pms, "fwhm_x": mb["fwhm_x"], "de_lobe": mb["de_lobe"]}
+        plain = {"form": "bluestein", "dtype": "f32", "value": rows * N / (pms / 1e3) / 1e9, "unit": UNIT,
+                 "ms_per_step": pms, "rows": rows}
+        if rows == N:
+            plain.update(fwhm_x=mb["fwhm_x"], de_lobe=mb["de_lobe"])
 
     if rank != 0:
         if pg:
@@ -331,9 +455,7 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": dtype, "data": "synthetic (procedural binary zone plate)",
-           "config": {"workload": args.workload, "form": args.form, "D_m": D, "lambda_m": lam, "f_number": fnum,
-                      "N": N, "samples_per_step": N * N, "roi": M, "roi_pitch_m": lam * fnum / 8,
-                      "l2": "256 MiB buffer written between steps (flush)"},
+           "config": _config(args, wl, N),
            "roofline": roof, "e2e": e2e, "gpu_launches": prof["kernel_launches"], "clocks": clocks,
            "metrics_last_step": {k: m[k] for k in ("fwhm_x", "de_lobe", "mtf_half_cut")}}
     if plain:

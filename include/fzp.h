@@ -140,7 +140,8 @@ typedef struct fzp_plan_info {
   int32_t row_batch;     /* Bluestein: aperture rows per FFT pass launch           */
   int64_t chunk_rows;    /* aperture rows per row-pass chunk                       */
   int32_t cluster;       /* dense: CTAs per cluster sharing each mask tile         */
-  int32_t reserved;
+  int32_t fft_inner;     /* Bluestein: inner FFT length L2 of the four-step split
+                            L = L1 L2 (L itself when L <= the inner limit)        */
 } fzp_plan_info;
 
 /* Metrics of Fig. 2 Stage 4 / Fig. 18 Stage 5. */

@@ -492,6 +492,9 @@ fzp_status layout_t(Plan& P, FormSizes* out) {
   b.L2 = b.L < Traits<R>::L2MAX ? b.L : Traits<R>::L2MAX;
   b.L1 = b.L / b.L2;
   if (P.M > b.L2) return set_error(FZP_E_UNSUPPORTED, "M larger than the inner FFT length");
+  // the F1 twiddles are read from the L2-entry table with stride L2 / L1
+  if (b.L1 > b.L2) return set_error(FZP_E_UNSUPPORTED, "FFT length %lld above %lld", (long long)b.L,
+                                    (long long)b.L2 * b.L2);
   // rows per pass: requested, else a transform workspace of about 1 GiB
   const int64_t zbytes = (int64_t)sizeof(C) * b.L;
   int64_t rows = P.row_batch_req > 0 ? P.row_batch_req : (1ll << 30) / zbytes;

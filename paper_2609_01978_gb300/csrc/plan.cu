@@ -272,6 +272,7 @@ fzp_status fzp_plan_info_get(fzp_plan_t plan, fzp_plan_info* out) {
   out->row_batch = P.form == FZP_FORM_BLUESTEIN ? (int32_t)P.bs.rows : 0;
   out->chunk_rows = P.chunk_rows;
   out->cluster = P.form == FZP_FORM_DENSE ? P.dn.cluster : 0;
+  out->fft_inner = P.form == FZP_FORM_BLUESTEIN ? (int32_t)P.bs.L2 : 0;
   out->device_bytes = P.device_bytes;
   return FZP_OK;
 }

@@ -97,3 +97,33 @@ def test_dense_bf16_hi_only_is_less_accurate(env):
         errs[prec] = rel_l2(I, Iref)
     print("rel L2 split-BF16 %.3e  BF16 %.3e" % (errs[2], errs[3]))
     assert errs[2] <= 1e-4 and errs[3] > errs[2]
+
+
+_SWEEP_REF = {}
+
+
+@pytest.mark.parametrize("D", [1.0, 2.0, 3.0, 4.0, 5.0])
+@pytest.mark.parametrize("form", ["dense", "bluestein"])
+def test_d_sweep_sampled_rows(env, D, form):
+    """The D sweep at f/# = 5 (N = 1,264,223 ... 6,321,113, ROI 512² at
+    λ f/# / 8), in the launch configuration of the full runs: 8 rows through
+    the centre and 8 rows at v = -0.75 R, each range against the oracle's
+    Bluestein evaluation of the same rows (relative L2 of I <= 1e-4).  The
+    oracle's fields are shared by the two forms."""
+    fzp, torch, O = env
+    lam = 632.8e-9
+    g = O.Geometry(D=D, f=5 * D, lam=lam, M=512, p=lam * 5 / 8)
+    if form == "dense":
+        plan = _plan(fzp, g)
+    else:
+        plan = fzp.Plan(D=g.D, f=g.f, lam=g.lam, M=g.M, pitch=g.p, dx=g.dx, N=g.N, form=fzp.FORM_BLUESTEIN,
+                        precision=fzp.PREC_FP32)
+    with plan:
+        assert plan.info["N"] == g.N
+        for j0 in [g.c - 4, g.N // 8]:
+            key = (D, j0)
+            if key not in _SWEEP_REF:
+                _SWEEP_REF[key] = np.abs(O.field_czt(g, j0, j0 + 8)) ** 2
+            _, I = run_plan(fzp, torch, plan, g.M, j0, j0 + 8)
+            err = rel_l2(I, _SWEEP_REF[key])
+            assert err <= 1e-4, (D, form, j0, err)
