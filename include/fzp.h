@@ -111,8 +111,9 @@ typedef struct fzp_params {
                           1 GiB transform workspace                               */
   int32_t cluster;     /* dense: CTAs of a thread-block cluster that share each
                           generated mask tile through distributed shared memory,
-                          each generating its share of the rows (1 or 2; 0 -> 1:
-                          at D = 0.25 m, 2 measured 20 % slower)                  */
+                          each generating its share of the rows (1, 2 or 4;
+                          0 -> the largest of 4, 2, 1 dividing the M/64 tile
+                          pairs; other values pad the pairs with zero tiles)      */
 } fzp_params;
 
 /* Opaque plan: geometry, zone-threshold table, chirp / kernel tables and the
@@ -142,6 +143,9 @@ typedef struct fzp_plan_info {
   int32_t cluster;       /* dense: CTAs per cluster sharing each mask tile         */
   int32_t fft_inner;     /* Bluestein: inner FFT length L2 of the four-step split
                             L = L1 L2 (L itself when L <= the inner limit)        */
+  int32_t ctas;          /* dense: CTAs of the persistent row-pass launch (whole
+                            clusters that are resident at once)                   */
+  int32_t reserved;
 } fzp_plan_info;
 
 /* Metrics of Fig. 2 Stage 4 / Fig. 18 Stage 5. */

@@ -51,9 +51,8 @@ constexpr int A_BYTES = TILES * 2 * SUB;  // 32 KiB per stage: [t0 hi][t1 hi][t0
 constexpr int B_BYTES = BN * BK * 2;      // 16 KiB per stage
 constexpr int EPI_WARPS = 8;           // warps 0-7: epilogue (tile = warp / 4)
 constexpr int LOAD_WARP = 8, MMA_WARP = 9, GEN_WARP0 = 10;
-// CTAs per cluster sharing each generated mask tile: each generates BN / CL rows
-template <int CL> constexpr int gen_warps() { return 8 / CL; }
-template <int CL> constexpr int num_threads() { return (GEN_WARP0 + gen_warps<CL>()) * 32; }
+constexpr int GEN_WARPS = 8;           // warps 10-17: mask generators
+constexpr int NUM_THREADS = (GEN_WARP0 + GEN_WARPS) * 32;
 constexpr int TMEM_COLS = 512;         // two 128 x 256 FP32 accumulators
 constexpr int ERR_TIMEOUT_BASE = 100;
 
@@ -64,6 +63,7 @@ struct DenseArgs {
   int64_t j_begin, j_end;   // aperture rows of this launch [j_begin, j_end)
   int64_t n_stripes;        // ceil((j_end - j_begin) / BN)
   int npairs;               // kernel tile pairs (items per stripe; a multiple of the cluster size)
+  int M;                    // ROI side: tiles t with 64 t >= M are zero padding, not stored
   int promote;              // stages per accumulation chunk
   int hi_only;              // 1: BF16 kernel (hi) only
   const uint8_t* A;         // pre-swizzled kernel tiles, [pair][kb][t0hi t1hi t0lo t1lo]
@@ -169,6 +169,76 @@ __device__ __forceinline__ uint32_t walker_bits(Walker& w, int64_t i0, uint32_t&
   return bits;
 }
 
+// Number of toggle events at columns <= X; the open state after column X is
+// its parity.  Left of the axis the zone at distance d = c - X says how many
+// left boundaries lie at or before X (those with m above it); right of the
+// axis the zone at d = X - c counts the right boundaries reached.
+__device__ __forceinline__ int32_t walker_count(const Walker& w, int64_t X, const MaskGeom& g) {
+  if (w.ne == 0 || X < w.c - w.bmax) return 0;
+  if (X < w.c) {
+    const int64_t d = w.c - X;
+    return w.odd + (int32_t)(w.ze - zone_of(w.dj2 + d * d, g));
+  }
+  const int64_t d = X - w.c < w.bmax ? X - w.c : w.bmax;
+  return w.odd + w.L + (int32_t)(zone_of(w.dj2 + d * d, g) - w.zc) + (X > w.c + w.bmax ? w.odd : 0);
+}
+
+// Open bits of columns [i0, i0 + 32) of the walker's row, for a whole warp at
+// once (each lane a row of the same stripe; every lane of the warp calls it).
+// Two zone evaluations give the block's events [e0, e1) without walking; the
+// zone boundaries among them index thresholds S_m that, over the warp's 32
+// neighbouring rows, form one short contiguous range of m (at most ~17 at four
+// samples per outermost zone), read with one coalesced load and handed to the
+// lanes by shuffles.  The events are independent of each other, so the block
+// costs one memory round trip instead of one per toggle.
+__device__ __forceinline__ uint32_t block_bits(const Walker& w, int64_t i0, const MaskGeom& g) {
+  const int32_t e0 = walker_count(w, i0 - 1, g);
+  const int32_t e1 = walker_count(w, i0 + 31, g);
+  // thresholds of this lane's boundary events: b = e - odd in [b0, b1) within [0, 2L)
+  int32_t mlo = INT32_MAX, mhi = INT32_MIN;
+  const int32_t b0 = max(e0 - w.odd, 0), b1 = min(e1 - w.odd, 2 * w.L);
+  if (w.ne > 0 && b1 > b0) {
+    if (b0 < w.L) {  // left boundaries: m = ze - b
+      mlo = (int32_t)w.ze - (min(b1, w.L) - 1);
+      mhi = (int32_t)w.ze - b0;
+    }
+    if (b1 > w.L) {  // right boundaries: m = zc + 1 + (b - L)
+      mlo = min(mlo, (int32_t)w.zc + 1 + (max(b0, w.L) - w.L));
+      mhi = max(mhi, (int32_t)w.zc + (b1 - w.L));
+    }
+  }
+  const int32_t wlo = __reduce_min_sync(0xffffffffu, mlo);
+  const int32_t whi = __reduce_max_sync(0xffffffffu, mhi);
+  const int32_t nev = (int32_t)__reduce_max_sync(0xffffffffu, (uint32_t)(e1 - e0));
+  const bool staged = whi >= wlo && whi - wlo < 32;
+  const int lane = threadIdx.x & 31;
+  long long tv = 0;
+  if (staged && wlo + lane <= whi) tv = __ldg(g.thr + (wlo + lane - 1));
+  uint32_t bits = 0u - ((uint32_t)e0 & 1u);
+  for (int32_t t = 0; t < nev; ++t) {
+    const int32_t e = e0 + t, b = e - w.odd;
+    const bool valid = e < e1;
+    const bool bnd = valid && b >= 0 && b < 2 * w.L;
+    const bool left = b < w.L;
+    const int32_t m = bnd ? (left ? (int32_t)w.ze - b : (int32_t)w.zc + 1 + (b - w.L)) : wlo;
+    long long S = __shfl_sync(0xffffffffu, tv, (m - wlo) & 31);
+    if (bnd && !staged) S = __ldg(g.thr + (m - 1));
+    if (valid) {
+      int64_t col;
+      if (b < 0) {
+        col = w.c - w.bmax;  // chord start
+      } else if (b >= 2 * w.L) {
+        col = w.c + w.bmax + 1;  // chord end
+      } else {
+        const int64_t aa = (int64_t)ceil_sqrt44((int64_t)S - w.dj2);
+        col = left ? w.c - aa + 1 : w.c + aa;
+      }
+      bits ^= 0xFFFFFFFFu << (uint32_t)(col - i0);
+    }
+  }
+  return bits;
+}
+
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
   uint32_t d;
   asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
@@ -193,12 +263,15 @@ __device__ __forceinline__ void expand_bits(uint32_t bits, uint32_t (&w)[16]) {
 
 // ---------------------------------------------------------------- kernel
 // Work units: unit u = (tile-pair group pu = u / n_stripes, stripe s = u % n_stripes);
-// CTA rank rk of a cluster of CL takes pair pu * CL + rk.  With CL = 2 both CTAs
-// of a cluster work on the same stripe and each generates half of its mask rows;
-// each half is copied to the peer's shared memory (distributed shared memory) by
-// one bulk copy per stage.
+// CTA rank rk of a cluster of CL takes pair pu * CL + rk, so the CL CTAs of a
+// cluster work on the same stripe with different kernel tiles.  Each generates
+// RPC = BN / CL of the stripe's mask rows and copies them into its peers' shared
+// memory (distributed shared memory, one bulk copy per peer and stage).  Its 8
+// generator warps form CL phases of 8 / CL warps; phase p generates the stages of
+// the CTA's global K blocks G with G % CL == p, so CL stages are in flight at once
+// and each warp has CL stage times for its rows.
 template <int CL>
-__global__ void __launch_bounds__(num_threads<CL>(), 1) k_dense(DenseArgs a) {
+__global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = base;                     // STAGES x 32 KiB
@@ -212,15 +285,18 @@ __global__ void __launch_bounds__(num_threads<CL>(), 1) k_dense(DenseArgs a) {
   uint64_t* drain = accEmpty + 1;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(drain + 1);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 2);
-  volatile int* gen_ok = reinterpret_cast<volatile int*>(drain + 3);  // generator warps' common decision
+  // common continue/abort decisions, double-buffered by block (or chunk) parity:
+  // gen_ok[2 * phase + parity] for each generator phase, epi_ok[parity] for the epilogue
+  volatile int* gen_ok = reinterpret_cast<volatile int*>(drain + 3);
+  volatile int* epi_ok = gen_ok + 2 * 4;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&fullA[s], 1);
-      // mask rows: 8 local generator warps (CL = 1), or 4 local warps + the
-      // expect-tx arrival for the peer's half, delivered by a bulk copy (CL = 2)
-      mbar_init(&fullB[s], CL > 1 ? 5 : 8);
+      // mask rows: the 8 / CL local warps of the stage's phase, plus (CL > 1) the
+      // expect-tx arrival for the rows the peers' bulk copies deliver
+      mbar_init(&fullB[s], CL > 1 ? GEN_WARPS / CL + 1 : GEN_WARPS);
       mbar_init(&empty[s], CL);  // MMA completion of every CTA that reads rows this CTA writes
     }
     mbar_init(accFull, 1);
@@ -331,86 +407,85 @@ __global__ void __launch_bounds__(num_threads<CL>(), 1) k_dense(DenseArgs a) {
       }
     }
   } else if (warp >= GEN_WARP0) {
-    // ---------------- mask generators: row (rk * BN/CL + g) of the unit's stripe
-    const int g = threadIdx.x - GEN_WARP0 * 32;  // 0 .. BN/CL - 1
-    const int row = (int)rk * (BN / CL) + g;
-    int stage = 0;
-    uint32_t phase = 0;
+    // ---------------- mask generators
+    constexpr int RPC = BN / CL, WPS = GEN_WARPS / CL;
+    const int gw = warp - GEN_WARP0;
+    const int ph = gw / WPS, wr = gw % WPS;
+    const int row = (int)rk * RPC + wr * 32 + lane;  // row of the stripe, 0 .. BN - 1
     // 64-byte swizzle, K-major: row at (row/8)*512 + (row%8)*64, 16-byte chunk q at q ^ ((row%8)/2)
     uint8_t* rowbase0 = sB + (row >> 3) * 512 + (row & 7) * 64;
     const int sw = (row & 7) >> 1;
-    if constexpr (CL == 1) {
-      for (int64_t it = u0; it < n_items; it += ustep) {
-        if (__shfl_sync(0xffffffffu, *abort_flag, 0)) break;
-        const int64_t s = it % a.n_stripes;
-        Walker w;
-        walker_init(w, a.j_begin + s * BN + row, a.j_end, a.mg);
-        uint32_t state = 0;
-        bool ok = true;
-        for (int64_t kb = 0; kb < nkb; ++kb) {
-          if (!warp_wait(&empty[stage], phase ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 5)) { ok = false; break; }
-          const uint32_t bits = walker_bits(w, kb * BK, state, a.mg.thr);
-          uint8_t* rowp = rowbase0 + stage * B_BYTES;
-          uint32_t wd[16];
-          expand_bits(bits, wd);
+    const bool leader = wr == 0 && lane == 0;
+    const int64_t my_units = u0 < n_items ? (n_items - u0 + ustep - 1) / ustep : 0;
+    const int64_t nblk = my_units * nkb;  // the CTA's global K blocks, in MMA order
+    int last[STAGES];  // leader: phase of the last peer copy expected on each stage
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<uint4*>(rowp + ((q ^ sw) << 4)) = make_uint4(wd[4 * q], wd[4 * q + 1], wd[4 * q + 2], wd[4 * q + 3]);
-          fence_proxy_async();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&fullB[stage]);
-          if (++stage == STAGES) { stage = 0; phase ^= 1; }
-        }
-        if (!ok) break;
+    for (int s2 = 0; s2 < STAGES; ++s2) last[s2] = -1;
+    Walker w;
+    uint32_t state = 0;  // CL = 1: open state of the sequential walk
+    int64_t cur_unit = -1;
+    int64_t ui = 0, kb = ph;  // G = ui * nkb + kb, advanced without division
+    while (kb >= nkb && nkb > 0) { kb -= nkb; ++ui; }
+    for (int64_t G = ph; G < nblk; G += CL) {
+      const int stage = (int)(G & (STAGES - 1));
+      const uint32_t phase = (uint32_t)((G / STAGES) & 1);
+      if (ui != cur_unit) {
+        cur_unit = ui;
+        const int64_t s = (u0 + ui * ustep) % a.n_stripes;
+        walker_init(w, a.j_begin + s * BN + row, a.j_end, a.mg);
+        state = 0;
       }
-    } else {
-      // The 4 generator warps act together (named barrier 1): thread g = 0 waits
-      // for the stage and publishes the decision, all rows are written to this
-      // CTA's half of the tile (8 KiB, contiguous), then g = 0 sends the half to
-      // the peer with one bulk copy that completes on the peer's fullB barrier.
-      constexpr int GT = BN / CL;  // generator threads
-      constexpr uint32_t HALF = B_BYTES / CL;
-      bool ok = true;
-      int last[STAGES];  // phase of the last peer copy expected on each stage (thread g = 0)
+      // One thread per phase waits for the stage; the phase's warps take its
+      // decision at a named barrier (waiting there issues no instructions).
+      const int slot = 2 * ph + (int)(G / CL & 1);
+      if (leader)
+        gen_ok[slot] = (CL > 1 ? mbar_wait_cl(&empty[stage], phase ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 5)
+                               : mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 5))
+                            ? 1
+                            : 0;
+      named_bar_sync(1 + ph, WPS * 32);
+      if (!gen_ok[slot]) break;
+      // one CTA, consecutive blocks: walk the row; clusters: each phase takes every
+      // CL-th block, found directly
+      const uint32_t bits = CL == 1 ? walker_bits(w, kb * BK, state, a.mg.thr) : block_bits(w, kb * BK, a.mg);
+      uint8_t* rowp = rowbase0 + stage * B_BYTES;
+      uint32_t wd[16];
+      expand_bits(bits, wd);
 #pragma unroll
-      for (int s2 = 0; s2 < STAGES; ++s2) last[s2] = -1;
-      for (int64_t it = u0; it < n_items && ok; it += ustep) {
-        const int64_t s = it % a.n_stripes;
-        Walker w;
-        walker_init(w, a.j_begin + s * BN + row, a.j_end, a.mg);
-        uint32_t state = 0;
-        for (int64_t kb = 0; kb < nkb; ++kb) {
-          if (g == 0) *gen_ok = mbar_wait_cl(&empty[stage], phase ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 5) ? 1 : 0;
-          named_bar_sync(1, GT);
-          ok = *gen_ok != 0;
-          if (!ok) break;
-          const uint32_t bits = walker_bits(w, kb * BK, state, a.mg.thr);
-          uint8_t* rowp = rowbase0 + stage * B_BYTES;
-          uint32_t wd[16];
-          expand_bits(bits, wd);
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(rowp + ((q ^ sw) << 4)) = make_uint4(wd[4 * q], wd[4 * q + 1], wd[4 * q + 2], wd[4 * q + 3]);
+      fence_proxy_async();
+      if constexpr (CL == 1) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&fullB[stage]);
+      } else {
+        // all of this CTA's rows of the stage are written: one thread sends them
+        named_bar_sync(1 + ph, WPS * 32);
+        if (leader) {
+          const uint32_t off = (uint32_t)(stage * B_BYTES + rk * RPC * 64);
+          mbar_arrive_tx(&fullB[stage], (uint32_t)((CL - 1) * RPC * 64));  // the peers' rows land here
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<uint4*>(rowp + ((q ^ sw) << 4)) = make_uint4(wd[4 * q], wd[4 * q + 1], wd[4 * q + 2], wd[4 * q + 3]);
-          fence_proxy_async();
-          named_bar_sync(1, GT);
-          if (g == 0) {
-            uint8_t* half = sB + stage * B_BYTES + rk * HALF;
-            mbar_arrive_tx(&fullB[stage], HALF);  // the peer's half lands here
-            bulk_s2peer(mapa(smem_u32(half), rk ^ 1u), half, HALF, mapa(smem_u32(&fullB[stage]), rk ^ 1u));
-            last[stage] = (int)phase;
+          for (int q = 1; q < CL; ++q) {
+            const uint32_t peer = (rk + (uint32_t)q) % (uint32_t)CL;
+            bulk_s2peer(mapa(smem_u32(sB + off), peer), sB + off, (uint32_t)(RPC * 64),
+                        mapa(smem_u32(&fullB[stage]), peer));
           }
-          if (lane == 0) mbar_arrive(&fullB[stage]);
-          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+          last[stage] = (int)phase;
         }
+        if (lane == 0) mbar_arrive(&fullB[stage]);
       }
-      if (g == 0 && *abort_flag) {
-        // after an abort the peer's copies already issued must land before this
-        // CTA's shared memory is released (bounded: the peer may have stopped first)
+      kb += CL;
+      while (kb >= nkb) { kb -= nkb; ++ui; }
+    }
+    if constexpr (CL > 1) {
+      if (leader && *abort_flag) {
+        // after an abort the peers' copies already issued must land before this
+        // CTA's shared memory is released (bounded: a peer may have stopped first)
 #pragma unroll
         for (int s2 = 0; s2 < STAGES; ++s2) {
           if (last[s2] < 0) continue;
           const uint64_t t0 = gtimer();
-          while (!mbar_try(&fullB[s2], (uint32_t)last[s2]) && gtimer() - t0 < WAIT_NS) {
+          while (!mbar_try_cl(&fullB[s2], (uint32_t)last[s2]) && gtimer() - t0 < WAIT_NS) {
           }
         }
       }
@@ -424,13 +499,18 @@ __global__ void __launch_bounds__(num_threads<CL>(), 1) k_dense(DenseArgs a) {
     for (int64_t it = u0; it < n_items && ok; it += ustep) {
       const int64_t pr = (it / a.n_stripes) * CL + rk;
       const int64_t s = it % a.n_stripes;
+      // zero-padding tiles (64 t >= M) have no rows in C1: nothing is stored
+      const bool live = (pr * TILES + q) * 64 < (int64_t)a.M;
       float* crow = a.C1 + ((pr * TILES + q) * BM + r) * a.c1_stride + (a.j_begin + s * BN - a.c1_j0);
       for (int64_t ch = 0; ch < nchunk; ++ch) {
-        if (!warp_wait(accFull, accph, abort_flag, a.err, ERR_TIMEOUT_BASE + 6)) { ok = false; break; }
+        // thread 0 waits for the accumulators; the 8 warps meet at a named barrier
+        if (threadIdx.x == 0) epi_ok[accph] = mbar_wait(accFull, accph, abort_flag, a.err, ERR_TIMEOUT_BASE + 6) ? 1 : 0;
+        named_bar_sync(1 + 4, EPI_WARPS * 32);
+        if (!epi_ok[accph]) { ok = false; break; }
         tc_fence_after();
         const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(q * BN);
 #pragma unroll 1
-        for (int col = 0; col < BN; col += 32) {
+        for (int col = 0; col < (live ? BN : 0); col += 32) {
           float v[32];
           tmem_ld32(taddr + col, v);
           float4* dst = reinterpret_cast<float4*>(crow + col);
@@ -536,9 +616,12 @@ fzp_status dense_layout(Plan& P, FormSizes* out) {
   Dense& d = P.dn;
   d.kblocks = (P.N + BK - 1) / BK;
   d.ntiles = 2 * P.M / BM;
-  d.npairs = ((d.ntiles + TILES - 1) / TILES + 1) / 2 * 2;  // padded to an even count (zero pair)
+  const int used = (d.ntiles + TILES - 1) / TILES;  // tile pairs holding ROI rows
+  // cluster: CTAs sharing each stripe's mask (default: the largest of 4, 2, 1
+  // that divides the pairs); pairs padded with zero tiles to a multiple of it
+  d.cluster = P.cluster_req > 0 ? P.cluster_req : (used % 4 == 0 ? 4 : used % 2 == 0 ? 2 : 1);
+  d.npairs = (used + d.cluster - 1) / d.cluster * d.cluster;
   d.promote_kblocks = P.promote_req > 0 ? P.promote_req : 128;  // 4096 samples per TMEM chunk
-  d.cluster = P.cluster_req == 2 ? 2 : 1;
   int dev = 0;
   FZP_CUDA_TRY(cudaGetDevice(&dev));
   FZP_CUDA_TRY(cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev));
@@ -547,7 +630,29 @@ fzp_status dense_layout(Plan& P, FormSizes* out) {
   if (!attrs) {
     FZP_CUDA_TRY(cudaFuncSetAttribute(k_dense<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem_bytes()));
     FZP_CUDA_TRY(cudaFuncSetAttribute(k_dense<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem_bytes()));
+    FZP_CUDA_TRY(cudaFuncSetAttribute(k_dense<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem_bytes()));
     attrs = true;
+  }
+  // The kernel is persistent: launch only CTAs that are resident at once.  A
+  // cluster must fit in one GPC, so with clusters fewer than all SMs may hold one.
+  d.max_ctas = d.num_sms;
+  if (d.cluster > 1) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(d.num_sms / d.cluster * d.cluster));
+    cfg.blockDim = dim3((unsigned)NUM_THREADS);
+    cfg.dynamicSmemBytes = dense_smem_bytes();
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)d.cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (d.cluster == 2) FZP_CUDA_TRY(cudaOccupancyMaxActiveClusters(&nclusters, k_dense<2>, &cfg));
+    else FZP_CUDA_TRY(cudaOccupancyMaxActiveClusters(&nclusters, k_dense<4>, &cfg));
+    if (nclusters < 1) return set_error(FZP_E_UNSUPPORTED, "no %d-CTA cluster of the dense kernel fits", d.cluster);
+    d.max_ctas = std::min(nclusters * d.cluster, d.num_sms / d.cluster * d.cluster);
   }
   return FZP_OK;
 }
@@ -587,8 +692,8 @@ fzp_status dense_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
   a.j_end = j0 + rows;
   a.n_stripes = (rows + BN - 1) / BN;
   const int CL = d.cluster;
-  const int used_pairs = (d.ntiles + TILES - 1) / TILES;
-  a.npairs = CL == 2 ? d.npairs : used_pairs;
+  a.npairs = d.npairs;
+  a.M = P.M;
   a.promote = d.promote_kblocks;
   a.hi_only = P.precision == FZP_PREC_BF16 ? 1 : 0;
   a.A = reinterpret_cast<const uint8_t*>(d.d_A);
@@ -597,26 +702,27 @@ fzp_status dense_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
   a.c1_j0 = j0;
   a.err = P.d_err;
   const int64_t units = a.n_stripes * (a.npairs / CL);
-  const int64_t max_ctas = d.num_sms / CL * CL;
+  const int64_t max_ctas = d.max_ctas;
   const int grid = (int)std::min<int64_t>(units * CL, max_ctas);
   P.dominant = "dense_tcgen05";
   prof_begin(P, s);
-  if (CL == 2) {
+  if (CL > 1) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)num_threads<2>());
+    cfg.blockDim = dim3((unsigned)NUM_THREADS);
     cfg.dynamicSmemBytes = dense_smem_bytes();
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.x = (unsigned)CL;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<2>, a));
+    if (CL == 2) FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<2>, a));
+    else FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<4>, a));
   } else {
-    k_dense<1><<<grid, num_threads<1>(), dense_smem_bytes(), s>>>(a);
+    k_dense<1><<<grid, NUM_THREADS, dense_smem_bytes(), s>>>(a);
   }
   prof_end(P, s);
   P.launches += 1;

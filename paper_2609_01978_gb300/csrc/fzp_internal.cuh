@@ -136,12 +136,13 @@ struct Bluestein {
 
 struct Dense {
   void* d_A = nullptr;     // kernel matrix, split-BF16, pre-swizzled tiles
-  int64_t kblocks = 0;     // ceil(N / 64)
+  int64_t kblocks = 0;     // ceil(N / 32)
   int ntiles = 0;          // 2M / 128 row tiles of the kernel matrix
   int promote_kblocks = 0; // K blocks per TMEM accumulation chunk
-  int npairs = 0;          // kernel tile pairs, padded to an even count
-  int cluster = 2;         // CTAs per cluster sharing each mask tile
+  int npairs = 0;          // kernel tile pairs, padded to a multiple of the cluster size
+  int cluster = 1;         // CTAs per cluster sharing each mask tile
   int num_sms = 0;
+  int max_ctas = 0;        // CTAs that can be resident at once (whole clusters)
 };
 
 struct Plan {

@@ -155,7 +155,8 @@ fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
   P.stripe_rows = in->stripe_rows;
   P.promote_req = in->promote;
   P.row_batch_req = in->row_batch;
-  if (in->cluster < 0 || in->cluster > 2) return set_error(FZP_E_INVALID, "cluster must be 0, 1 or 2");
+  if (in->cluster != 0 && in->cluster != 1 && in->cluster != 2 && in->cluster != 4)
+    return set_error(FZP_E_INVALID, "cluster must be 0, 1, 2 or 4");
   P.cluster_req = in->cluster;
   return FZP_OK;
 }
@@ -273,6 +274,7 @@ fzp_status fzp_plan_info_get(fzp_plan_t plan, fzp_plan_info* out) {
   out->chunk_rows = P.chunk_rows;
   out->cluster = P.form == FZP_FORM_DENSE ? P.dn.cluster : 0;
   out->fft_inner = P.form == FZP_FORM_BLUESTEIN ? (int32_t)P.bs.L2 : 0;
+  out->ctas = P.form == FZP_FORM_DENSE ? P.dn.max_ctas : 0;
   out->device_bytes = P.device_bytes;
   return FZP_OK;
 }

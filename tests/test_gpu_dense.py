@@ -39,11 +39,11 @@ def test_dense_config1(env):
     assert abs(m["de_lobe"] - mref["de_lobe"]) < 1e-4
 
 
-@pytest.mark.parametrize("cluster", [1, 2])
+@pytest.mark.parametrize("cluster", [1, 2, 4])
 def test_dense_ragged_tiles(env, cluster):
     """N = 9001 (last K block partial), M = 128 (one pair of kernel tiles, padded
-    to a couple for the 2-CTA cluster), row ranges that cut stripes (partial
-    256-row tiles); both the single-CTA and the cluster variant."""
+    with zero pairs for the 2- and 4-CTA clusters), row ranges that cut stripes
+    (partial 256-row tiles); the single-CTA and both cluster variants."""
     fzp, torch, O = env
     g = O.Geometry(D=4e-3 * 9001 / 5057, f=20e-3 * 9001 / 5057, lam=632.8e-9, M=128, p=0.3e-6, N=9001)
     with _plan(fzp, g, cluster=cluster) as plan:
