@@ -244,6 +244,7 @@ fzp_status fzp_batch_plan(const fzp_params* params, int n, fzp_batch_t* out) {
       return set_error(st, "instance %d: %s", i, fzp_last_error());
     }
     P->chunk_rows = chunk_rows_for(*P);
+    P->c1_rows = (2 * (int64_t)P->M + 511) / 512 * 512;
     FormSizes z;
     st = P->form == FZP_FORM_DENSE ? dense_layout(*P, &z) : bluestein_layout(*P, &z);
     if (st != FZP_OK) { batch_release(b); return st; }

@@ -30,6 +30,8 @@
 //              0.25 m aperture without promotion, 8e-6 with 4096-sample chunks).
 // Every mbarrier wait is bounded in time; on expiry the kernel records an error
 // code, drains what it issued, frees tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -54,6 +56,8 @@ constexpr int LOAD_WARP = 8, MMA_WARP = 9, GEN_WARP0 = 10;
 constexpr int GEN_WARPS = 8;           // warps 10-17: mask generators
 constexpr int NUM_THREADS = (GEN_WARP0 + GEN_WARPS) * 32;
 constexpr int TMEM_COLS = 512;         // two 128 x 256 FP32 accumulators
+constexpr int EPI_BOX = 32;            // epilogue: 32 rows x 32 columns FP32 per bulk reduction
+constexpr int EPI_BYTES = EPI_WARPS * EPI_BOX * EPI_BOX * 4;  // 32 KiB of staging, one box per warp
 constexpr int ERR_TIMEOUT_BASE = 100;
 
 struct DenseArgs {
@@ -271,12 +275,13 @@ __device__ __forceinline__ void expand_bits(uint32_t bits, uint32_t (&w)[16]) {
 // the CTA's global K blocks G with G % CL == p, so CL stages are in flight at once
 // and each warp has CL stage times for its rows.
 template <int CL>
-__global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
+__global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, const __grid_constant__ CUtensorMap tmC1) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = base;                     // STAGES x 32 KiB
   uint8_t* sB = base + STAGES * A_BYTES;  // STAGES x 16 KiB
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * B_BYTES);
+  uint8_t* sE = sB + STAGES * B_BYTES;     // EPI_BYTES: epilogue staging (1024-aligned)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sE + EPI_BYTES);
   uint64_t* fullA = bars;
   uint64_t* fullB = bars + STAGES;
   uint64_t* empty = bars + 2 * STAGES;
@@ -491,9 +496,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
       }
     }
   } else {
-    // ---------------- epilogue: warp w drains tile w/4, TMEM lanes 32(w%4)..+31
+    // ---------------- epilogue: warp w drains tile w/4, TMEM lanes 32(w%4)..+31.
+    // Each 32 x 32 piece goes registers -> shared memory (128-byte swizzle) ->
+    // one TMA store (first chunk of a unit) or TMA reduce-add in L2 (later chunks).
     const int q = warp >> 2;
-    const int r = (warp & 3) * 32 + lane;  // kernel row within the tile
+    uint8_t* eb = sE + warp * (EPI_BOX * EPI_BOX * 4);
     uint32_t accph = 0;
     bool ok = true;
     for (int64_t it = u0; it < n_items && ok; it += ustep) {
@@ -501,7 +508,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
       const int64_t s = it % a.n_stripes;
       // zero-padding tiles (64 t >= M) have no rows in C1: nothing is stored
       const bool live = (pr * TILES + q) * 64 < (int64_t)a.M;
-      float* crow = a.C1 + ((pr * TILES + q) * BM + r) * a.c1_stride + (a.j_begin + s * BN - a.c1_j0);
+      const int x0 = (int)(a.j_begin + s * BN - a.c1_j0);       // C1 column of the stripe's first row
+      const int y0 = (int)((pr * TILES + q) * BM + (warp & 3) * 32);  // C1 row of lane 0
       for (int64_t ch = 0; ch < nchunk; ++ch) {
         // thread 0 waits for the accumulators; the 8 warps meet at a named barrier
         if (threadIdx.x == 0) epi_ok[accph] = mbar_wait(accFull, accph, abort_flag, a.err, ERR_TIMEOUT_BASE + 6) ? 1 : 0;
@@ -509,22 +517,23 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
         if (!epi_ok[accph]) { ok = false; break; }
         tc_fence_after();
         const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(q * BN);
+        if (ch == 1 && lane == 0) bulk_wait0();  // the unit's stores have landed before the first add
 #pragma unroll 1
-        for (int col = 0; col < (live ? BN : 0); col += 32) {
+        for (int col = 0; col < (live ? BN : 0); col += EPI_BOX) {
           float v[32];
           tmem_ld32(taddr + col, v);
-          float4* dst = reinterpret_cast<float4*>(crow + col);
-          if (ch == 0) {
+          if (lane == 0) bulk_wait_read0();  // the previous piece has been read out of eb
+          __syncwarp();
 #pragma unroll
-            for (int k = 0; k < 8; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-          } else {
-            // fire-and-forget FP32 adds in L2: the accumulator is released without
-            // waiting for a read of the partial sums
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-              asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + k), "f"(v[4 * k]),
-                           "f"(v[4 * k + 1]), "f"(v[4 * k + 2]), "f"(v[4 * k + 3])
-                           : "memory");
+          for (int c4 = 0; c4 < 8; ++c4)
+            *reinterpret_cast<float4*>(eb + lane * 128 + ((c4 ^ (lane & 7)) << 4)) =
+                make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) {
+            if (ch == 0) tma_store_2d(&tmC1, eb, x0 + col, y0);
+            else tma_reduce_add_2d(&tmC1, eb, x0 + col, y0);
+            bulk_commit();
           }
         }
         tc_fence_before();
@@ -533,6 +542,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(DenseArgs a) {
         accph ^= 1;
       }
     }
+    if (lane == 0) bulk_wait0();  // C1 complete before the kernel ends
   }
   tc_fence_before();
   __syncthreads();
@@ -608,7 +618,29 @@ __global__ void k_mask_rows(MaskGeom mg, int64_t N, int64_t j0, int64_t rows, ui
   }
 }
 
-size_t dense_smem_bytes() { return 1024 + STAGES * (A_BYTES + B_BYTES) + 256; }
+size_t dense_smem_bytes() { return 1024 + STAGES * (A_BYTES + B_BYTES) + EPI_BYTES + 256; }
+
+// 2-D FP32 tensor map of the row intermediate: x = C1 column (aperture row of
+// the chunk), y = kernel row; 32 x 32 boxes with the 128-byte swizzle.
+fzp_status c1_tensor_map(const Plan& P, CUtensorMap* tm) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    FZP_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !fn) return set_error(FZP_E_CUDA, "cuTensorMapEncodeTiled unavailable");
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)P.chunk_rows, (cuuint64_t)P.c1_rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)P.chunk_rows * 4};
+  const cuuint32_t box[2] = {EPI_BOX, EPI_BOX};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, P.d_C1, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(FZP_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return FZP_OK;
+}
 
 }  // namespace
 
@@ -704,6 +736,11 @@ fzp_status dense_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
   const int64_t units = a.n_stripes * (a.npairs / CL);
   const int64_t max_ctas = d.max_ctas;
   const int grid = (int)std::min<int64_t>(units * CL, max_ctas);
+  CUtensorMap tm;
+  {
+    const fzp_status st = c1_tensor_map(P, &tm);
+    if (st != FZP_OK) return st;
+  }
   P.dominant = "dense_tcgen05";
   prof_begin(P, s);
   if (CL > 1) {
@@ -719,10 +756,10 @@ fzp_status dense_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (CL == 2) FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<2>, a));
-    else FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<4>, a));
+    if (CL == 2) FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<2>, a, tm));
+    else FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<4>, a, tm));
   } else {
-    k_dense<1><<<grid, NUM_THREADS, dense_smem_bytes(), s>>>(a);
+    k_dense<1><<<grid, NUM_THREADS, dense_smem_bytes(), s>>>(a, tm);
   }
   prof_end(P, s);
   P.launches += 1;

@@ -164,6 +164,7 @@ struct Plan {
   float* d_C1 = nullptr;       // row intermediate [2M][chunk_rows] (FP32 forms)
   double* d_C1d = nullptr;     // row intermediate [2M][chunk_rows] (FP64 form)
   int64_t chunk_rows = 0;
+  int64_t c1_rows = 0;          // rows of C1: 2M rounded up to 512
   double2* d_Uacc = nullptr;   // FP64 ROI accumulator M*M
   int* d_err = nullptr;        // device error word (bounded waits)
   double* d_metrics = nullptr; // device scratch for the metric extractor

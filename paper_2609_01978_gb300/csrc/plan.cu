@@ -231,6 +231,7 @@ fzp_status fzp_plan(const fzp_params* params, fzp_plan_t* out) {
     // rows of C1: 2M kernel rows, rounded up to whole couples of 2 x 128-row tile pairs (dense form)
     const int64_t M2 = (2 * (int64_t)P->M + 511) / 512 * 512;
     P->chunk_rows = chunk_rows_for(*P);
+    P->c1_rows = M2;
     const int64_t rows = P->chunk_rows;
     cudaError_t e = cudaSuccess;
     if (P->precision == FZP_PREC_FP64) e = cudaMalloc(&P->d_C1d, (size_t)(M2 * rows) * sizeof(double));
