@@ -62,8 +62,8 @@ KERNEL_SOURCES = {
     "bluestein": ["bluestein.cu", "fzp_internal.cuh"],
 }
 TRAFFIC = {
-    ("fzp-d0.25m", "dense"): (644.87e9 + 97.88e9,
-                              "d44e0f4ab3e79f3bfda013c442dbf81b02d733b83e831b2ebfca46241936b19f"),
+    ("fzp-d0.25m", "dense"): (702.89e9 + 98.67e9,
+                              "458e1d693f499f468803b3b21cfe66dc2dadfdd7d7ce856ac09a5b75ea6f5413"),
 }
 METRIC = "aperture Gsamples/s into 512² ROI, split-BF16 vs FP32 CZT at ≤1e-4 PSF error"
 UNIT = "Gsamples/s"
