@@ -41,6 +41,7 @@ FZP_PARAXIAL = 0
 LENS = 1
 FZP_EXACT = 2
 CIRC = 3
+FZP_PHASE = 4  # L-level phase FZP (Fig. 18): transmission e^{-2 pi i q / L}
 
 # First zero of J1 divided by pi: Airy null radius in units of lambda f / D.
 AIRY_NULL = 3.8317059702075125 / math.pi  # 1.2196698...
@@ -67,7 +68,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("dx", ctypes.c_double), ("lam", ctypes.c_double),
                 ("f", ctypes.c_double), ("R", ctypes.c_double), ("M", ctypes.c_int32),
                 ("kind", ctypes.c_int32), ("p", ctypes.c_double), ("x0", ctypes.c_double),
-                ("deform", ctypes.POINTER(_Deform))]
+                ("deform", ctypes.POINTER(_Deform)), ("levels", ctypes.c_int32), ("pad2_", ctypes.c_int32)]
 
 
 _lib = None
@@ -153,10 +154,17 @@ class Geometry:
     N: Optional[int] = None
     kind: int = FZP_PARAXIAL
     deform: Optional[Deform] = None
+    levels: int = 0  # FZP_PHASE: phase levels L (>= 2)
 
     def __post_init__(self):
+        if self.kind == FZP_PHASE and self.levels < 2:
+            raise ValueError("a phase FZP needs levels >= 2")
         if self.dx is None:
-            self.dx = self.lam * self.f / (4.0 * self.D)
+            # Fig. 18 Stage 1: dx_in = Lambda_edge / (S_samp max(L, 2)), Lambda_edge =
+            # lambda f / R, S_samp = 4; for the amplitude plate (and L = 2) this is
+            # lambda f / (4 D)
+            mult = max(self.levels, 2) if self.kind == FZP_PHASE else 2
+            self.dx = self.lam * self.f / (2.0 * mult * self.D)
         if self.N is None:
             n = int(math.ceil(self.D / self.dx))
             self.N = n + 1 if n % 2 == 0 else n
@@ -184,6 +192,7 @@ class Geometry:
         P = _Params()
         P.N, P.dx, P.lam, P.f, P.R = self.N, self.dx, self.lam, self.f, self.R
         P.M, P.kind, P.p, P.x0 = self.M, self.kind, self.p, self.x0
+        P.levels = self.levels
         P.deform = ctypes.pointer(self._deform_c) if self._deform_c is not None else None
         return P
 
@@ -390,6 +399,14 @@ def circ_mtf(nu_over_cut: float) -> float:
     """Diffraction-limited MTF of a clear circular pupil, (2/pi)(acos v - v sqrt(1 - v^2))."""
     v = nu_over_cut
     return (2.0 / math.pi) * (math.acos(v) - v * math.sqrt(1.0 - v * v))
+
+
+def phase_fzp_efficiency(levels: int) -> float:
+    """First-order efficiency of an L-level phase kinoform, sinc^2(1/L) =
+    (sin(pi/L) / (pi/L))^2 (textbook value for a staircase approximation of a
+    blazed profile; 4/pi^2 = 0.405 for L = 2)."""
+    x = math.pi / levels
+    return (math.sin(x) / x) ** 2
 
 
 def binary_fzp_efficiency() -> float:

@@ -63,7 +63,8 @@ enum {
   ORC_FZP_PARAXIAL = 0, /* binary amplitude FZP, paraxial radii (Eq. 4, Fig. 2) */
   ORC_LENS = 1,         /* ideal thin lens: circ(r<=R) * exp(-i pi r^2/(lambda f)) */
   ORC_FZP_EXACT = 2,    /* binary amplitude FZP, exact radii (Eq. 3)             */
-  ORC_CIRC = 3          /* clear circular pupil (no focusing phase)              */
+  ORC_CIRC = 3,         /* clear circular pupil (no focusing phase)              */
+  ORC_FZP_PHASE = 4     /* L-level phase FZP (Fig. 18 Stage 3), levels = L >= 2  */
 };
 
 /* Deformation of the membrane, w(u,v) in metres; phase phi = (4 pi/lambda) w.
@@ -89,6 +90,8 @@ typedef struct {
   double p;         /* ROI pitch dx_out [m]                                  */
   double x0;        /* first ROI coordinate (both axes) [m]                  */
   const orc_deform* deform; /* NULL: flat membrane                           */
+  int32_t levels;   /* ORC_FZP_PHASE: phase levels L per 2 pi (>= 2)         */
+  int32_t pad2_;
 } orc_params;
 
 /* ------------------------------------------------------------------ */
@@ -120,7 +123,21 @@ static int orc_open(const orc_params* P, int64_t j, int64_t i) {
     const double n = 2.0 * (sqrt(P->f * P->f + r2) - P->f) / P->lambda;
     return ((int64_t)floor(n) & 1) ? 1 : 0;
   }
-  return 1; /* lens / clear pupil: full disc */
+  return 1; /* lens / clear pupil / phase FZP: full disc */
+}
+
+/* Level index of an L-level phase FZP (Fig. 18 Stage 3: z = r^2/(lambda f),
+ * L-level phase).  The lens phase -pi z wrapped to [0, 2 pi) and quantised to
+ * L steps: q = floor(L frac(z / 2)) = floor(s kappa_L) mod L with
+ * kappa_L = fl(kappa * (L/2)), so that for L = 2 the steps are the zones of the
+ * amplitude rule.  Transmission e^{-2 pi i q / L}. */
+static int64_t orc_level(const orc_params* P, int64_t j, int64_t i) {
+  const int64_t c = (P->N - 1) / 2;
+  const int64_t di = i - c, dj = j - c;
+  const int64_t s = di * di + dj * dj;
+  const double kL = orc_kappa(P) * (0.5 * (double)P->levels);
+  const int64_t step = (int64_t)floor((double)s * kL);
+  return step % P->levels;
 }
 
 static double orc_deform_w(const orc_deform* d, double u, double v, double R) {
@@ -143,6 +160,7 @@ static cplx orc_u0(const orc_params* P, int64_t j, int64_t i) {
   const double u = (double)(i - c) * P->dx, v = (double)(j - c) * P->dx;
   cplx a = 1.0;
   if (P->kind == ORC_LENS) a = cexp(-I * M_PI * (u * u + v * v) / (P->lambda * P->f));
+  if (P->kind == ORC_FZP_PHASE) a = cexp(-I * 2.0 * M_PI * (double)orc_level(P, j, i) / (double)P->levels);
   if (P->deform) a *= cexp(I * (4.0 * M_PI / P->lambda) * orc_deform_w(P->deform, u, v, P->R));
   return a;
 }
@@ -150,7 +168,12 @@ static cplx orc_u0(const orc_params* P, int64_t j, int64_t i) {
 int orc_mask_rows(const orc_params* P, int64_t j0, int64_t j1, uint8_t* out) {
   if (!P || !out || j0 < 0 || j1 > P->N || j0 > j1) return 1;
   for (int64_t j = j0; j < j1; ++j)
-    for (int64_t i = 0; i < P->N; ++i) out[(j - j0) * P->N + i] = (uint8_t)orc_open(P, j, i);
+    for (int64_t i = 0; i < P->N; ++i) {
+      const int open = orc_open(P, j, i);
+      /* phase FZP: 1 + level inside the aperture, 0 outside */
+      out[(j - j0) * P->N + i] =
+          (uint8_t)(P->kind == ORC_FZP_PHASE ? (open ? 1 + orc_level(P, j, i) : 0) : open);
+    }
   return 0;
 }
 

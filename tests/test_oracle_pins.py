@@ -302,3 +302,52 @@ def test_mtf_extractor_gaussian(oracle_mod):
     assert np.max(np.abs(mean[has] - ref[has] / cnt[has])) < 1e-10
     # the first sample off DC lands in bin floor(200 * 2 p / (M p)) = 1
     assert np.isfinite(mean[0]) and mean[0] == 1.0
+
+
+@pytest.mark.parametrize("L", [2, 4, 8])
+def test_phase_fzp_efficiency_ladder(oracle_mod, L):
+    """L-level phase FZP (Fig. 18, Stage 3 "L-level phase"; the DE ladder of its
+    report): the first order carries sinc^2(1/L) of the incident power
+    (0.405 / 0.811 / 0.950), so the main lobe holds EE(r_null) sinc^2(1/L); the
+    focal spot is the Airy spot.  Grid of Fig. 18 Stage 1 (S_samp = 4):
+    dx = lambda f / (2 D max(L, 2)).  Measured deviations are about 1e-4."""
+    O = oracle_mod
+    lam = 632.8e-9
+    g = O.Geometry(D=2e-3, f=10e-3, lam=lam, M=256, p=lam * 5 / 8, kind=O.FZP_PHASE, levels=L)
+    assert g.N == {2: 2529, 4: 5057, 8: 10115}[L]
+    m = O.metrics(g, O.field_czt(g))
+    target = O.airy_encircled(O.AIRY_NULL) * O.phase_fzp_efficiency(L)
+    assert abs(m["de_lobe"] / target - 1) < 5e-4
+    airy = O.airy_fwhm_factor() * g.lam * g.f / (2 * g.R)
+    assert abs(m["fwhm_x"] / airy - 1) < 3e-4
+
+
+def test_binary_phase_is_disc_minus_twice_amplitude(oracle_mod):
+    """For L = 2 the level steps are the zones of the amplitude rule (kappa_L =
+    kappa), so the transmission is +1 on even and -1 on odd zones: T_phase =
+    circ - 2 T_amplitude exactly, and the fields obey the same identity (the
+    propagation is linear)."""
+    O = oracle_mod
+    lam = 632.8e-9
+    kw = dict(D=1e-3, f=5e-3, lam=lam, M=64, p=lam * 5 / 8)
+    gp = O.Geometry(kind=O.FZP_PHASE, levels=2, **kw)
+    ga = O.Geometry(kind=O.FZP_PARAXIAL, **kw)
+    gc = O.Geometry(kind=O.CIRC, **kw)
+    assert gp.N == ga.N == gc.N and gp.dx == ga.dx
+    Up, Ua, Uc = O.field_czt(gp), O.field_czt(ga), O.field_czt(gc)
+    assert rel(Up, Uc - 2 * Ua) < 1e-12
+    # the exported level map: 1 + q inside the aperture, q = zone parity here
+    lev = O.mask_rows(gp, 0, gp.N)
+    amp = O.mask_rows(ga, 0, ga.N)
+    disc = O.mask_rows(gc, 0, gc.N)
+    assert np.array_equal(lev, disc * (1 + amp))
+
+
+def test_phase_fzp_direct_equals_czt(oracle_mod):
+    """O1 (Eq. 1 summed literally) and O3 (the Bluestein method) agree for a
+    4-level phase plate on a small grid."""
+    O = oracle_mod
+    lam = 632.8e-9
+    g = O.Geometry(D=0.15e-3, f=0.75e-3, lam=lam, M=24, p=lam * 5 / 8, kind=O.FZP_PHASE, levels=4)
+    assert g.N < 400
+    assert rel(O.field_direct(g), O.field_czt(g)) < 1e-10
