@@ -48,6 +48,14 @@ WORKLOADS = {
     "fzp-d3m": dict(D=3.0, lam=632.8e-9, fnum=5.0, M=512),
     "fzp-d4m": dict(D=4.0, lam=632.8e-9, fnum=5.0, M=512),
     "fzp-d5m": dict(D=5.0, lam=632.8e-9, fnum=5.0, M=512),
+    # the paper's Tables 1-5 (lambda = 532 nm, f/# = 5, dx = Lambda_edge / k with
+    # Lambda_edge = lambda f / R): L-level phase plates; Nx = 12,030,077 /
+    # 12,030,077 / 9,022,557 / 12,030,077 / 15,037,595
+    "fzp-t1": dict(D=1.0, lam=532e-9, fnum=5.0, M=512, levels=16, k=64),
+    "fzp-t2": dict(D=2.0, lam=532e-9, fnum=5.0, M=512, levels=8, k=32),
+    "fzp-t3": dict(D=3.0, lam=532e-9, fnum=5.0, M=512, levels=4, k=16),
+    "fzp-t4": dict(D=4.0, lam=532e-9, fnum=5.0, M=512, levels=4, k=16),
+    "fzp-t5": dict(D=5.0, lam=532e-9, fnum=5.0, M=512, levels=2, k=16),
     # batched deformed membranes (D ~ U[0.05, 0.30] m, 450/550/650 nm, ROI 256^2,
     # seed 0): the first --instances of the 256 draws, one CUDA graph per step
     "membranes": dict(D=0.0, lam=0.0, fnum=5.0, M=256),
@@ -234,16 +242,34 @@ def run_membranes(args, fzp, torch, dev, ws, pg, rank, local):
 
 def _config(args, wl, N):
     """The workload description shared by both arms' JSON lines."""
-    return {"workload": args.workload, "form": args.form, "D_m": wl["D"], "lambda_m": wl["lam"],
-            "f_number": wl["fnum"], "N": N, "samples_per_step": N * N, "roi": wl["M"],
-            "roi_pitch_m": wl["lam"] * wl["fnum"] / 8, "l2": "256 MiB buffer written between steps (flush)"}
+    rows = N if args.rows <= 0 else min(N, args.rows)
+    cfg = {"workload": args.workload, "form": args.form, "D_m": wl["D"], "lambda_m": wl["lam"],
+           "f_number": wl["fnum"], "N": N, "samples_per_step": rows * N, "roi": wl["M"],
+           "roi_pitch_m": wl["lam"] * wl["fnum"] / 8, "l2": "256 MiB buffer written between steps (flush)"}
+    if wl.get("levels"):
+        cfg.update(levels=wl["levels"], dx_m=_dx(wl))
+    if rows < N:
+        cfg["rows_timed"] = f"{rows} central aperture rows of {N} per step (a sample)"
+    return cfg
+
+
+def _dx(wl):
+    """Table workloads: dx = Lambda_edge / k, Lambda_edge = lambda f / R."""
+    return wl["lam"] * wl["D"] * wl["fnum"] / (wl["D"] / 2) / wl["k"]
+
+
+def _oracle_geometry(O, wl):
+    kw = dict(D=wl["D"], f=wl["D"] * wl["fnum"], lam=wl["lam"], M=wl["M"], p=wl["lam"] * wl["fnum"] / 8)
+    if wl.get("levels"):
+        kw.update(kind=O.FZP_PHASE, levels=wl["levels"], dx=_dx(wl))
+    return O.Geometry(**kw)
 
 
 def run_reference(args, wl):
     """The oracle (CPU FP64 Bluestein CZT, fzp_oracle.c) timed on the host cores on
     a bounded sample of aperture rows of the same workload."""
     import oracle as O
-    g = O.Geometry(D=wl["D"], f=wl["D"] * wl["fnum"], lam=wl["lam"], M=wl["M"], p=wl["lam"] * wl["fnum"] / 8)
+    g = _oracle_geometry(O, wl)
     rows = args.ref_rows
     j0 = g.c - rows // 2
     for _ in range(args.warmup):
@@ -266,7 +292,7 @@ def run_reference(args, wl):
 
 def cpu_baseline(wl, budget_s: float = 15.0) -> dict:
     import oracle as O
-    g = O.Geometry(D=wl["D"], f=wl["D"] * wl["fnum"], lam=wl["lam"], M=wl["M"], p=wl["lam"] * wl["fnum"] / 8)
+    g = _oracle_geometry(O, wl)
     # grow the sample until one evaluation takes at least half the budget (small
     # samples carry fixed costs, so one extrapolation undershoots)
     rows = 16
@@ -297,6 +323,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 Bluestein form")
     ap.add_argument("--plain-rows", type=int, default=0, help="rows of the plain form's timed sample (0: all)")
     ap.add_argument("--instances", type=int, default=16, help="membranes workload: instances per batch")
+    ap.add_argument("--rows", type=int, default=0,
+                    help="time only this many central aperture rows per step (a sample; 0: all N)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     ws, rank, local = _dist()
@@ -335,16 +363,20 @@ def main():
     else:
         form, prec, dtype = fzp.FORM_BLUESTEIN, fzp.PREC_FP32, "f32"
     params = dict(D=D, f=D * fnum, lam=lam, M=M, pitch=lam * fnum / 8, form=form, precision=prec)
+    if wl.get("levels"):
+        params.update(levels=wl["levels"], dx=_dx(wl))
     plan = fzp.Plan(**params)
     info = plan.info
     N = info["N"]
+    rows = N if args.rows <= 0 else min(N, args.rows)  # timed rows per step
+    r0 = (N - rows) // 2
     stream = torch.cuda.current_stream(dev)
     U = torch.empty((M, M), dtype=torch.complex128, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MiB > L2 (129 MB)
 
     def step():
         flush.fill_(1.0)  # evict L2 between steps
-        plan.propagate_roi(0, N, U, stream=stream)
+        plan.propagate_roi(r0, r0 + rows, U, stream=stream)
         return plan.metrics(U, stream=stream)
 
     for _ in range(args.warmup):
@@ -375,7 +407,7 @@ def main():
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         ms = float(t.item())
-    value = ws * args.steps * N * N / (ms / 1e3) / 1e9
+    value = ws * args.steps * rows * N / (ms / 1e3) / 1e9
 
     # roofline of the dominant kernel, from CUDA events on its own stream
     peaks, peak_kind = _peaks()
@@ -384,14 +416,14 @@ def main():
         # algorithmic work of the contraction: 2 real rows (Re, Im) x M outputs x
         # 2 flops x 2 split terms per aperture sample = 8 M flops per sample
         launches = max(1, prof["dominant_launches"])
-        flops_launch = 8.0 * M * N * N * args.steps / launches
+        flops_launch = 8.0 * M * rows * N * args.steps / launches
         achieved = flops_launch / (avg_ms / 1e3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": _traffic(args.workload, "dense"), "kernel": prof["dominant_name"], "peak_source": peak_kind + " bf16 sustained"}
     else:
         launches = max(1, prof["dominant_launches"])
-        rows_per_launch = N * args.steps / launches
+        rows_per_launch = rows * args.steps / launches
         flops_launch = bluestein_f2_flops(info, rows_per_launch)
         achieved = flops_launch / (avg_ms / 1e3) / 1e12
         peak = SM_COUNT * 128 * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12  # FP32 FMA lanes x clock
@@ -413,7 +445,7 @@ def main():
         for _ in range(args.e2e_steps):
             with fzp.Plan(**params) as p2:
                 h2d = 8 * p2.info["n_thresholds"] + 96
-                p2.propagate_roi(0, N, U, stream=stream)
+                p2.propagate_roi(r0, r0 + rows, U, stream=stream)
                 host.copy_(U, non_blocking=True)
                 p2.metrics(U, stream=stream)
                 torch.cuda.synchronize(dev)
@@ -422,7 +454,7 @@ def main():
             t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
             pg.all_reduce(t, op=pg.ReduceOp.MAX)
             e2e_s = float(t.item())
-        e2e = {"value": ws * N * N / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": ws * rows * N / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": M * M * 16 + 8 * 28,
                "note": "fzp_plan + fzp_propagate_roi + field to pinned host + fzp_metrics + fzp_plan_destroy"}
     plan.close()

@@ -114,6 +114,14 @@ typedef struct fzp_params {
                           each generating its share of the rows (1, 2 or 4;
                           0 -> the largest of 4, 2, 1 dividing the M/64 tile
                           pairs; other values pad the pairs with zero tiles)      */
+  int32_t levels;      /* 0 or 1: binary amplitude FZP (Fig. 2: open where the
+                          paraxial zone index is odd).  L >= 2: L-level phase FZP
+                          (Fig. 18 Stage 3): transmission e^{-2 pi i q/L} inside
+                          the aperture, q = floor(fl(s kappa_L)) mod L with
+                          kappa_L = fl(kappa L/2), so L = 2 steps on the zones.
+                          The default dx becomes lambda f/(2 D max(L, 2))
+                          (Fig. 18 Stage 1, S_samp = 4).  The dense form takes
+                          L <= 2 (its mask values must be exact in BF16)      */
 } fzp_params;
 
 /* Opaque plan: geometry, zone-threshold table, chirp / kernel tables and the
@@ -145,7 +153,7 @@ typedef struct fzp_plan_info {
                             L = L1 L2 (L itself when L <= the inner limit)        */
   int32_t ctas;          /* dense: CTAs of the persistent row-pass launch (whole
                             clusters that are resident at once)                   */
-  int32_t reserved;
+  int32_t levels;        /* phase levels L (0: binary amplitude FZP)               */
 } fzp_plan_info;
 
 /* Metrics of Fig. 2 Stage 4 / Fig. 18 Stage 5. */

@@ -5,7 +5,8 @@
 // accumulation-chunk lengths, and the FP32 Bluestein form -- times each on a
 // probe stripe of central aperture rows sized to fill the GPU twice with dense
 // work items, and keeps the fastest.  Deformed membranes have complex
-// transmission, which only the Bluestein form supports.  Results are cached
+// transmission, which only the Bluestein form supports, and so have phase
+// plates of more than two levels.  Results are cached
 // per (N, M, deformed) for the process and, when FZP_TUNE_CACHE names a file,
 // in that file (one "key value..." line per problem).
 //
@@ -47,9 +48,9 @@ std::mutex g_tune_mu;
 std::map<std::string, Choice> g_tune;
 bool g_tune_loaded = false;
 
-std::string tune_key(int64_t N, int M, bool deformed) {
+std::string tune_key(int64_t N, int M, bool deformed, int levels) {
   char buf[96];
-  snprintf(buf, sizeof(buf), "N=%lld,M=%d,deformed=%d", (long long)N, M, deformed ? 1 : 0);
+  snprintf(buf, sizeof(buf), "N=%lld,M=%d,deformed=%d,levels=%d", (long long)N, M, deformed ? 1 : 0, levels);
   return buf;
 }
 
@@ -136,7 +137,7 @@ fzp_status autotune(const fzp_params* in, fzp_params* chosen, fzp_plan_t* keep) 
   fzp_status st = validate_and_derive(&probe, geo);
   if (st != FZP_OK) return st;
   const bool deformed = in->deform != nullptr;
-  const std::string key = tune_key(geo.N, geo.M, deformed);
+  const std::string key = tune_key(geo.N, geo.M, deformed, geo.levels);
   *chosen = *in;
   std::lock_guard<std::mutex> lock(g_tune_mu);
   tune_load();
@@ -151,7 +152,7 @@ fzp_status autotune(const fzp_params* in, fzp_params* chosen, fzp_plan_t* keep) 
     return FZP_OK;
   }
   std::vector<Choice> cands;
-  if (!deformed) {
+  if (!deformed && geo.levels <= 2) {  // the dense form's mask values must be exact in BF16
     cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 128, 0, 1, 0});
     cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 256, 0, 1, 0});
     cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 128, 0, 2, 0});

@@ -91,6 +91,14 @@ struct RowArgs {
   int has_deform;
   fzp_deform def;
   double dx, R, inv_lambda;
+  // the deformation phase in turns, 2 w / lambda, as FP32 coefficients:
+  //   amp2 sin(2 pi (di kx + dj ky)) (1 - tq (di^2 + dj^2)) + sum_k h2_k exp(-q_k d_k^2),
+  //   d_k = (di - pi_k) nx_k + (dj - pj_k) ny_k  (sample units; (pi_k, pj_k) on the crease)
+  struct DeformF {
+    float kxh, kxl, kyh, kyl, amp2, tq;  // wrinkle rates split hi + lo, hi a multiple of 2^-14
+    int n;
+    float nx[3], ny[3], pi_[3], pj[3], q[3], h2[3];
+  } df;
   const void* pre;   // N
   const void* H;     // [L1][L2]
   void* Z;           // [rows][L1][L2]
@@ -111,8 +119,34 @@ __device__ __forceinline__ typename Cplx<R>::T aperture(const RowArgs& a, int64_
   typename Cplx<R>::T v;
   v.x = 0; v.y = 0;
   if (i >= a.N) return v;
-  if (!mask_open(j - a.mg.c, i - a.mg.c, a.mg)) return v;
-  if (!a.has_deform) { v.x = 1; return v; }
+  const int64_t dj = j - a.mg.c, di = i - a.mg.c, s = dj * dj + di * di;
+  if (s > a.mg.sR) return v;
+  const int64_t z = zone_of(s, a.mg);
+  if (a.mg.levels >= 2) {
+    // L-level phase plate: e^{-2 pi i q / L}, q = zone mod L (Fig. 18 Stage 3)
+    const int64_t q = z % a.mg.levels;
+    v = cis_turns<R>(-(double)q / (double)a.mg.levels);
+    if (!a.has_deform) return v;
+  } else {
+    if ((z & 1) == 0) return v;  // binary amplitude: open on odd zones
+    v.x = 1;
+    if (!a.has_deform) return v;
+  }
+  if (sizeof(R) == 4) {
+    // FP32 form: the phase is at most about a turn, so FP32 coefficients
+    // (relative error ~1e-7 of it) are far inside the form's tolerance
+    const float fi = (float)di, fj = (float)dj;
+    // turns of the wrinkle: |di| < 2^20 and kxh a multiple of 2^-14 with few
+    // significant bits, so di kxh is exact and its integer part drops exactly
+    const float th = fi * a.df.kxh + fj * a.df.kyh;
+    const float tt = (th - rintf(th)) + (fi * a.df.kxl + fj * a.df.kyl);
+    float wz = a.df.amp2 * sinpif(2.0f * (tt - rintf(tt))) * (1.0f - a.df.tq * (fi * fi + fj * fj));
+    for (int k = 0; k < a.df.n; ++k) {
+      const float d = (fi - a.df.pi_[k]) * a.df.nx[k] + (fj - a.df.pj[k]) * a.df.ny[k];
+      wz += a.df.h2[k] * __expf(-a.df.q[k] * d * d);
+    }
+    return cmul(v, cis_turns<R>((double)wz));
+  }
   const double u = (double)(i - a.mg.c) * a.dx, w = (double)(j - a.mg.c) * a.dx;
   const fzp_deform& d = a.def;
   const double tt = (u * cos(d.theta) + w * sin(d.theta)) / d.period;  // turns
@@ -123,7 +157,7 @@ __device__ __forceinline__ typename Cplx<R>::T aperture(const RowArgs& a, int64_
     const double sg = d.ridge_width[k] / (2.0 * sqrt(2.0 * log(2.0)));
     wz += d.ridge_h[k] * exp(-dist * dist / (2.0 * sg * sg));
   }
-  return cis_turns<R>(2.0 * wz * a.inv_lambda);  // phi / (2 pi) = 2 w / lambda
+  return cmul(v, cis_turns<R>(2.0 * wz * a.inv_lambda));  // phi / (2 pi) = 2 w / lambda
 }
 
 // e^{sign 2 pi i t / L} for 0 <= t < L = L1 * L2 from two tables:
@@ -474,6 +508,28 @@ static RowArgs make_args(const Plan& P) {
   a.has_deform = P.has_deform ? 1 : 0;
   a.def = P.deform;
   a.dx = P.dx; a.R = P.R; a.inv_lambda = 1.0 / P.lambda;
+  if (P.has_deform) {
+    const fzp_deform& d = P.deform;
+    const double k2 = 2.0 / P.lambda;  // metres -> turns of phase (phi / 2 pi = 2 w / lambda)
+    const double kx = std::cos(d.theta) * P.dx / d.period, ky = std::sin(d.theta) * P.dx / d.period;
+    a.df.kxh = (float)(std::rint(kx * 16384.0) / 16384.0);
+    a.df.kyh = (float)(std::rint(ky * 16384.0) / 16384.0);
+    a.df.kxl = (float)(kx - (double)a.df.kxh);
+    a.df.kyl = (float)(ky - (double)a.df.kyh);
+    a.df.amp2 = (float)(d.amp * k2);
+    a.df.tq = (float)(d.taper * P.dx * P.dx / (P.R * P.R));
+    a.df.n = d.n_ridges;
+    for (int k = 0; k < d.n_ridges && k < 3; ++k) {
+      const double nx = -std::sin(d.ridge_alpha[k]), ny = std::cos(d.ridge_alpha[k]);
+      const double sg = d.ridge_width[k] / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+      a.df.nx[k] = (float)nx;
+      a.df.ny[k] = (float)ny;
+      a.df.pi_[k] = (float)(d.ridge_px[k] / P.dx);
+      a.df.pj[k] = (float)(d.ridge_py[k] / P.dx);
+      a.df.q[k] = (float)(P.dx * P.dx / (2.0 * sg * sg));
+      a.df.h2[k] = (float)(d.ridge_h[k] * k2);
+    }
+  }
   a.pre = b.d_pre; a.H = b.d_H; a.Z = b.d_Z; a.G = b.d_G; a.post = b.d_post; a.tw = b.d_tw;
   a.twN = (int)b.L2;
   a.twL = b.d_twL;
@@ -589,7 +645,9 @@ __global__ void k_mask(MaskGeom mg, int64_t N, int64_t j0, int64_t rows, uint8_t
   const int64_t total = rows * N;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = t / N, i = t % N;
-    out[t] = mask_open(j0 + r - mg.c, i - mg.c, mg) ? 1 : 0;
+    const int64_t dj = j0 + r - mg.c, di = i - mg.c, sq = dj * dj + di * di;
+    if (mg.levels >= 2) out[t] = sq > mg.sR ? 0 : (uint8_t)(1 + zone_of(sq, mg) % mg.levels);
+    else out[t] = mask_open(dj, di, mg) ? 1 : 0;
   }
 }
 

@@ -68,6 +68,7 @@ struct DenseArgs {
   int64_t n_stripes;        // ceil((j_end - j_begin) / BN)
   int npairs;               // kernel tile pairs (items per stripe; a multiple of the cluster size)
   int M;                    // ROI side: tiles t with 64 t >= M are zero padding, not stored
+  int signed_mask;          // 1: binary phase plate, T = +1 / -1 on even / odd zones inside the disc
   int promote;              // stages per accumulation chunk
   int hi_only;              // 1: BF16 kernel (hi) only
   const uint8_t* A;         // pre-swizzled kernel tiles, [pair][kb][t0hi t1hi t0lo t1lo]
@@ -104,11 +105,12 @@ __device__ __forceinline__ int64_t isqrt_floor(int64_t t) {  // largest a with a
   return a;
 }
 
-// Smallest a >= 0 with a^2 >= t, for 0 < t < 2^44.  The hardware square root
-// of a float within 2^-12 of t (low bits dropped for t >= 2^24) lands within
+// Smallest a >= 0 with a^2 >= t, for 0 < t < 2^46.  t converted to float
+// (relative error 2^-24) and the approximate square root (relative error
+// below 2^-23) give r within 1.3 of sqrt(t) for a < 2^23, so floor(r) lies in
 // [a - 3, a + 1]; exact integer corrections follow, without branches.
-__device__ __forceinline__ uint32_t ceil_sqrt44(int64_t t) {
-  const float tf = t < (1ll << 24) ? (float)(uint32_t)t : (float)(uint32_t)(t >> 12) * 4096.0f;
+__device__ __forceinline__ uint32_t ceil_sqrt46(int64_t t) {
+  const float tf = __ll2float_rn(t);
   float r;
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(tf));
   uint32_t a = (uint32_t)r;
@@ -132,6 +134,7 @@ struct Walker {
   int64_t next;  // column of event e (INT64_MAX: none left)
   int64_t dj2, c, bmax, zc, ze;
   int32_t e, ne, L, odd;
+  int32_t in;    // the row meets the aperture disc (chord [c - bmax, c + bmax])
 };
 
 __device__ __forceinline__ int64_t walker_event(const Walker& w, int32_t e, const int64_t* __restrict__ thr) {
@@ -141,7 +144,7 @@ __device__ __forceinline__ int64_t walker_event(const Walker& w, int32_t e, cons
   if (b >= 2 * w.L) return w.c + w.bmax + 1;
   const bool left = b < w.L;
   const int64_t m = left ? w.ze - b : w.zc + 1 + (b - w.L);
-  const int64_t a = (int64_t)ceil_sqrt44(__ldg(thr + (m - 1)) - w.dj2);
+  const int64_t a = (int64_t)ceil_sqrt46(__ldg(thr + (m - 1)) - w.dj2);
   return left ? w.c - a + 1 : w.c + a;
 }
 
@@ -149,9 +152,11 @@ __device__ __forceinline__ void walker_init(Walker& w, int64_t j, int64_t j_end,
   w.c = g.c;
   w.e = 0;
   w.ne = 0;
+  w.in = 0;
   w.next = INT64_MAX;
   const int64_t dj = j - g.c;
   if (j >= j_end || dj * dj > g.sR) return;
+  w.in = 1;
   w.dj2 = dj * dj;
   w.bmax = isqrt_floor(g.sR - w.dj2);
   w.zc = zone_of(w.dj2, g);
@@ -234,13 +239,23 @@ __device__ __forceinline__ uint32_t block_bits(const Walker& w, int64_t i0, cons
       } else if (b >= 2 * w.L) {
         col = w.c + w.bmax + 1;  // chord end
       } else {
-        const int64_t aa = (int64_t)ceil_sqrt44((int64_t)S - w.dj2);
+        const int64_t aa = (int64_t)ceil_sqrt46((int64_t)S - w.dj2);
         col = left ? w.c - aa + 1 : w.c + aa;
       }
       bits ^= 0xFFFFFFFFu << (uint32_t)(col - i0);
     }
   }
   return bits;
+}
+
+// Columns [i0, i0 + 32) of the row that lie on its chord of the aperture disc.
+__device__ __forceinline__ uint32_t disc_bits(const Walker& w, int64_t i0) {
+  if (!w.in) return 0u;
+  const int64_t lo = w.c - w.bmax - i0, hi = w.c + w.bmax - i0;  // inclusive, relative to i0
+  if (hi < 0 || lo > 31) return 0u;
+  const uint32_t a = lo <= 0 ? 0xFFFFFFFFu : (0xFFFFFFFFu << (uint32_t)lo);
+  const uint32_t b = hi >= 31 ? 0xFFFFFFFFu : (0xFFFFFFFFu >> (uint32_t)(31 - hi));
+  return a & b;
 }
 
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
@@ -263,6 +278,16 @@ __device__ __forceinline__ void expand_bits(uint32_t bits, uint32_t (&w)[16]) {
     const uint32_t sel = (uint32_t)((8 | q) | ((8 | q) << 4) | ((8 | (4 + q)) << 8) | ((8 | (4 + q)) << 12));
     w[k] = prmt(y[j], y[j + 1], sel) & 0x3F803F80u;
   }
+}
+
+// Binary phase plate: +1 (0x3F80) on the disc, -1 (0xBF80) where also on an
+// odd zone (odd is a subset of disc), 0 off the disc.
+__device__ __forceinline__ void expand_signed(uint32_t disc, uint32_t odd, uint32_t (&w)[16]) {
+  uint32_t mag[16], sgn[16];
+  expand_bits(disc, mag);
+  expand_bits(odd, sgn);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) w[k] = mag[k] | ((sgn[k] << 8) & 0x80008000u);
 }
 
 // ---------------------------------------------------------------- kernel
@@ -455,7 +480,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
       const uint32_t bits = CL == 1 ? walker_bits(w, kb * BK, state, a.mg.thr) : block_bits(w, kb * BK, a.mg);
       uint8_t* rowp = rowbase0 + stage * B_BYTES;
       uint32_t wd[16];
-      expand_bits(bits, wd);
+      if (a.signed_mask) expand_signed(disc_bits(w, kb * BK), bits, wd);
+      else expand_bits(bits, wd);
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         *reinterpret_cast<uint4*>(rowp + ((q ^ sw) << 4)) = make_uint4(wd[4 * q], wd[4 * q + 1], wd[4 * q + 2], wd[4 * q + 3]);
@@ -726,6 +752,7 @@ fzp_status dense_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
   const int CL = d.cluster;
   a.npairs = d.npairs;
   a.M = P.M;
+  a.signed_mask = P.levels == 2 ? 1 : 0;
   a.promote = d.promote_kblocks;
   a.hi_only = P.precision == FZP_PREC_BF16 ? 1 : 0;
   a.A = reinterpret_cast<const uint8_t*>(d.d_A);

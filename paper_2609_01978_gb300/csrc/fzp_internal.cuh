@@ -46,16 +46,20 @@ struct MaskGeom {
   uint64_t K64;       // floor(kappa * 2^64): fixed-point zone rate
   const int64_t* thr; // device: thr[m-1] = S_m, m = 1..nthr
   int64_t nthr;
+  int levels;         // 0: binary amplitude (open on odd zones); L >= 2: phase level = zone mod L
 };
 
-// zone(s) for 0 <= s <= sR.  The 64x64->128 fixed-point product gives
-// floor(s kappa) except within 2^-19 of an integer; there the threshold table
-// decides, which reproduces floor(fl(s kappa)) bit for bit.
+// zone(s) for 0 <= s <= sR (the zone rate kappa is kappa_L for phase plates).
+// The 64x64->128 fixed-point product s K64 / 2^64 lies below s kappa by less
+// than s / 2^64 < 2^-18 (s < 2^46), and fl(s kappa) differs from s kappa by
+// less than 2^-29 (s kappa < 2^24); so outside a window of 2^-17 below and
+// 2^-28 above an integer the product's integer part is floor(fl(s kappa)), and
+// inside it the threshold table decides, bit for bit.
 __device__ __forceinline__ int64_t zone_of(int64_t s, const MaskGeom& g) {
   const uint64_t hi = __umul64hi((uint64_t)s, g.K64);
   const uint64_t lo = (uint64_t)s * g.K64;
   int64_t z = (int64_t)hi;
-  if (lo < (1ull << 31) || lo >= 0xFFFFE00000000000ull) {
+  if (lo < (1ull << 36) || lo >= 0xFFFF800000000000ull) {
     if (z >= 1 && __ldg(g.thr + (z - 1)) > s) z -= 1;
     else if (z < g.nthr && __ldg(g.thr + z) <= s) z += 1;
   }
@@ -156,6 +160,8 @@ struct Plan {
   // derived
   double kappa, delta, dx2, R2;
   int64_t total_zones;
+  int levels = 0;               // 0: binary amplitude FZP; L >= 2: L-level phase FZP
+  double kappa_mask = 0;        // zone rate of the mask rule: kappa, or kappa_L = fl(kappa L/2)
   MaskGeom mg;
   int64_t* d_thr = nullptr;
   bool has_deform = false;

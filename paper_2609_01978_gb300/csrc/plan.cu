@@ -110,9 +110,13 @@ fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
     return set_error(FZP_E_INVALID, "unknown precision");
   if (in->deform && (in->deform->n_ridges < 0 || in->deform->n_ridges > 3))
     return set_error(FZP_E_INVALID, "deform.n_ridges must be in [0, 3]");
+  if (in->levels < 0 || in->levels > 64) return set_error(FZP_E_INVALID, "levels must be in [0, 64]");
+  P.levels = in->levels >= 2 ? in->levels : 0;
   const double lf = in->lambda * in->f;
   P.D = in->D; P.f = in->f; P.lambda = in->lambda; P.p = in->pitch; P.M = in->M;
-  P.dx = in->dx > 0 ? in->dx : lf / (4.0 * in->D);
+  // Fig. 2 / Fig. 18 Stage 1: dx_in = Lambda_edge / (S_samp max(L, 2)), Lambda_edge =
+  // lambda f / R, S_samp = 4: lambda f / (4 D) for the amplitude plate and L = 2
+  P.dx = in->dx > 0 ? in->dx : lf / (2.0 * (P.levels > 2 ? P.levels : 2) * in->D);
   // Eq. 6: dx <= lambda f / (2 D)  (two samples across the outermost zone)
   if (P.dx > lf / (2.0 * in->D) * (1.0 + 1e-12))
     return set_error(FZP_E_INVALID, "dx = %g violates Eq. 6 (dx <= lambda f / (2D) = %g)", P.dx, lf / (2.0 * in->D));
@@ -131,6 +135,7 @@ fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
   P.dx2 = P.dx * P.dx;
   P.R2 = P.R * P.R;
   P.kappa = P.dx2 / lf;
+  P.kappa_mask = P.levels >= 2 ? P.kappa * (0.5 * (double)P.levels) : P.kappa;
   P.delta = P.p * P.dx / lf;  // Eq. 10: W = exp(-2 pi i dx_out dx_in / (lambda z))
   // Eq. 3 zone count: (lambda^2/4) n^2 + lambda f n - R^2 = 0
   {
@@ -146,6 +151,8 @@ fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
     return set_error(FZP_E_UNSUPPORTED, "dense form runs in split-BF16 or BF16 precision only");
   if (P.form == FZP_FORM_BLUESTEIN && dense_prec)
     return set_error(FZP_E_UNSUPPORTED, "Bluestein form runs in FP32 or FP64 precision only");
+  if (P.form == FZP_FORM_DENSE && P.levels > 2)
+    return set_error(FZP_E_UNSUPPORTED, "dense form: phase plates with more than 2 levels need complex mask values");
   if (in->deform) {
     if (P.form == FZP_FORM_DENSE)
       return set_error(FZP_E_UNSUPPORTED, "deformation phase is supported by the Bluestein form only");
@@ -164,16 +171,17 @@ fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
 fzp_status build_mask_tables(Plan& P) {
   P.mg.c = P.c;
   P.mg.sR = disc_limit(P.dx2, P.R2);
-  const int64_t zmax = zone_host(P.mg.sR, P.kappa);
-  // zone_of() error analysis needs s_R < 2^44 and zone < 2^19.
-  if (P.mg.sR >= (1ll << 44) || zmax + 1 >= (1ll << 19))
+  P.mg.levels = P.levels;
+  const int64_t zmax = zone_host(P.mg.sR, P.kappa_mask);
+  // zone_of() error analysis needs s_R < 2^46 and zone < 2^24.
+  if (P.mg.sR >= (1ll << 46) || zmax + 1 >= (1ll << 24))
     return set_error(FZP_E_UNSUPPORTED, "aperture too large for the exact zone rule (s_R=%lld, zones=%lld)",
                      (long long)P.mg.sR, (long long)zmax);
-  const double k64 = std::ldexp(P.kappa, 64);
+  const double k64 = std::ldexp(P.kappa_mask, 64);
   if (!(k64 < 18446744073709551616.0)) return set_error(FZP_E_INVALID, "kappa >= 1: grid far too coarse");
   P.mg.K64 = (uint64_t)std::floor(k64);
   std::vector<int64_t> S;
-  thresholds(P.kappa, zmax + 2, S);
+  thresholds(P.kappa_mask, zmax + 2, S);
   P.mg.nthr = (int64_t)S.size();
   FZP_CUDA_TRY(cudaMalloc(&P.d_thr, S.size() * sizeof(int64_t)));
   P.device_bytes += S.size() * sizeof(int64_t);
@@ -276,6 +284,7 @@ fzp_status fzp_plan_info_get(fzp_plan_t plan, fzp_plan_info* out) {
   out->cluster = P.form == FZP_FORM_DENSE ? P.dn.cluster : 0;
   out->fft_inner = P.form == FZP_FORM_BLUESTEIN ? (int32_t)P.bs.L2 : 0;
   out->ctas = P.form == FZP_FORM_DENSE ? P.dn.max_ctas : 0;
+  out->levels = P.levels;
   out->device_bytes = P.device_bytes;
   return FZP_OK;
 }
@@ -317,8 +326,11 @@ fzp_status fzp_aperture_mask(fzp_plan_t plan, int64_t row_begin, int64_t row_end
                      (long long)row_end, (long long)P.N);
   if (row_end == row_begin) return FZP_OK;
   uint8_t* out = reinterpret_cast<uint8_t*>(d_mask);
-  return P.form == FZP_FORM_DENSE ? dense_mask(P, row_begin, row_end - row_begin, out, (cudaStream_t)stream)
-                                  : bluestein_mask(P, row_begin, row_end - row_begin, out, (cudaStream_t)stream);
+  // the dense form exports through its own row walker (amplitude plates); level
+  // maps of phase plates come from the per-sample rule
+  return P.form == FZP_FORM_DENSE && P.levels < 2
+             ? dense_mask(P, row_begin, row_end - row_begin, out, (cudaStream_t)stream)
+             : bluestein_mask(P, row_begin, row_end - row_begin, out, (cudaStream_t)stream);
 }
 
 fzp_status fzp_profile_enable(fzp_plan_t plan, int enable) {

@@ -127,3 +127,49 @@ def test_d_sweep_sampled_rows(env, D, form):
             _, I = run_plan(fzp, torch, plan, g.M, j0, j0 + 8)
             err = rel_l2(I, _SWEEP_REF[key])
             assert err <= 1e-4, (D, form, j0, err)
+
+
+def test_section41_validation_configuration(env):
+    """Sec. 4.1's validation configuration: binary negative-centred amplitude FZP,
+    D = 0.08 m, f = 1.5 m, lambda0 = 532 nm (N = 32,081 at four samples per
+    outermost zone width).  The paper reports the CZT method's DE 1.16 % above
+    its reference 0.0840 (Fig. 7 discussion); the FZP's main lobe converges to
+    EE(r_null)/pi^2 = 0.084885, 1.05 % above 0.0840.  Both forms agree with the
+    oracle's extractor on sampled stripes and with each other on the metrics."""
+    fzp, torch, O = env
+    lam = 532e-9
+    g = O.Geometry(D=0.08, f=1.5, lam=lam, M=512, p=lam * (1.5 / 0.08) / 8)
+    assert g.N == 32081
+    out = {}
+    for form, prec in [(fzp.FORM_DENSE, fzp.PREC_SPLIT_BF16), (fzp.FORM_BLUESTEIN, fzp.PREC_FP32)]:
+        with fzp.Plan(D=g.D, f=g.f, lam=g.lam, M=g.M, pitch=g.p, form=form, precision=prec) as plan:
+            U = torch.empty((g.M, g.M), dtype=torch.complex128, device="cuda")
+            plan.propagate_roi(0, g.N, U)
+            out[form] = plan.metrics(U)
+            j0 = g.c - 128
+            _, I = run_plan(fzp, torch, plan, g.M, j0, j0 + 256)
+            assert rel_l2(I, np.abs(O.field_czt(g, j0, j0 + 256)) ** 2) <= 1e-4
+    md, mb = out[fzp.FORM_DENSE], out[fzp.FORM_BLUESTEIN]
+    assert abs(md["de_lobe"] - mb["de_lobe"]) < 1e-4 and abs(md["fwhm_x"] / mb["fwhm_x"] - 1) < 1e-4
+    err = md["de_lobe"] / 0.0840 - 1
+    assert abs(err - 0.0116) < 3e-3, err
+    airy = O.airy_fwhm_factor() * lam * g.f / (2 * g.R)
+    assert abs(md["fwhm_x"] / airy - 1) < 2e-3
+    print(f"Sec. 4.1: DE {md['de_lobe']:.6f} ({100 * err:.2f} % vs 0.0840), FWHM/Airy - 1 = "
+          f"{md['fwhm_x'] / airy - 1:.2e}, Strehl {md['strehl']:.4f}")
+
+
+def test_resume_groups_equal_one_pass(env, tmp_path):
+    """Row-group checkpoints through the device plan: the summed group fields
+    equal one propagation over all rows, and a second run reuses them."""
+    fzp, torch, O = env
+    from paper_2609_01978_gb300 import resume
+    g = O.Geometry(D=4e-3, f=20e-3, lam=632.8e-9, M=256, p=0.2e-6)
+    with fzp.Plan(D=g.D, f=g.f, lam=g.lam, M=g.M, pitch=g.p, form=fzp.FORM_BLUESTEIN,
+                  precision=fzp.PREC_FP64) as plan:
+        U1, _ = run_plan(fzp, torch, plan, g.M, 0, g.N)
+        params = {"D": g.D, "f": g.f, "lambda": g.lam, "N": g.N, "M": g.M, "precision": "fp64"}
+        run = resume.GroupRun(str(tmp_path), params, g.M, 0, g.N, 700)
+        U2 = run.run(resume.plan_source(plan, torch))
+        assert np.max(np.abs(U2 - U1)) <= 1e-12 * np.max(np.abs(U1))
+        assert resume.GroupRun(str(tmp_path), params, g.M, 0, g.N, 700).pending() == []

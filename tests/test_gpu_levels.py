@@ -1,0 +1,124 @@
+"""L-level phase FZPs (Fig. 18, Stage 3) through the C ABI against the oracle:
+the level map bit for bit, the field in FP64 / FP32 (Bluestein form) and, for
+L = 2, in split-BF16 (dense form, signed mask), the metric extractor, and the
+paper's own large configurations (Tables 4-5) on sampled rows."""
+import numpy as np
+import pytest
+
+from gpu_util import rel_l2, run_plan
+
+pytestmark = pytest.mark.gpu
+LAM = 532e-9  # Sec. 1
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    import paper_2609_01978_gb300 as fzp
+    return fzp, torch, oracle
+
+
+def _plan(fzp, g, form, prec):
+    return fzp.Plan(D=g.D, f=g.f, lam=g.lam, M=g.M, pitch=g.p, dx=g.dx, N=g.N, form=form, precision=prec,
+                    levels=g.levels)
+
+
+def _level_rows(fzp, torch, plan, j0, j1, N):
+    out = torch.empty(((j1 - j0) * N,), dtype=torch.uint8, device="cuda")
+    plan.aperture_mask(j0, j1, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().reshape(j1 - j0, N)
+
+
+@pytest.mark.parametrize("L", [2, 4, 8, 16])
+def test_level_map_bit_exact(env, L):
+    fzp, torch, O = env
+    g = O.Geometry(D=2e-3, f=10e-3, lam=LAM, M=64, p=LAM * 5 / 8, kind=O.FZP_PHASE, levels=L)
+    with _plan(fzp, g, fzp.FORM_BLUESTEIN, fzp.PREC_FP32) as plan:
+        assert plan.info["N"] == g.N and plan.info["levels"] == L
+        rng = np.random.default_rng(L)
+        for j0 in [g.c - 3, 0, g.N - 4, int(rng.integers(0, g.N - 4)), int(rng.integers(0, g.N - 4))]:
+            got = _level_rows(fzp, torch, plan, j0, j0 + 4, g.N)
+            assert np.array_equal(got, O.mask_rows(g, j0, j0 + 4)), (L, j0)
+
+
+def test_level_map_table4_grid(env):
+    """Table 4 (D = 4 m, f = 20 m, L = 4, dx = Lambda_edge / 16, Nx = 12,030,077):
+    751,880 level steps, sampled rows bit for bit."""
+    fzp, torch, O = env
+    D, f = 4.0, 20.0
+    dx = LAM * f / (D / 2) / 16
+    g = O.Geometry(D=D, f=f, lam=LAM, M=512, p=LAM * 5 / 8, dx=dx, kind=O.FZP_PHASE, levels=4)
+    assert g.N == 12030077
+    with _plan(fzp, g, fzp.FORM_BLUESTEIN, fzp.PREC_FP32) as plan:
+        for j0 in [g.c - 1, g.N // 7, g.N - 2_000_000]:
+            got = _level_rows(fzp, torch, plan, j0, j0 + 2, g.N)
+            assert np.array_equal(got, O.mask_rows(g, j0, j0 + 2)), j0
+
+
+@pytest.mark.parametrize("L", [2, 4, 8])
+def test_phase_field_parity(env, L):
+    fzp, torch, O = env
+    g = O.Geometry(D=1e-3, f=5e-3, lam=LAM, M=64, p=LAM * 5 / 8, kind=O.FZP_PHASE, levels=L)
+    Uref = O.field_czt(g)
+    Iref = np.abs(Uref) ** 2
+    cases = [(fzp.FORM_BLUESTEIN, fzp.PREC_FP64, 1e-6), (fzp.FORM_BLUESTEIN, fzp.PREC_FP32, 1e-4)]
+    if L == 2:
+        cases.append((fzp.FORM_DENSE, fzp.PREC_SPLIT_BF16, 1e-4))
+    for form, prec, tol in cases:
+        with _plan(fzp, g, form, prec) as plan:
+            U, I = run_plan(fzp, torch, plan, g.M, 0, g.N)
+            assert rel_l2(I, Iref) <= tol, (L, form, prec, rel_l2(I, Iref))
+            assert rel_l2(U, Uref) <= 10 * tol, (L, form, prec)
+
+
+def test_dense_rejects_multilevel(env):
+    fzp, torch, O = env
+    with pytest.raises(fzp.FzpError):
+        fzp.Plan(D=1e-3, f=5e-3, lam=LAM, M=64, pitch=LAM * 5 / 8, form=fzp.FORM_DENSE,
+                 precision=fzp.PREC_SPLIT_BF16, levels=4)
+
+
+@pytest.mark.parametrize("L", [4, 8])
+def test_phase_metrics_and_ladder(env, L):
+    """The device extractor on the device field: DE and FWHM equal the oracle's
+    (0.01 pp, 0.01 %) and follow the sinc^2(1/L) ladder."""
+    fzp, torch, O = env
+    g = O.Geometry(D=2e-3, f=10e-3, lam=LAM, M=256, p=LAM * 5 / 8, kind=O.FZP_PHASE, levels=L)
+    mref = O.metrics(g, O.field_czt(g))
+    with _plan(fzp, g, fzp.FORM_BLUESTEIN, fzp.PREC_FP32) as plan:
+        U = torch.empty((g.M, g.M), dtype=torch.complex128, device="cuda")
+        plan.propagate_roi(0, g.N, U)
+        m = plan.metrics(U)
+    assert abs(m["de_lobe"] - mref["de_lobe"]) < 1e-4
+    assert abs(m["fwhm_x"] / mref["fwhm_x"] - 1) < 1e-4
+    target = O.airy_encircled(O.AIRY_NULL) * O.phase_fzp_efficiency(L)
+    assert abs(m["de_lobe"] / target - 1) < 1e-3
+
+
+_T5_REF = {}
+
+
+@pytest.mark.parametrize("form", ["dense", "bluestein"])
+def test_table5_sampled_rows(env, form):
+    """Table 5: D = 5 m, f = 25 m, L = 2, dx = Lambda_edge / 16, Nx = 15,037,595,
+    ROI 512^2 at lambda f/# / 8: 8 central rows and 8 rows at v = -0.75 R
+    against the oracle (relative L2 of I <= 1e-4)."""
+    fzp, torch, O = env
+    D, f = 5.0, 25.0
+    dx = LAM * f / (D / 2) / 16
+    g = O.Geometry(D=D, f=f, lam=LAM, M=512, p=LAM * 5 / 8, dx=dx, kind=O.FZP_PHASE, levels=2)
+    assert g.N == 15037595
+    fm, pr = (fzp.FORM_DENSE, fzp.PREC_SPLIT_BF16) if form == "dense" else (fzp.FORM_BLUESTEIN, fzp.PREC_FP32)
+    with _plan(fzp, g, fm, pr) as plan:
+        for j0 in [g.c - 4, g.N // 8]:
+            _, I = run_plan(fzp, torch, plan, g.M, j0, j0 + 8)
+            if j0 not in _T5_REF:
+                _T5_REF[j0] = np.abs(O.field_czt(g, j0, j0 + 8)) ** 2
+            Iref = _T5_REF[j0]
+            assert rel_l2(I, Iref) <= 1e-4, (form, j0, rel_l2(I, Iref))
