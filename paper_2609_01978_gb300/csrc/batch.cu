@@ -304,7 +304,7 @@ static fzp_status batch_enqueue(Plan& P, void* field, cudaStream_t s) {
     const int64_t rows = std::min(P.chunk_rows, jhi - j0);
     st = P.form == FZP_FORM_DENSE ? dense_rows(P, j0, rows, s) : bluestein_rows(P, j0, rows, s);
     if (st != FZP_OK) return st;
-    st = column_pass(P, j0, rows, s);
+    st = column_pass_tc_applies(P) ? column_pass_tc(P, j0, rows, s) : column_pass(P, j0, rows, s);
     if (st != FZP_OK) return st;
   }
   return epilogue(P, field, 0, s);

@@ -205,6 +205,8 @@ fzp_status dense_fill_tables(Plan& P, cudaStream_t s);
 fzp_status dense_build_tables(Plan& P);
 fzp_status dense_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream);
 fzp_status column_pass(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream);
+bool column_pass_tc_applies(const Plan& P);
+fzp_status column_pass_tc(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream);
 fzp_status epilogue(Plan& P, void* d_field, int accumulate, cudaStream_t stream);
 fzp_status intensity(Plan& P, const void* d_field, void* d_I, cudaStream_t stream);
 fzp_status metrics(Plan& P, const void* d_field, cudaStream_t stream, fzp_metrics_t* out);

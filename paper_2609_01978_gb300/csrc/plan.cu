@@ -312,7 +312,7 @@ fzp_status fzp_propagate_roi(fzp_plan_t plan, int64_t row_begin, int64_t row_end
     const int64_t rows = std::min(P.chunk_rows, b - j0);
     fzp_status st = (P.form == FZP_FORM_DENSE) ? dense_rows(P, j0, rows, s) : bluestein_rows(P, j0, rows, s);
     if (st != FZP_OK) return st;
-    st = column_pass(P, j0, rows, s);
+    st = column_pass_tc_applies(P) ? column_pass_tc(P, j0, rows, s) : column_pass(P, j0, rows, s);
     if (st != FZP_OK) return st;
   }
   return epilogue(P, d_field, accumulate, s);
