@@ -70,8 +70,8 @@ KERNEL_SOURCES = {
     "bluestein": ["bluestein.cu", "fzp_internal.cuh"],
 }
 TRAFFIC = {
-    ("fzp-d0.25m", "dense"): (702.89e9 + 98.67e9,
-                              "458e1d693f499f468803b3b21cfe66dc2dadfdd7d7ce856ac09a5b75ea6f5413"),
+    ("fzp-d0.25m", "dense"): (672.70e9 + 98.57e9,
+                              "fb557032443315cf4a07c8072d7a3b987840e2f11b1644da430fcc78653a843d"),
 }
 METRIC = "aperture Gsamples/s into 512² ROI, split-BF16 vs FP32 CZT at ≤1e-4 PSF error"
 UNIT = "Gsamples/s"

@@ -62,6 +62,51 @@ __device__ void dit(C* x, int logn, int batch, const C* __restrict__ tw, int twN
   }
 }
 
+// The same transform with two radix-2 stages per pass (radix 2^2): each work
+// item takes the four elements k, k + h, k + 2h, k + 3h of a group of 4h
+// (h = 2^(s-1)), applies stage s to the pairs (0,1), (2,3) and stage s + 1 to
+// (0,2), (1,3) in registers; a single radix-2 stage finishes odd lengths.
+// tws[t] = e^{-2 pi i t / n} for t < n / 2, in shared memory.
+template <typename C>
+__device__ void dit22(C* x, int logn, int batch, const C* tws, int colstride) {
+  const int n = 1 << logn;
+  int s = 1;
+  for (; s + 1 <= logn; s += 2) {
+    const int h = 1 << (s - 1);
+    const int items = (n >> 2) * batch;
+    for (int t = threadIdx.x; t < items; t += blockDim.x) {
+      const int col = t >> (logn - 2), g = t & ((n >> 2) - 1);
+      const int k = g & (h - 1);
+      const int i0 = col * colstride + ((g >> (s - 1)) << (s + 1)) + k;
+      const C w1 = tws[k << (logn - s)];
+      const C w2 = tws[k << (logn - s - 1)], w3 = tws[(k + h) << (logn - s - 1)];
+      C a0 = x[i0], a1 = x[i0 + h], a2 = x[i0 + 2 * h], a3 = x[i0 + 3 * h];
+      const C v1 = cmul(a1, w1), v3 = cmul(a3, w1);
+      const C b0 = cadd(a0, v1), b1 = csub(a0, v1), b2 = cadd(a2, v3), b3 = csub(a2, v3);
+      const C u2 = cmul(b2, w2), u3 = cmul(b3, w3);
+      x[i0] = cadd(b0, u2);
+      x[i0 + 2 * h] = csub(b0, u2);
+      x[i0 + h] = cadd(b1, u3);
+      x[i0 + 3 * h] = csub(b1, u3);
+    }
+    __syncthreads();
+  }
+  if (s == logn) {  // one radix-2 stage left
+    const int h = 1 << (s - 1);
+    const int items = (n >> 1) * batch;
+    for (int t = threadIdx.x; t < items; t += blockDim.x) {
+      const int col = t >> (logn - 1), b = t & ((n >> 1) - 1);
+      const int k = b & (h - 1);
+      const int i0 = col * colstride + ((b >> (s - 1)) << s) + k;
+      const C w = tws[k << (logn - s)];
+      const C a0 = x[i0], v = cmul(x[i0 + h], w);
+      x[i0] = cadd(a0, v);
+      x[i0 + h] = csub(a0, v);
+    }
+    __syncthreads();
+  }
+}
+
 // In-place radix-2 DIF, natural input, bit-reversed output, inverse sign (no 1/n).
 template <typename C>
 __device__ void dif_inverse(C* x, int logn, const C* __restrict__ tw, int twN) {
@@ -87,7 +132,7 @@ struct RowArgs {
   int logL1, logL2, M;
   int64_t j0;        // first aperture row of this launch
   int64_t rows;      // rows in this launch
-  int B;             // columns per F1 block
+  int B, logB;       // columns per F1 block (a power of two)
   int has_deform;
   fzp_deform def;
   double dx, R, inv_lambda;
@@ -191,9 +236,12 @@ __global__ void __launch_bounds__(256) k_f1(RowArgs a, int mode) {
   const int L1 = (int)a.L1;
   const C* pre = reinterpret_cast<const C*>(a.pre);
   const C* vin = reinterpret_cast<const C*>(a.vin);
+  C* tws = sm + (L1 + 1) * B;  // L1 / 2 twiddles of the column FFT
+  for (int t = threadIdx.x; t < (L1 >> 1); t += blockDim.x)
+    tws[t] = reinterpret_cast<const C*>(a.tw)[t * (a.twN / L1)];
   // load, bit-reversed within each column
   for (int t = threadIdx.x; t < L1 * B; t += blockDim.x) {
-    const int n1 = t / B, b = t % B;
+    const int n1 = t >> a.logB, b = t & (B - 1);
     const int64_t n = (int64_t)n1 * a.L2 + n2_0 + b;
     C x;
     if (mode == 0) {
@@ -205,10 +253,10 @@ __global__ void __launch_bounds__(256) k_f1(RowArgs a, int mode) {
     sm[b * (L1 + 1) + brev(n1, a.logL1)] = x;  // odd column stride: no bank conflicts across columns
   }
   __syncthreads();
-  dit(sm, a.logL1, B, reinterpret_cast<const C*>(a.tw), a.twN, L1 + 1);
+  dit22(sm, a.logL1, B, tws, L1 + 1);
   C* Z = reinterpret_cast<C*>(a.Z) + r * a.L;
   for (int t = threadIdx.x; t < L1 * B; t += blockDim.x) {
-    const int k1 = t / B, b = t % B;
+    const int k1 = t >> a.logB, b = t & (B - 1);
     const int64_t n2 = n2_0 + b;
     const C w = twiddle_L<R>(a, n2 * k1, false);
     Z[(int64_t)k1 * a.L2 + n2] = cmul(sm[b * (L1 + 1) + k1], w);
@@ -493,6 +541,11 @@ __global__ void k_tables(int64_t N, int M, int64_t L, int64_t c, double kappa, d
   }
 }
 
+template <typename R>
+static size_t f1_smem(const RowArgs& a) {
+  return sizeof(typename Cplx<R>::T) * (size_t)((a.L1 + 1) * a.B + a.L1 / 2);
+}
+
 static RowArgs make_args(const Plan& P) {
   const Bluestein& b = P.bs;
   RowArgs a{};
@@ -502,8 +555,9 @@ static RowArgs make_args(const Plan& P) {
   {
     const int64_t csz = P.precision == FZP_PREC_FP64 ? 16 : 8;
     int64_t B = 16;
-    while (B > 1 && B * (b.L1 + 1) * csz > 65536) B >>= 1;
+    while (B > 1 && (B * (b.L1 + 1) + b.L1 / 2) * csz > 65536) B >>= 1;
     a.B = (int)std::min<int64_t>(B, b.L2);
+    a.logB = ilog2(a.B);
   }
   a.has_deform = P.has_deform ? 1 : 0;
   a.def = P.deform;
@@ -564,7 +618,8 @@ fzp_status layout_t(Plan& P, FormSizes* out) {
   out->G = b.L1 > 1 ? sizeof(C) * b.L1 * P.M * b.rows : 0;
   static bool attrs = false;
   if (!attrs) {
-    FZP_CUDA_TRY(cudaFuncSetAttribute(k_f1<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+    // 64 KiB covers every FP32 case; FP64 at L1 = 4096 needs ~96 KiB
+    FZP_CUDA_TRY(cudaFuncSetAttribute(k_f1<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     FZP_CUDA_TRY(cudaFuncSetAttribute(k_f2<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(sizeof(C) * Traits<R>::L2MAX)));
     attrs = true;
@@ -587,7 +642,7 @@ fzp_status fill_tables_t(Plan& P, cudaStream_t s) {
   RowArgs a = make_args(P);
   a.j0 = 0;
   a.rows = 1;
-  if (b.L1 > 1) k_f1<R><<<dim3((unsigned)(b.L2 / a.B), 1), 256, sizeof(C) * (b.L1 + 1) * a.B, s>>>(a, 1);
+  if (b.L1 > 1) k_f1<R><<<dim3((unsigned)(b.L2 / a.B), 1), 256, f1_smem<R>(a), s>>>(a, 1);
   if (sizeof(R) == 4 && b.L2 == RL) k_f2_r16<<<dim3((unsigned)b.L1, 1), RT, 0, s>>>(a, 1);
   else k_f2<R><<<dim3((unsigned)b.L1, 1), 512, sizeof(C) * b.L2, s>>>(a, 1);
   FZP_CUDA_TRY(cudaGetLastError());
@@ -622,7 +677,7 @@ fzp_status rows_t(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
     a.j0 = j0 + r0;
     a.rows = rb;
     if (b.L1 > 1) {
-      k_f1<R><<<dim3((unsigned)(b.L2 / a.B), (unsigned)rb), 256, sizeof(C) * (b.L1 + 1) * a.B, s>>>(a, 0);
+      k_f1<R><<<dim3((unsigned)(b.L2 / a.B), (unsigned)rb), 256, f1_smem<R>(a), s>>>(a, 0);
       prof_begin(P, s);
       if (sizeof(R) == 4 && b.L2 == RL) k_f2_r16<<<dim3((unsigned)b.L1, (unsigned)rb), RT, 0, s>>>(a, 0);
       else k_f2<R><<<dim3((unsigned)b.L1, (unsigned)rb), 512, sizeof(C) * b.L2, s>>>(a, 0);
