@@ -414,9 +414,10 @@ def main():
     avg_ms = prof["dominant_ms"] / max(1, prof["dominant_launches"])
     if args.form == "dense":
         # algorithmic work of the contraction: 2 real rows (Re, Im) x M outputs x
-        # 2 flops x 2 split terms per aperture sample = 8 M flops per sample
+        # 2 flops x 2 split terms per aperture sample = 8 M flops per sample and
+        # mask pass (a phase plate with L >= 4 takes L/2 passes)
         launches = max(1, prof["dominant_launches"])
-        flops_launch = 8.0 * M * rows * N * args.steps / launches
+        flops_launch = 8.0 * M * rows * N * info["passes"] * args.steps / launches
         achieved = flops_launch / (avg_ms / 1e3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,

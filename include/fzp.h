@@ -121,7 +121,9 @@ typedef struct fzp_params {
                           kappa_L = fl(kappa L/2), so L = 2 steps on the zones.
                           The default dx becomes lambda f/(2 D max(L, 2))
                           (Fig. 18 Stage 1, S_samp = 4).  The dense form takes
-                          L <= 2 (its mask values must be exact in BF16)      */
+                          even L: L = 2 as one +-1 mask, L >= 4 as L/2 passes of
+                          masks with values -1, 0, +1 (exact in BF16) whose
+                          fields are summed with the weights of Re T and Im T */
 } fzp_params;
 
 /* Opaque plan: geometry, zone-threshold table, chirp / kernel tables and the
@@ -154,6 +156,9 @@ typedef struct fzp_plan_info {
   int32_t ctas;          /* dense: CTAs of the persistent row-pass launch (whole
                             clusters that are resident at once)                   */
   int32_t levels;        /* phase levels L (0: binary amplitude FZP)               */
+  int32_t passes;        /* dense form: signed-mask passes per row chunk (1, or L/2
+                            for a phase plate with L >= 4)                         */
+  int32_t reserved;
 } fzp_plan_info;
 
 /* Metrics of Fig. 2 Stage 4 / Fig. 18 Stage 5. */

@@ -58,7 +58,7 @@ class PlanInfo(ctypes.Structure):
                 ("fft_length", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
                 ("promote", ctypes.c_int32), ("row_batch", ctypes.c_int32), ("chunk_rows", ctypes.c_int64),
                 ("cluster", ctypes.c_int32), ("fft_inner", ctypes.c_int32), ("ctas", ctypes.c_int32),
-                ("levels", ctypes.c_int32)]
+                ("levels", ctypes.c_int32), ("passes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Metrics(ctypes.Structure):

@@ -152,7 +152,7 @@ fzp_status autotune(const fzp_params* in, fzp_params* chosen, fzp_plan_t* keep) 
     return FZP_OK;
   }
   std::vector<Choice> cands;
-  if (!deformed && geo.levels <= 2) {  // the dense form's mask values must be exact in BF16
+  if (!deformed && geo.levels % 2 == 0) {  // the dense form's mask values must be exact in BF16
     cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 128, 0, 1, 0});
     cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 256, 0, 1, 0});
     cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 128, 0, 2, 0});
@@ -302,9 +302,7 @@ static fzp_status batch_enqueue(Plan& P, void* field, cudaStream_t s) {
   disc_rows(P, jlo, jhi);
   for (int64_t j0 = jlo; j0 < jhi; j0 += P.chunk_rows) {
     const int64_t rows = std::min(P.chunk_rows, jhi - j0);
-    st = P.form == FZP_FORM_DENSE ? dense_rows(P, j0, rows, s) : bluestein_rows(P, j0, rows, s);
-    if (st != FZP_OK) return st;
-    st = column_pass_tc_applies(P) ? column_pass_tc(P, j0, rows, s) : column_pass(P, j0, rows, s);
+    st = chunk_passes(P, j0, rows, s);
     if (st != FZP_OK) return st;
   }
   return epilogue(P, field, 0, s);

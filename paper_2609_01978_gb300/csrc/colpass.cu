@@ -23,6 +23,7 @@ struct ColArgs {
   int64_t c, j0, rows, c1_stride;
   int M;
   double kappa, delta;
+  double wr, wi;  // weight of this pass's field (1, 0 for a single-pass plate)
 };
 
 template <typename R> struct RowPhase;
@@ -121,8 +122,9 @@ __global__ void __launch_bounds__(256) k_colpass(ColArgs g, const R* __restrict_
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int n = n0 + tn + 16 * a, m = m0 + tm + 16 * b;
-      atomicAdd(&Uacc[(int64_t)n * g.M + m].x, (double)acc[a][b].x);
-      atomicAdd(&Uacc[(int64_t)n * g.M + m].y, (double)acc[a][b].y);
+      const double ux = (double)acc[a][b].x, uy = (double)acc[a][b].y;
+      atomicAdd(&Uacc[(int64_t)n * g.M + m].x, g.wr * ux - g.wi * uy);
+      atomicAdd(&Uacc[(int64_t)n * g.M + m].y, g.wr * uy + g.wi * ux);
     }
 }
 
@@ -154,7 +156,11 @@ __global__ void k_intensity(int64_t count, const double2* __restrict__ U, double
 }  // namespace
 
 fzp_status column_pass(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
-  ColArgs g{P.c, j0, rows, P.chunk_rows, P.M, P.kappa, P.delta};
+  ColArgs g{P.c, j0, rows, P.chunk_rows, P.M, P.kappa, P.delta, 1.0, 0.0};
+  if (P.pass_index >= 0) {
+    g.wr = P.passes[P.pass_index].wr;
+    g.wi = P.passes[P.pass_index].wi;
+  }
   dim3 grid((unsigned)(P.M / TM), (unsigned)(P.M / TN), (unsigned)((rows + JC - 1) / JC));
   if (P.precision == FZP_PREC_FP64) k_colpass<double><<<grid, 256, 0, s>>>(g, P.d_C1d, P.d_Uacc);
   else k_colpass<float><<<grid, 256, 0, s>>>(g, P.d_C1, P.d_Uacc);

@@ -69,6 +69,7 @@ struct ColTcArgs {
   int64_t kb_lo, nkb;       // table K blocks covering [j0, j0 + rows)
   int slices;               // K slices per output tile
   double2* Uacc;            // [n][m]
+  double wr, wi;            // weight of this pass's field (1, 0 for a single-pass plate)
   int* err;
 };
 
@@ -289,19 +290,31 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_colpass_tc(const ColTcArgs a) 
             const uint32_t cre = (uint32_t)(128 * q + r0), cim = cre + 64u;
             const int n0 = 128 * nt + 64 * q + r0;
             float x[32], y[32];
+            // U += (wr + i wi)(Re + i Im): Re feeds x with wr and y with wi,
+            // Im feeds x with -wi and y with wr (zero weights are skipped)
             tmem_ld32(tl + cre, x);         // D1 at Re K columns
             tmem_ld32(tl + 256u + cim, y);  // D2 at Im K columns
             if (m < a.M) {
 #pragma unroll
               for (int k = 0; k < 32; ++k)
-                if (n0 + k < a.M) atomicAdd(&a.Uacc[(int64_t)(n0 + k) * a.M + m].x, (double)(x[k] - y[k]));
+                if (n0 + k < a.M) {
+                  const double re = (double)(x[k] - y[k]);
+                  double2* u = &a.Uacc[(int64_t)(n0 + k) * a.M + m];
+                  if (a.wr != 0.0) atomicAdd(&u->x, a.wr * re);
+                  if (a.wi != 0.0) atomicAdd(&u->y, a.wi * re);
+                }
             }
             tmem_ld32(tl + 256u + cre, x);  // D2 at Re K columns
             tmem_ld32(tl + cim, y);         // D1 at Im K columns
             if (m < a.M) {
 #pragma unroll
               for (int k = 0; k < 32; ++k)
-                if (n0 + k < a.M) atomicAdd(&a.Uacc[(int64_t)(n0 + k) * a.M + m].y, (double)(x[k] + y[k]));
+                if (n0 + k < a.M) {
+                  const double im = (double)(x[k] + y[k]);
+                  double2* u = &a.Uacc[(int64_t)(n0 + k) * a.M + m];
+                  if (a.wr != 0.0) atomicAdd(&u->y, a.wr * im);
+                  if (a.wi != 0.0) atomicAdd(&u->x, -a.wi * im);
+                }
             }
           }
         }
@@ -352,6 +365,8 @@ fzp_status column_pass_tc(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
   slices = std::max<int64_t>(1, std::min<int64_t>(slices, a.nkb / 16));
   a.slices = (int)slices;
   a.Uacc = reinterpret_cast<double2*>(P.d_Uacc);
+  a.wr = P.pass_index >= 0 ? P.passes[P.pass_index].wr : 1.0;
+  a.wi = P.pass_index >= 0 ? P.passes[P.pass_index].wi : 0.0;
   a.err = P.d_err;
   const int64_t units = tiles2 * slices;
   const int grid = (int)std::min<int64_t>(units, P.dn.num_sms);

@@ -69,6 +69,9 @@ struct DenseArgs {
   int npairs;               // kernel tile pairs (items per stripe; a multiple of the cluster size)
   int M;                    // ROI side: tiles t with 64 t >= M are zero padding, not stored
   int signed_mask;          // 1: binary phase plate, T = +1 / -1 on even / odd zones inside the disc
+  int level_mode;           // 1: phase plate pass: +1 on levels in pos, -1 on levels in neg
+  int lmod;                 // level count L (level = zone step mod L)
+  uint64_t pos, neg;        // level sets of the pass (bit q)
   int promote;              // stages per accumulation chunk
   int hi_only;              // 1: BF16 kernel (hi) only
   const uint8_t* A;         // pre-swizzled kernel tiles, [pair][kb][t0hi t1hi t0lo t1lo]
@@ -148,7 +151,10 @@ __device__ __forceinline__ int64_t walker_event(const Walker& w, int32_t e, cons
   return left ? w.c - a + 1 : w.c + a;
 }
 
-__device__ __forceinline__ void walker_init(Walker& w, int64_t j, int64_t j_end, const MaskGeom& g) {
+// level_events: the chord's two ends are events of every row (a phase plate
+// is nonzero on the whole chord); otherwise only where the edge zone is open.
+__device__ __forceinline__ void walker_init(Walker& w, int64_t j, int64_t j_end, const MaskGeom& g,
+                                            bool level_events = false) {
   w.c = g.c;
   w.e = 0;
   w.ne = 0;
@@ -162,7 +168,7 @@ __device__ __forceinline__ void walker_init(Walker& w, int64_t j, int64_t j_end,
   w.zc = zone_of(w.dj2, g);
   w.ze = zone_of(w.dj2 + w.bmax * w.bmax, g);
   w.L = (int32_t)(w.ze - w.zc);
-  w.odd = (int32_t)(w.ze & 1);
+  w.odd = level_events ? 1 : (int32_t)(w.ze & 1);
   w.ne = 2 * w.L + 2 * w.odd;
   w.next = walker_event(w, 0, g.thr);
 }
@@ -246,6 +252,80 @@ __device__ __forceinline__ uint32_t block_bits(const Walker& w, int64_t i0, cons
     }
   }
   return bits;
+}
+
+// Zone step of the row after its first e events (walker with level events):
+// -1 before the chord start or after its end.
+__device__ __forceinline__ int32_t zone_after(const Walker& w, int32_t e) {
+  if (e <= 0 || e >= w.ne) return -1;
+  const int32_t nb = e - 1;  // zone boundaries passed
+  return nb <= w.L ? (int32_t)w.ze - nb : (int32_t)w.zc + (nb - w.L);
+}
+
+// Phase-plate pass: bits of columns [i0, i0 + 32) where the level (zone step
+// mod lmod) is in `pos` (out_pos) or in `neg` (out_neg); whole warp, like
+// block_bits, whose event search and threshold staging it shares.  Between two
+// events the zone step is constant, so each block is a few runs of columns.
+__device__ __forceinline__ void block_values(const Walker& w, int64_t i0, const MaskGeom& g, int lmod, uint64_t pos,
+                                             uint64_t neg, uint32_t& out_pos, uint32_t& out_neg) {
+  const int32_t e0 = walker_count(w, i0 - 1, g);
+  const int32_t e1 = walker_count(w, i0 + 31, g);
+  int32_t mlo = INT32_MAX, mhi = INT32_MIN;
+  const int32_t b0 = max(e0 - w.odd, 0), b1 = min(e1 - w.odd, 2 * w.L);
+  if (w.ne > 0 && b1 > b0) {
+    if (b0 < w.L) {
+      mlo = (int32_t)w.ze - (min(b1, w.L) - 1);
+      mhi = (int32_t)w.ze - b0;
+    }
+    if (b1 > w.L) {
+      mlo = min(mlo, (int32_t)w.zc + 1 + (max(b0, w.L) - w.L));
+      mhi = max(mhi, (int32_t)w.zc + (b1 - w.L));
+    }
+  }
+  const int32_t wlo = __reduce_min_sync(0xffffffffu, mlo);
+  const int32_t whi = __reduce_max_sync(0xffffffffu, mhi);
+  const int32_t nev = (int32_t)__reduce_max_sync(0xffffffffu, (uint32_t)(e1 - e0));
+  const bool staged = whi >= wlo && whi - wlo < 32;
+  const int lane = threadIdx.x & 31;
+  long long tv = 0;
+  if (staged && wlo + lane <= whi) tv = __ldg(g.thr + (wlo + lane - 1));
+  uint32_t P = 0u, Q = 0u;
+  int32_t z = zone_after(w, e0);
+  uint32_t c0 = 0;  // first column of the current run, relative to i0
+  auto fill = [&](int32_t zz, uint32_t a, uint32_t b) {
+    if (zz < 0 || b <= a) return;
+    const int q = zz % lmod;
+    const uint32_t m = (b >= 32 ? 0xFFFFFFFFu : ((1u << b) - 1u)) & ~((1u << a) - 1u);
+    if ((pos >> q) & 1ull) P |= m;
+    if ((neg >> q) & 1ull) Q |= m;
+  };
+  for (int32_t t = 0; t < nev; ++t) {
+    const int32_t e = e0 + t, b = e - w.odd;
+    const bool valid = e < e1;
+    const bool bnd = valid && b >= 0 && b < 2 * w.L;
+    const bool left = b < w.L;
+    const int32_t m = bnd ? (left ? (int32_t)w.ze - b : (int32_t)w.zc + 1 + (b - w.L)) : wlo;
+    long long S = __shfl_sync(0xffffffffu, tv, (m - wlo) & 31);
+    if (bnd && !staged) S = __ldg(g.thr + (m - 1));
+    if (valid) {
+      int64_t col;
+      if (b < 0) {
+        col = w.c - w.bmax;
+      } else if (b >= 2 * w.L) {
+        col = w.c + w.bmax + 1;
+      } else {
+        const int64_t aa = (int64_t)ceil_sqrt46((int64_t)S - w.dj2);
+        col = left ? w.c - aa + 1 : w.c + aa;
+      }
+      const uint32_t cc = (uint32_t)(col - i0);
+      fill(z, c0, cc);
+      z = zone_after(w, e + 1);
+      c0 = cc;
+    }
+  }
+  fill(z, c0, 32u);
+  out_pos = P;
+  out_neg = Q;
 }
 
 // Columns [i0, i0 + 32) of the row that lie on its chord of the aperture disc.
@@ -462,7 +542,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
       if (ui != cur_unit) {
         cur_unit = ui;
         const int64_t s = (u0 + ui * ustep) % a.n_stripes;
-        walker_init(w, a.j_begin + s * BN + row, a.j_end, a.mg);
+        walker_init(w, a.j_begin + s * BN + row, a.j_end, a.mg, a.level_mode != 0);
         state = 0;
       }
       // One thread per phase waits for the stage; the phase's warps take its
@@ -475,13 +555,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
                             : 0;
       named_bar_sync(1 + ph, WPS * 32);
       if (!gen_ok[slot]) break;
-      // one CTA, consecutive blocks: walk the row; clusters: each phase takes every
-      // CL-th block, found directly
-      const uint32_t bits = CL == 1 ? walker_bits(w, kb * BK, state, a.mg.thr) : block_bits(w, kb * BK, a.mg);
       uint8_t* rowp = rowbase0 + stage * B_BYTES;
       uint32_t wd[16];
-      if (a.signed_mask) expand_signed(disc_bits(w, kb * BK), bits, wd);
-      else expand_bits(bits, wd);
+      if (a.level_mode) {
+        // phase-plate pass: +1 / -1 on the pass's level sets
+        uint32_t pb, nb;
+        block_values(w, kb * BK, a.mg, a.lmod, a.pos, a.neg, pb, nb);
+        expand_signed(pb | nb, nb, wd);
+      } else {
+        // one CTA, consecutive blocks: walk the row; clusters: each phase takes
+        // every CL-th block, found directly
+        const uint32_t bits = CL == 1 ? walker_bits(w, kb * BK, state, a.mg.thr) : block_bits(w, kb * BK, a.mg);
+        if (a.signed_mask) expand_signed(disc_bits(w, kb * BK), bits, wd);
+        else expand_bits(bits, wd);
+      }
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         *reinterpret_cast<uint4*>(rowp + ((q ^ sw) << 4)) = make_uint4(wd[4 * q], wd[4 * q + 1], wd[4 * q + 2], wd[4 * q + 3]);
@@ -753,6 +840,12 @@ fzp_status dense_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
   a.npairs = d.npairs;
   a.M = P.M;
   a.signed_mask = P.levels == 2 ? 1 : 0;
+  a.level_mode = P.pass_index >= 0 ? 1 : 0;
+  a.lmod = P.levels > 0 ? P.levels : 2;
+  if (P.pass_index >= 0) {
+    a.pos = P.passes[P.pass_index].pos;
+    a.neg = P.passes[P.pass_index].neg;
+  }
   a.promote = d.promote_kblocks;
   a.hi_only = P.precision == FZP_PREC_BF16 ? 1 : 0;
   a.A = reinterpret_cast<const uint8_t*>(d.d_A);

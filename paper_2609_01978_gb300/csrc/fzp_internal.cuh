@@ -138,6 +138,14 @@ struct Bluestein {
   int64_t rows = 0;       // rows per batch of the workspace
 };
 
+// One signed-mask pass of a phase plate in the dense form: the mask is +1 on
+// the levels in `pos`, -1 on those in `neg` (bit q for level q), 0 elsewhere,
+// and the pass's field enters the ROI accumulator times (wr + i wi).
+struct MaskPass {
+  uint64_t pos = 0, neg = 0;
+  double wr = 1.0, wi = 0.0;
+};
+
 struct Dense {
   void* d_A = nullptr;     // kernel matrix, split-BF16, pre-swizzled tiles
   int64_t kblocks = 0;     // ceil(N / 32)
@@ -161,6 +169,8 @@ struct Plan {
   double kappa, delta, dx2, R2;
   int64_t total_zones;
   int levels = 0;               // 0: binary amplitude FZP; L >= 2: L-level phase FZP
+  std::vector<MaskPass> passes; // dense form, L >= 4: the signed-mask passes summing to T
+  int pass_index = -1;          // pass being run (-1: the plate's single pass)
   double kappa_mask = 0;        // zone rate of the mask rule: kappa, or kappa_L = fl(kappa L/2)
   MaskGeom mg;
   int64_t* d_thr = nullptr;
@@ -206,6 +216,9 @@ fzp_status dense_build_tables(Plan& P);
 fzp_status dense_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream);
 fzp_status column_pass(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream);
 bool column_pass_tc_applies(const Plan& P);
+// Row pass and column pass of rows [j0, j0 + rows) (every mask pass of a dense
+// phase plate), accumulated into the ROI accumulator.
+fzp_status chunk_passes(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream);
 fzp_status column_pass_tc(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream);
 fzp_status epilogue(Plan& P, void* d_field, int accumulate, cudaStream_t stream);
 fzp_status intensity(Plan& P, const void* d_field, void* d_I, cudaStream_t stream);

@@ -151,8 +151,29 @@ fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
     return set_error(FZP_E_UNSUPPORTED, "dense form runs in split-BF16 or BF16 precision only");
   if (P.form == FZP_FORM_BLUESTEIN && dense_prec)
     return set_error(FZP_E_UNSUPPORTED, "Bluestein form runs in FP32 or FP64 precision only");
-  if (P.form == FZP_FORM_DENSE && P.levels > 2)
-    return set_error(FZP_E_UNSUPPORTED, "dense form: phase plates with more than 2 levels need complex mask values");
+  if (P.form == FZP_FORM_DENSE && P.levels > 2) {
+    // T = e^{-2 pi i q/L} = sum over passes of w (pos - neg): Re T by magnitude
+    // classes cos(2 pi k/L) > 0, Im T by sin(2 pi k/L) > 0; each pass's mask
+    // is -1 / 0 / +1, exact in BF16 (L/2 passes)
+    if (P.levels % 2) return set_error(FZP_E_UNSUPPORTED, "dense form: phase plates need an even level count");
+    const int L = P.levels;
+    for (int k = 0; 4 * k < L; ++k) {
+      MaskPass mp;
+      mp.pos = (1ull << (k % L)) | (1ull << ((L - k) % L));
+      mp.neg = (1ull << ((L / 2 - k) % L)) | (1ull << ((L / 2 + k) % L));
+      mp.wr = std::cos(2.0 * M_PI * k / L);
+      mp.wi = 0.0;
+      P.passes.push_back(mp);
+    }
+    for (int k = 1; 4 * k <= L; ++k) {
+      MaskPass mp;
+      mp.neg = (1ull << (k % L)) | (1ull << ((L / 2 - k) % L));
+      mp.pos = (1ull << ((L / 2 + k) % L)) | (1ull << ((L - k) % L));
+      mp.wr = 0.0;
+      mp.wi = std::sin(2.0 * M_PI * k / L);
+      P.passes.push_back(mp);
+    }
+  }
   if (in->deform) {
     if (P.form == FZP_FORM_DENSE)
       return set_error(FZP_E_UNSUPPORTED, "deformation phase is supported by the Bluestein form only");
@@ -188,6 +209,19 @@ fzp_status build_mask_tables(Plan& P) {
   FZP_CUDA_TRY(cudaMemcpy(P.d_thr, S.data(), S.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
   P.mg.thr = P.d_thr;
   return FZP_OK;
+}
+
+fzp_status chunk_passes(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
+  const int np = (P.form == FZP_FORM_DENSE && !P.passes.empty()) ? (int)P.passes.size() : 1;
+  fzp_status st = FZP_OK;
+  for (int k = 0; k < np && st == FZP_OK; ++k) {
+    P.pass_index = np > 1 || !P.passes.empty() ? k : -1;
+    st = (P.form == FZP_FORM_DENSE) ? dense_rows(P, j0, rows, s) : bluestein_rows(P, j0, rows, s);
+    if (st == FZP_OK)
+      st = column_pass_tc_applies(P) ? column_pass_tc(P, j0, rows, s) : column_pass(P, j0, rows, s);
+  }
+  P.pass_index = -1;
+  return st;
 }
 
 // Rows per row-pass chunk: requested (multiple of 256), else as many as an
@@ -285,6 +319,7 @@ fzp_status fzp_plan_info_get(fzp_plan_t plan, fzp_plan_info* out) {
   out->fft_inner = P.form == FZP_FORM_BLUESTEIN ? (int32_t)P.bs.L2 : 0;
   out->ctas = P.form == FZP_FORM_DENSE ? P.dn.max_ctas : 0;
   out->levels = P.levels;
+  out->passes = P.passes.empty() ? 1 : (int32_t)P.passes.size();
   out->device_bytes = P.device_bytes;
   return FZP_OK;
 }
@@ -309,10 +344,7 @@ fzp_status fzp_propagate_roi(fzp_plan_t plan, int64_t row_begin, int64_t row_end
   disc_rows(P, jlo, jhi);
   const int64_t a = std::max(row_begin, jlo), b = std::min(row_end, jhi);
   for (int64_t j0 = a; j0 < b; j0 += P.chunk_rows) {
-    const int64_t rows = std::min(P.chunk_rows, b - j0);
-    fzp_status st = (P.form == FZP_FORM_DENSE) ? dense_rows(P, j0, rows, s) : bluestein_rows(P, j0, rows, s);
-    if (st != FZP_OK) return st;
-    st = column_pass_tc_applies(P) ? column_pass_tc(P, j0, rows, s) : column_pass(P, j0, rows, s);
+    const fzp_status st = chunk_passes(P, j0, std::min(P.chunk_rows, b - j0), s);
     if (st != FZP_OK) return st;
   }
   return epilogue(P, d_field, accumulate, s);

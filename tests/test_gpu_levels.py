@@ -67,9 +67,8 @@ def test_phase_field_parity(env, L):
     g = O.Geometry(D=1e-3, f=5e-3, lam=LAM, M=64, p=LAM * 5 / 8, kind=O.FZP_PHASE, levels=L)
     Uref = O.field_czt(g)
     Iref = np.abs(Uref) ** 2
-    cases = [(fzp.FORM_BLUESTEIN, fzp.PREC_FP64, 1e-6), (fzp.FORM_BLUESTEIN, fzp.PREC_FP32, 1e-4)]
-    if L == 2:
-        cases.append((fzp.FORM_DENSE, fzp.PREC_SPLIT_BF16, 1e-4))
+    cases = [(fzp.FORM_BLUESTEIN, fzp.PREC_FP64, 1e-6), (fzp.FORM_BLUESTEIN, fzp.PREC_FP32, 1e-4),
+             (fzp.FORM_DENSE, fzp.PREC_SPLIT_BF16, 1e-4)]  # dense: L/2 signed-mask passes
     for form, prec, tol in cases:
         with _plan(fzp, g, form, prec) as plan:
             U, I = run_plan(fzp, torch, plan, g.M, 0, g.N)
@@ -77,11 +76,31 @@ def test_phase_field_parity(env, L):
             assert rel_l2(U, Uref) <= 10 * tol, (L, form, prec)
 
 
-def test_dense_rejects_multilevel(env):
+def test_dense_rejects_odd_level_counts(env):
     fzp, torch, O = env
     with pytest.raises(fzp.FzpError):
         fzp.Plan(D=1e-3, f=5e-3, lam=LAM, M=64, pitch=LAM * 5 / 8, form=fzp.FORM_DENSE,
-                 precision=fzp.PREC_SPLIT_BF16, levels=4)
+                 precision=fzp.PREC_SPLIT_BF16, levels=3)
+
+
+@pytest.mark.parametrize("L", [4, 16])
+def test_dense_multilevel_sampled_rows(env, L):
+    """Dense form, L/2 signed passes: Table 4's grid (L = 4, D = 4 m, Nx =
+    12,030,077) and L = 16 on a small aperture, sampled rows against the oracle."""
+    fzp, torch, O = env
+    if L == 4:
+        D, f = 4.0, 20.0
+        g = O.Geometry(D=D, f=f, lam=LAM, M=512, p=LAM * 5 / 8, dx=LAM * f / (D / 2) / 16, kind=O.FZP_PHASE,
+                       levels=4)
+        ranges = [(g.c - 4, g.c + 4), (g.N // 8, g.N // 8 + 8)]
+    else:
+        g = O.Geometry(D=2e-3, f=10e-3, lam=LAM, M=256, p=LAM * 5 / 8, kind=O.FZP_PHASE, levels=16)
+        ranges = [(0, g.N)]
+    with _plan(fzp, g, fzp.FORM_DENSE, fzp.PREC_SPLIT_BF16) as plan:
+        for (j0, j1) in ranges:
+            _, I = run_plan(fzp, torch, plan, g.M, j0, j1)
+            Iref = np.abs(O.field_czt(g, j0, j1)) ** 2
+            assert rel_l2(I, Iref) <= 1e-4, (L, j0, rel_l2(I, Iref))
 
 
 @pytest.mark.parametrize("L", [4, 8])
