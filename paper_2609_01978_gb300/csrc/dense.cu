@@ -10,24 +10,29 @@
 // K_hi T^T + K_lo T^T is accumulated into the same accumulator, so the product
 // carries the ~16 significant bits of the split kernel.
 //
-// GB300 mapping (tcgen05, one CTA per SM, persistent over items):
-//   item     : one stripe of 256 aperture rows x one pair of kernel tiles
-//              (2 x 128 kernel rows = 128 values of m, Re and Im); the mask
-//              tile generated for a stage feeds both tiles (hi and lo each)
+// GB300 mapping (tcgen05, one CTA per SM, persistent over units, clusters of
+// CL = 4 CTAs for M = 512):
+//   unit     : one stripe of 256 aperture rows x one pair of kernel tiles
+//              (2 x 128 kernel rows = 128 values of m, Re and Im); the CL CTAs
+//              of a cluster take CL pairs of the same stripe
 //   stage    : K step of 32 columns, 64-byte-swizzled K-major operands
 //              (A 32 KiB: [t0 hi][t1 hi][t0 lo][t1 lo]; B 16 KiB), 4 stages
 //   warp 8   : copies the A stage, pre-swizzled in HBM, with one cp.async.bulk
-//   warps 10-17: mask generators, one aperture row each; a walker carries the
-//              zone state along the row and yields the columns where the binary
-//              transmission toggles (exact integer thresholds)
+//   warps 10-17: mask generators in CL phases; each CTA generates 256 / CL of the
+//              stripe's rows for every CL-th stage (two zone evaluations give a
+//              block's toggle events; the thresholds of a warp's rows come from
+//              one coalesced load) and bulk-copies them to its peers' shared memory
 //   warp 9   : allocates 512 TMEM columns and issues tcgen05.mma (M128 N256 K16)
-//              into two FP32 accumulators (one per tile)
+//              into two FP32 accumulators (one per tile), completion multicast
+//              to the cluster's empty barriers
 //   warps 0-7: epilogue; every `promote` stages both accumulators are read with
-//              tcgen05.ld and added in FP32 to the C1 tiles in global memory
-//              (stored for the first chunk, red.global.add afterwards).
-//              The tensor core's FP32 accumulation loses precision in proportion
-//              to the chunk length (measured: 8e-4 relative error of I over a
-//              0.25 m aperture without promotion, 8e-6 with 4096-sample chunks).
+//              tcgen05.ld into shared memory and written to C1 by TMA (store
+//              for the first chunk, reduce-add afterwards).  The tensor core's
+//              FP32 accumulation loses precision in proportion to the chunk
+//              length (measured: 8e-4 relative error of I over a 0.25 m
+//              aperture without promotion, 8e-6 with 4096-sample chunks).
+// Phase plates: L = 2 as a +-1 mask (disc and odd-zone bits); L >= 4 as L/2
+// passes of -1 / 0 / +1 masks on level sets (level mode of the generator).
 // Every mbarrier wait is bounded in time; on expiry the kernel records an error
 // code, drains what it issued, frees tensor memory and returns.
 #include <cuda.h>
