@@ -297,9 +297,10 @@ __device__ __forceinline__ void block_values(const Walker& w, int64_t i0, const 
   uint32_t P = 0u, Q = 0u;
   int32_t z = zone_after(w, e0);
   uint32_t c0 = 0;  // first column of the current run, relative to i0
+  const int lmask = (lmod & (lmod - 1)) == 0 ? lmod - 1 : -1;  // power-of-two L: a mask, no division
   auto fill = [&](int32_t zz, uint32_t a, uint32_t b) {
     if (zz < 0 || b <= a) return;
-    const int q = zz % lmod;
+    const int q = lmask >= 0 ? (zz & lmask) : zz % lmod;
     const uint32_t m = (b >= 32 ? 0xFFFFFFFFu : ((1u << b) - 1u)) & ~((1u << a) - 1u);
     if ((pos >> q) & 1ull) P |= m;
     if ((neg >> q) & 1ull) Q |= m;
