@@ -210,13 +210,22 @@ __device__ __forceinline__ int32_t walker_count(const Walker& w, int64_t X, cons
 // neighbouring rows, form one short contiguous range of m (at most ~17 at four
 // samples per outermost zone), read with one coalesced load and handed to the
 // lanes by shuffles.  The events are independent of each other, so the block
-// costs one memory round trip instead of one per toggle.
-__device__ __forceinline__ uint32_t block_bits(const Walker& w, int64_t i0, const MaskGeom& g) {
-  const int32_t e0 = walker_count(w, i0 - 1, g);
-  const int32_t e1 = walker_count(w, i0 + 31, g);
+// costs one memory round trip instead of one per toggle.  In two halves:
+// block_prep finds the events and issues the threshold load, block_finish
+// turns them into bits; the generator prepares its next block before it
+// finishes the current one, so the load's latency is hidden.
+struct BlockPrep {
+  int32_t e0, e1, wlo, nev;
+  int staged;
+  long long tv;
+};
+
+__device__ __forceinline__ void block_prep(const Walker& w, int64_t i0, const MaskGeom& g, BlockPrep& p) {
+  p.e0 = walker_count(w, i0 - 1, g);
+  p.e1 = walker_count(w, i0 + 31, g);
   // thresholds of this lane's boundary events: b = e - odd in [b0, b1) within [0, 2L)
   int32_t mlo = INT32_MAX, mhi = INT32_MIN;
-  const int32_t b0 = max(e0 - w.odd, 0), b1 = min(e1 - w.odd, 2 * w.L);
+  const int32_t b0 = max(p.e0 - w.odd, 0), b1 = min(p.e1 - w.odd, 2 * w.L);
   if (w.ne > 0 && b1 > b0) {
     if (b0 < w.L) {  // left boundaries: m = ze - b
       mlo = (int32_t)w.ze - (min(b1, w.L) - 1);
@@ -227,22 +236,26 @@ __device__ __forceinline__ uint32_t block_bits(const Walker& w, int64_t i0, cons
       mhi = max(mhi, (int32_t)w.zc + (b1 - w.L));
     }
   }
-  const int32_t wlo = __reduce_min_sync(0xffffffffu, mlo);
+  p.wlo = __reduce_min_sync(0xffffffffu, mlo);
   const int32_t whi = __reduce_max_sync(0xffffffffu, mhi);
-  const int32_t nev = (int32_t)__reduce_max_sync(0xffffffffu, (uint32_t)(e1 - e0));
-  const bool staged = whi >= wlo && whi - wlo < 32;
+  p.nev = (int32_t)__reduce_max_sync(0xffffffffu, (uint32_t)(p.e1 - p.e0));
+  p.staged = (whi >= p.wlo && whi - p.wlo < 32) ? 1 : 0;
   const int lane = threadIdx.x & 31;
-  long long tv = 0;
-  if (staged && wlo + lane <= whi) tv = __ldg(g.thr + (wlo + lane - 1));
-  uint32_t bits = 0u - ((uint32_t)e0 & 1u);
-  for (int32_t t = 0; t < nev; ++t) {
-    const int32_t e = e0 + t, b = e - w.odd;
-    const bool valid = e < e1;
+  p.tv = 0;
+  if (p.staged && p.wlo + lane <= whi) p.tv = __ldg(g.thr + (p.wlo + lane - 1));
+}
+
+__device__ __forceinline__ uint32_t block_finish(const Walker& w, int64_t i0, const MaskGeom& g, const BlockPrep& p) {
+  uint32_t bits = 0u - ((uint32_t)p.e0 & 1u);
+#pragma unroll 2
+  for (int32_t t = 0; t < p.nev; ++t) {
+    const int32_t e = p.e0 + t, b = e - w.odd;
+    const bool valid = e < p.e1;
     const bool bnd = valid && b >= 0 && b < 2 * w.L;
     const bool left = b < w.L;
-    const int32_t m = bnd ? (left ? (int32_t)w.ze - b : (int32_t)w.zc + 1 + (b - w.L)) : wlo;
-    long long S = __shfl_sync(0xffffffffu, tv, (m - wlo) & 31);
-    if (bnd && !staged) S = __ldg(g.thr + (m - 1));
+    const int32_t m = bnd ? (left ? (int32_t)w.ze - b : (int32_t)w.zc + 1 + (b - w.L)) : p.wlo;
+    long long S = __shfl_sync(0xffffffffu, p.tv, (m - p.wlo) & 31);
+    if (bnd && !p.staged) S = __ldg(g.thr + (m - 1));
     if (valid) {
       int64_t col;
       if (b < 0) {
@@ -258,6 +271,7 @@ __device__ __forceinline__ uint32_t block_bits(const Walker& w, int64_t i0, cons
   }
   return bits;
 }
+
 
 // Zone step of the row after its first e events (walker with level events):
 // -1 before the chord start or after its end.
@@ -542,6 +556,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
     int64_t cur_unit = -1;
     int64_t ui = 0, kb = ph;  // G = ui * nkb + kb, advanced without division
     while (kb >= nkb && nkb > 0) { kb -= nkb; ++ui; }
+    // clusters, binary plates: the next own block's events and thresholds are
+    // prepared (its load issued) before the current block is finished
+    const bool prefetch = CL > 1 && !a.level_mode;
+    BlockPrep pre{}, cur{};
+    bool have_pre = false;
     for (int64_t G = ph; G < nblk; G += CL) {
       const int stage = (int)(G & (STAGES - 1));
       const uint32_t phase = (uint32_t)((G / STAGES) & 1);
@@ -550,6 +569,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
         const int64_t s = (u0 + ui * ustep) % a.n_stripes;
         walker_init(w, a.j_begin + s * BN + row, a.j_end, a.mg, a.level_mode != 0);
         state = 0;
+        have_pre = false;
+      }
+      if (prefetch) {
+        if (!have_pre) block_prep(w, kb * BK, a.mg, pre);
+        cur = pre;
+        have_pre = kb + CL < nkb;
+        if (have_pre) block_prep(w, (kb + CL) * BK, a.mg, pre);
       }
       // One thread per phase waits for the stage; the phase's warps take its
       // decision at a named barrier (waiting there issues no instructions).
@@ -571,7 +597,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
       } else {
         // one CTA, consecutive blocks: walk the row; clusters: each phase takes
         // every CL-th block, found directly
-        const uint32_t bits = CL == 1 ? walker_bits(w, kb * BK, state, a.mg.thr) : block_bits(w, kb * BK, a.mg);
+        const uint32_t bits = CL == 1 ? walker_bits(w, kb * BK, state, a.mg.thr) : block_finish(w, kb * BK, a.mg, cur);
         if (a.signed_mask) expand_signed(disc_bits(w, kb * BK), bits, wd);
         else expand_bits(bits, wd);
       }
