@@ -70,8 +70,8 @@ KERNEL_SOURCES = {
     "bluestein": ["bluestein.cu", "fzp_internal.cuh"],
 }
 TRAFFIC = {
-    ("fzp-d0.25m", "dense"): (672.70e9 + 98.57e9,
-                              "fb557032443315cf4a07c8072d7a3b987840e2f11b1644da430fcc78653a843d"),
+    ("fzp-d0.25m", "dense"): (856.72e9 + 98.74e9,
+                              "39a8af06b0b20d1d4434cb980bd07cccd392ec17e746459c60365bff28c5537f"),
 }
 METRIC = "aperture Gsamples/s into 512² ROI, split-BF16 vs FP32 CZT at ≤1e-4 PSF error"
 UNIT = "Gsamples/s"
