@@ -282,34 +282,14 @@ __device__ __forceinline__ int32_t zone_after(const Walker& w, int32_t e) {
 }
 
 // Phase-plate pass: bits of columns [i0, i0 + 32) where the level (zone step
-// mod lmod) is in `pos` (out_pos) or in `neg` (out_neg); whole warp, like
-// block_bits, whose event search and threshold staging it shares.  Between two
+// mod lmod) is in `pos` (out_pos) or in `neg` (out_neg), from the block's
+// prepared events (block_prep, with level events); whole warp.  Between two
 // events the zone step is constant, so each block is a few runs of columns.
-__device__ __forceinline__ void block_values(const Walker& w, int64_t i0, const MaskGeom& g, int lmod, uint64_t pos,
-                                             uint64_t neg, uint32_t& out_pos, uint32_t& out_neg) {
-  const int32_t e0 = walker_count(w, i0 - 1, g);
-  const int32_t e1 = walker_count(w, i0 + 31, g);
-  int32_t mlo = INT32_MAX, mhi = INT32_MIN;
-  const int32_t b0 = max(e0 - w.odd, 0), b1 = min(e1 - w.odd, 2 * w.L);
-  if (w.ne > 0 && b1 > b0) {
-    if (b0 < w.L) {
-      mlo = (int32_t)w.ze - (min(b1, w.L) - 1);
-      mhi = (int32_t)w.ze - b0;
-    }
-    if (b1 > w.L) {
-      mlo = min(mlo, (int32_t)w.zc + 1 + (max(b0, w.L) - w.L));
-      mhi = max(mhi, (int32_t)w.zc + (b1 - w.L));
-    }
-  }
-  const int32_t wlo = __reduce_min_sync(0xffffffffu, mlo);
-  const int32_t whi = __reduce_max_sync(0xffffffffu, mhi);
-  const int32_t nev = (int32_t)__reduce_max_sync(0xffffffffu, (uint32_t)(e1 - e0));
-  const bool staged = whi >= wlo && whi - wlo < 32;
-  const int lane = threadIdx.x & 31;
-  long long tv = 0;
-  if (staged && wlo + lane <= whi) tv = __ldg(g.thr + (wlo + lane - 1));
+__device__ __forceinline__ void block_values(const Walker& w, int64_t i0, const MaskGeom& g, const BlockPrep& p,
+                                             int lmod, uint64_t pos, uint64_t neg, uint32_t& out_pos,
+                                             uint32_t& out_neg) {
   uint32_t P = 0u, Q = 0u;
-  int32_t z = zone_after(w, e0);
+  int32_t z = zone_after(w, p.e0);
   uint32_t c0 = 0;  // first column of the current run, relative to i0
   const int lmask = (lmod & (lmod - 1)) == 0 ? lmod - 1 : -1;  // power-of-two L: a mask, no division
   auto fill = [&](int32_t zz, uint32_t a, uint32_t b) {
@@ -319,14 +299,14 @@ __device__ __forceinline__ void block_values(const Walker& w, int64_t i0, const 
     if ((pos >> q) & 1ull) P |= m;
     if ((neg >> q) & 1ull) Q |= m;
   };
-  for (int32_t t = 0; t < nev; ++t) {
-    const int32_t e = e0 + t, b = e - w.odd;
-    const bool valid = e < e1;
+  for (int32_t t = 0; t < p.nev; ++t) {
+    const int32_t e = p.e0 + t, b = e - w.odd;
+    const bool valid = e < p.e1;
     const bool bnd = valid && b >= 0 && b < 2 * w.L;
     const bool left = b < w.L;
-    const int32_t m = bnd ? (left ? (int32_t)w.ze - b : (int32_t)w.zc + 1 + (b - w.L)) : wlo;
-    long long S = __shfl_sync(0xffffffffu, tv, (m - wlo) & 31);
-    if (bnd && !staged) S = __ldg(g.thr + (m - 1));
+    const int32_t m = bnd ? (left ? (int32_t)w.ze - b : (int32_t)w.zc + 1 + (b - w.L)) : p.wlo;
+    long long S = __shfl_sync(0xffffffffu, p.tv, (m - p.wlo) & 31);
+    if (bnd && !p.staged) S = __ldg(g.thr + (m - 1));
     if (valid) {
       int64_t col;
       if (b < 0) {
@@ -556,9 +536,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
     int64_t cur_unit = -1;
     int64_t ui = 0, kb = ph;  // G = ui * nkb + kb, advanced without division
     while (kb >= nkb && nkb > 0) { kb -= nkb; ++ui; }
-    // clusters, binary plates: the next own block's events and thresholds are
-    // prepared (its load issued) before the current block is finished
-    const bool prefetch = CL > 1 && !a.level_mode;
+    // block-wise generation (clusters, and every phase-plate pass): the next
+    // own block's events and thresholds are prepared (its load issued) before
+    // the current block is finished
+    const bool prefetch = CL > 1 || a.level_mode;
     BlockPrep pre{}, cur{};
     bool have_pre = false;
     for (int64_t G = ph; G < nblk; G += CL) {
@@ -592,7 +573,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
       if (a.level_mode) {
         // phase-plate pass: +1 / -1 on the pass's level sets
         uint32_t pb, nb;
-        block_values(w, kb * BK, a.mg, a.lmod, a.pos, a.neg, pb, nb);
+        block_values(w, kb * BK, a.mg, cur, a.lmod, a.pos, a.neg, pb, nb);
         expand_signed(pb | nb, nb, wd);
       } else {
         // one CTA, consecutive blocks: walk the row; clusters: each phase takes
