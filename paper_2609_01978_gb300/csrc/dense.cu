@@ -214,11 +214,44 @@ __device__ __forceinline__ int32_t walker_count(const Walker& w, int64_t X, cons
 // block_prep finds the events and issues the threshold load, block_finish
 // turns them into bits; the generator prepares its next block before it
 // finishes the current one, so the load's latency is hidden.
+// Per block, a boundary's distance a = ceil(sqrt(S_m - dj^2)) from the axis lies
+// in a 32-wide window [d, d + 31] fixed by the block (right of the axis
+// d = i0 - c, left of it d = c - i0 - 30).  With a = d + k, k is the smallest
+// k >= 0 with k (k + 2d) >= S_m - dj^2 - d^2, a 32-bit quantity; for d >= 1024
+// the estimate (S_m - dj^2 - d^2) / (2d) is off by less than 31^2 / (2d) < 1,
+// and two steps up and one down in 32-bit arithmetic make k exact.  Blocks
+// within 1024 columns of the axis use the 64-bit square root.
 struct BlockPrep {
   int32_t e0, e1, wlo, nev;
   int staged;
   long long tv;
+  int64_t D2r, D2l;     // dj^2 + d^2, right and left of the axis
+  float ir, il;         // 1 / (2 d)
+  int32_t tdr, tdl;     // 2 d
+  int fr, fl;           // the 32-bit path applies
 };
+
+__device__ __forceinline__ int32_t window_k(int32_t D, float inv2d, int32_t two_d) {
+  int32_t k = __float2int_ru((float)D * inv2d);
+  k = k < 0 ? 0 : k;
+  k += (k * (k + two_d) < D) ? 1 : 0;
+  k += (k * (k + two_d) < D) ? 1 : 0;
+  k -= (k > 0 && (k - 1) * (k - 1 + two_d) >= D) ? 1 : 0;
+  return k;
+}
+
+// Column of boundary event b (0 <= b < 2L) of the walker's row, relative to i0.
+__device__ __forceinline__ uint32_t boundary_col(const Walker& w, int64_t i0, const BlockPrep& p, int32_t b,
+                                                 long long S) {
+  if (b < w.L) {  // left of the axis: column c - a + 1
+    if (p.fl) return 31u - (uint32_t)window_k((int32_t)((int64_t)S - p.D2l), p.il, p.tdl);
+    const int64_t aa = (int64_t)ceil_sqrt46((int64_t)S - w.dj2);
+    return (uint32_t)(w.c - aa + 1 - i0);
+  }
+  if (p.fr) return (uint32_t)window_k((int32_t)((int64_t)S - p.D2r), p.ir, p.tdr);
+  const int64_t aa = (int64_t)ceil_sqrt46((int64_t)S - w.dj2);
+  return (uint32_t)(w.c + aa - i0);
+}
 
 __device__ __forceinline__ void block_prep(const Walker& w, int64_t i0, const MaskGeom& g, BlockPrep& p) {
   p.e0 = walker_count(w, i0 - 1, g);
@@ -243,6 +276,15 @@ __device__ __forceinline__ void block_prep(const Walker& w, int64_t i0, const Ma
   const int lane = threadIdx.x & 31;
   p.tv = 0;
   if (p.staged && p.wlo + lane <= whi) p.tv = __ldg(g.thr + (p.wlo + lane - 1));
+  const int64_t dr = i0 - w.c, dl = w.c - i0 - 30;
+  p.fr = dr >= 1024 ? 1 : 0;
+  p.fl = dl >= 1024 ? 1 : 0;
+  p.D2r = w.dj2 + dr * dr;
+  p.D2l = w.dj2 + dl * dl;
+  p.tdr = (int32_t)(2 * dr);
+  p.tdl = (int32_t)(2 * dl);
+  p.ir = p.fr ? 0.5f / (float)dr : 0.0f;
+  p.il = p.fl ? 0.5f / (float)dl : 0.0f;
 }
 
 __device__ __forceinline__ uint32_t block_finish(const Walker& w, int64_t i0, const MaskGeom& g, const BlockPrep& p) {
@@ -257,16 +299,11 @@ __device__ __forceinline__ uint32_t block_finish(const Walker& w, int64_t i0, co
     long long S = __shfl_sync(0xffffffffu, p.tv, (m - p.wlo) & 31);
     if (bnd && !p.staged) S = __ldg(g.thr + (m - 1));
     if (valid) {
-      int64_t col;
-      if (b < 0) {
-        col = w.c - w.bmax;  // chord start
-      } else if (b >= 2 * w.L) {
-        col = w.c + w.bmax + 1;  // chord end
-      } else {
-        const int64_t aa = (int64_t)ceil_sqrt46((int64_t)S - w.dj2);
-        col = left ? w.c - aa + 1 : w.c + aa;
-      }
-      bits ^= 0xFFFFFFFFu << (uint32_t)(col - i0);
+      uint32_t cc;
+      if (b < 0) cc = (uint32_t)(w.c - w.bmax - i0);            // chord start
+      else if (b >= 2 * w.L) cc = (uint32_t)(w.c + w.bmax + 1 - i0);  // chord end
+      else cc = boundary_col(w, i0, p, b, S);
+      bits ^= 0xFFFFFFFFu << cc;
     }
   }
   return bits;
@@ -308,16 +345,10 @@ __device__ __forceinline__ void block_values(const Walker& w, int64_t i0, const 
     long long S = __shfl_sync(0xffffffffu, p.tv, (m - p.wlo) & 31);
     if (bnd && !p.staged) S = __ldg(g.thr + (m - 1));
     if (valid) {
-      int64_t col;
-      if (b < 0) {
-        col = w.c - w.bmax;
-      } else if (b >= 2 * w.L) {
-        col = w.c + w.bmax + 1;
-      } else {
-        const int64_t aa = (int64_t)ceil_sqrt46((int64_t)S - w.dj2);
-        col = left ? w.c - aa + 1 : w.c + aa;
-      }
-      const uint32_t cc = (uint32_t)(col - i0);
+      uint32_t cc;
+      if (b < 0) cc = (uint32_t)(w.c - w.bmax - i0);
+      else if (b >= 2 * w.L) cc = (uint32_t)(w.c + w.bmax + 1 - i0);
+      else cc = boundary_col(w, i0, p, b, S);
       fill(z, c0, cc);
       z = zone_after(w, e + 1);
       c0 = cc;
