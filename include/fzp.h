@@ -312,12 +312,28 @@ FZP_API fzp_status fzp_surrogate_destroy(fzp_surrogate_t s);
 FZP_API fzp_status fzp_metrics_noalloc(const fzp_params* params, const void* d_field, void* stream,
                                        fzp_metrics_t* out);
 
+/* Self-test of the failure path shared by the library's kernels (no
+ * counterpart in the paper).  Every device-side wait is bounded: when it
+ * expires, the kernel records a code in an error word, stops, and the host
+ * reports FZP_E_TIMEOUT (fzp_metrics does for a propagation).  This call runs
+ * one such wait on a barrier that nothing completes, with a limit of limit_us
+ * microseconds (1 .. 2,000,000; the production kernels use 2 s), so that the
+ * path can be tested without a fault: nothing else is in flight and the
+ * context stays usable.
+ *   stream  cudaStream_t; the call synchronises it.
+ * Returns FZP_E_TIMEOUT when the wait ran out and was reported (the expected
+ * outcome), FZP_E_CUDA if it was not, FZP_E_INVALID for a limit out of range.
+ * Allocates nothing (the error word is a file-scope device variable). */
+FZP_API fzp_status fzp_selftest_wait_timeout(uint32_t limit_us, void* stream);
+
 /* Binary aperture transmission T[j, i] of rows [row_begin, row_end), produced
  * by the same device code that feeds the plan's row transform (Fig. 2 Stage 2:
  * open where the paraxial zone index floor(r^2/(lambda f)) is odd and
  * r <= R_eff), for inspection and testing.  The dense form's generator walks
  * zone thresholds along each row; the Bluestein form's evaluates each sample.
- *   d_mask  device uint8, (row_end - row_begin) * N, row-major, 0 or 1.
+ * For an L-level phase plate (levels >= 2) the level map: 1 + q inside the
+ * aperture (q = the phase level, Fig. 18 Stage 3), 0 outside.
+ *   d_mask  device uint8, (row_end - row_begin) * N, row-major.
  * Errors: FZP_E_INVALID (range outside [0, N], NULL). */
 FZP_API fzp_status fzp_aperture_mask(fzp_plan_t plan, int64_t row_begin, int64_t row_end, void* d_mask,
                                      void* stream);

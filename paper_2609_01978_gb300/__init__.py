@@ -99,6 +99,7 @@ def lib() -> ctypes.CDLL:
             "fzp_metrics": [vp, vp, vp, ctypes.POINTER(Metrics)],
             "fzp_aperture_mask": [vp, i64, i64, vp, vp],
             "fzp_metrics_noalloc": [ctypes.POINTER(Params), vp, vp, ctypes.POINTER(Metrics)],
+            "fzp_selftest_wait_timeout": [ctypes.c_uint32, vp],
             "fzp_profile_enable": [vp, i32],
             "fzp_batch_plan": [ctypes.POINTER(Params), i32, ctypes.POINTER(vp)],
             "fzp_batch_propagate": [vp, ctypes.POINTER(vp), vp],
@@ -328,6 +329,12 @@ def metrics_noalloc(field, D: float, f: float, lam: float, M: int, pitch: float,
     m = Metrics()
     _check(lib().fzp_metrics_noalloc(ctypes.byref(p), _ptr(field), _stream(stream), ctypes.byref(m)))
     return m.as_dict()
+
+
+def selftest_wait_timeout(limit_us: int, stream=None) -> None:
+    """fzp_selftest_wait_timeout: one bounded device wait that runs out; raises
+    FzpError with status FZP_E_TIMEOUT, the expected outcome."""
+    _check(lib().fzp_selftest_wait_timeout(int(limit_us), _stream(stream)))
 
 
 def version() -> str:

@@ -42,20 +42,24 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait: returns false (after recording `code`) when the wait expires
-// or another role of this CTA has aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                          int code) {
+// after limit_ns or another role of this CTA has aborted.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                              int code, uint64_t limit_ns) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = gtimer();
   while (true) {
     if (mbar_try(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (gtimer() - t0 > WAIT_NS) {
+    if (gtimer() - t0 > limit_ns) {
       atomicCAS(err, 0, code);
       *abort_flag = 1;
       return false;
     }
   }
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                          int code) {
+  return mbar_wait_for(bar, parity, abort_flag, err, code, WAIT_NS);
 }
 
 // Warp-uniform bounded wait: lane 0 polls, the result is broadcast.
