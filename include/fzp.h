@@ -253,7 +253,7 @@ FZP_API fzp_status fzp_batch_destroy(fzp_batch_t batch);
  * operands and accumulates in FP32 on the tensor cores (tcgen05); master
  * weights, optimiser state and gradients are FP32.  It learns the map from
  * membrane-deformation parameters to the PSF and metrics that this library's
- * propagation computes; the propagation stays the reference that judges it.
+ * propagation computes; the propagation stays the reference its error is measured against.
  * Parameters are one flat FP32 vector: for each layer W (n_out x n_in,
  * row-major) then b (n_out). */
 typedef struct fzp_surrogate_s* fzp_surrogate_t;

@@ -8,7 +8,7 @@ the 8-vector (A/lambda, log10 period, theta, taper, three ridge heights /
 lambda, lambda) to 4114 outputs: log10(I / I_ideal + 1e-6) on the central 64^2
 of a 128^2 ROI at pitch lambda f/# / 8 (I_ideal = (pi R^2/(lambda f))^2, the
 Strehl denominator of Fig. 18), then FWHM, DE and the MTF samples.  The
-propagation stays the judge: held-out predictions are compared with what it
+propagation stays the reference: held-out predictions are compared with what it
 computes.
 """
 from __future__ import annotations

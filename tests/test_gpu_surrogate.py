@@ -1,5 +1,5 @@
 """Learned surrogate: GPU training kernels against the FP64 oracle, and a
-trained network judged by the plain CZT on held-out membranes."""
+trained network checked against the plain CZT on held-out membranes."""
 import math
 import time
 
