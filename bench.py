@@ -70,8 +70,8 @@ KERNEL_SOURCES = {
     "bluestein": ["bluestein.cu", "fzp_internal.cuh"],
 }
 TRAFFIC = {
-    ("fzp-d0.25m", "dense"): (856.72e9 + 98.74e9,
-                              "39a8af06b0b20d1d4434cb980bd07cccd392ec17e746459c60365bff28c5537f"),
+    ("fzp-d0.25m", "dense"): (823.07e9 + 98.34e9,
+                              "dc7c6f3d63dfaffcdf5689aa841b16c65747202e772f331bb685ecd9bbb1bd5b"),
 }
 METRIC = "aperture Gsamples/s into 512² ROI, split-BF16 vs FP32 CZT at ≤1e-4 PSF error"
 UNIT = "Gsamples/s"
