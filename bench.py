@@ -71,7 +71,7 @@ KERNEL_SOURCES = {
 }
 TRAFFIC = {
     ("fzp-d0.25m", "dense"): (823.07e9 + 98.34e9,
-                              "dc7c6f3d63dfaffcdf5689aa841b16c65747202e772f331bb685ecd9bbb1bd5b"),
+                              "e987a310af8108608feea313d0292e73a30ec353ab0595edca1e72dc7e434083"),
 }
 METRIC = "aperture Gsamples/s into 512² ROI, split-BF16 vs FP32 CZT at ≤1e-4 PSF error"
 UNIT = "Gsamples/s"

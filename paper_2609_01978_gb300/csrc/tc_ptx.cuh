@@ -138,12 +138,6 @@ __device__ __forceinline__ bool mbar_wait_cl(uint64_t* bar, uint32_t parity, vol
     }
   }
 }
-__device__ __forceinline__ bool warp_wait_cl(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                             int code) {
-  int ok = 0;
-  if ((threadIdx.x & 31) == 0) ok = mbar_wait_cl(bar, parity, abort_flag, err, code) ? 1 : 0;
-  return __shfl_sync(0xffffffffu, ok, 0) != 0;
-}
 // Bulk copy from this CTA's shared memory into a peer's (shared::cluster
 // addresses for the destination and its mbarrier, which counts the bytes).
 __device__ __forceinline__ void bulk_s2peer(uint32_t dst_cluster, const void* src, uint32_t bytes,
