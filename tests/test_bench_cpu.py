@@ -1,0 +1,53 @@
+"""The benchmark's contract pieces that run without a GPU: the reference arm
+(the oracle on the host cores) prints one JSON line with the required keys and
+the same workload description as the GPU arm, and the helpers that the GPU arm
+uses for its roofline (flop model, captured traffic keyed to the sources)."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_reference_arm_json_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                          "fzp-d0.05m", "--steps", "1", "--warmup", "0", "--ref-rows", "4"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == bench.UNIT
+    assert d["metric"] == bench.METRIC and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert d["config"]["workload"] == "fzp-d0.05m" and d["config"]["N"] == 63213
+    assert d["config"]["rows_per_step"] == 4
+
+
+def test_config_is_shared_and_names_the_sample():
+    class A:
+        workload, form, rows = "fzp-d0.25m", "dense", 0
+    c = bench._config(A, bench.WORKLOADS["fzp-d0.25m"], 316057)
+    assert c["samples_per_step"] == 316057 ** 2 and "rows_timed" not in c
+    A.rows = 4096
+    c = bench._config(A, bench.WORKLOADS["fzp-d0.25m"], 316057)
+    assert c["samples_per_step"] == 4096 * 316057 and "4096" in c["rows_timed"]
+    A.workload = "fzp-t5"
+    c = bench._config(A, bench.WORKLOADS["fzp-t5"], 15037595)
+    assert c["levels"] == 2 and abs(c["dx_m"] - 532e-9 * 25 / 2.5 / 16) < 1e-18
+
+
+def test_bluestein_flop_model_and_traffic_keying():
+    info = {"fft_length": 1 << 19, "fft_inner": 4096}
+    assert bench.bluestein_f2_flops(info, 256) == 256 * 128 * (10.0 * 4096 * 12 + 6.0 * 4096)
+    assert bench._traffic("fzp-d1m", "dense") is None  # nothing captured for this workload
+    t = bench._traffic("fzp-d0.25m", "dense")
+    assert t is None or t > 1e9  # reported only while the sources hash to the capture
