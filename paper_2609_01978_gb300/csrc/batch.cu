@@ -153,9 +153,10 @@ fzp_status autotune(const fzp_params* in, fzp_params* chosen, fzp_plan_t* keep) 
   }
   std::vector<Choice> cands;
   if (!deformed && geo.levels % 2 == 0) {  // the dense form's mask values must be exact in BF16
+    // cluster 0: the plan's own choice (4 CTAs for M = 512); 1: single-CTA kernel
+    cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 128, 0, 0, 0});
+    cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 256, 0, 0, 0});
     cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 128, 0, 1, 0});
-    cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 256, 0, 1, 0});
-    cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 128, 0, 2, 0});
   }
   cands.push_back({FZP_FORM_BLUESTEIN, FZP_PREC_FP32, 0, 0, 0, 0});
   fzp_plan_t best = nullptr;
