@@ -14,8 +14,10 @@
  * the ROI grid x_m = (m - M/2) p (sample M/2 on the axis), T the binary FZP
  * mask (open where floor(r^2/(lambda f)) is odd and r <= R_eff, Fig. 2 Stage 2,
  * paraxial radii of Eq. 4, centre zone opaque) and phi an optional membrane
- * deformation phase (4 pi / lambda) w(u, v).  The mask is generated inside the
- * kernels stripe by stripe and never stored.
+ * deformation phase (4 pi / lambda) w(u, v).  With fzp_params.levels = L >= 2
+ * T is instead the L-level phase transmission e^{-2 pi i q / L} inside R_eff,
+ * q = floor(L r^2 / (2 lambda f)) mod L (Fig. 18 Stage 3; Tables 3-5).  The mask is
+ * generated inside the kernels stripe by stripe and never stored.
  *
  * Conventions shared by every call:
  *   - Units are SI (metres).  Complex data are interleaved (re, im) pairs of
