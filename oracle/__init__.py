@@ -42,6 +42,7 @@ LENS = 1
 FZP_EXACT = 2
 CIRC = 3
 FZP_PHASE = 4  # L-level phase FZP (Fig. 18): transmission e^{-2 pi i q / L}
+FZP_POSITIVE = 5  # binary amplitude FZP with the centre zone open (even zones open)
 
 # First zero of J1 divided by pi: Airy null radius in units of lambda f / D.
 AIRY_NULL = 3.8317059702075125 / math.pi  # 1.2196698...

@@ -22,6 +22,8 @@
  *          (Eq. 4), a pixel is open where its zone index is odd, the centre
  *          zone (index 0) is opaque ("negative-centred", Sec. 4.1); the
  *          aperture is limited to R_eff = min(D/2, lambda f / (2 dx_in)).
+ *          The positive-centred plate (centre zone open) is the second
+ *          centre configuration the Fig. 18 engine offers.
  *
  * Three independent evaluations of the focal-plane field are provided:
  *   O1  orc_field_direct    : Eq. 1 summed literally over every aperture
@@ -64,7 +66,8 @@ enum {
   ORC_LENS = 1,         /* ideal thin lens: circ(r<=R) * exp(-i pi r^2/(lambda f)) */
   ORC_FZP_EXACT = 2,    /* binary amplitude FZP, exact radii (Eq. 3)             */
   ORC_CIRC = 3,         /* clear circular pupil (no focusing phase)              */
-  ORC_FZP_PHASE = 4     /* L-level phase FZP (Fig. 18 Stage 3), levels = L >= 2  */
+  ORC_FZP_PHASE = 4,    /* L-level phase FZP (Fig. 18 Stage 3), levels = L >= 2  */
+  ORC_FZP_POSITIVE = 5  /* binary amplitude FZP, paraxial radii, centre zone open */
 };
 
 /* Deformation of the membrane, w(u,v) in metres; phase phi = (4 pi/lambda) w.
@@ -116,6 +119,12 @@ static int orc_open(const orc_params* P, int64_t j, int64_t i) {
   if (P->kind == ORC_FZP_PARAXIAL) {
     const double zone = floor((double)s * orc_kappa(P));
     return ((int64_t)zone & 1) ? 1 : 0;
+  }
+  if (P->kind == ORC_FZP_POSITIVE) {
+    /* the other centre configuration of the v8 engine (Fig. 18): the even
+     * zones, the centre zone among them, are the open ones */
+    const double zone = floor((double)s * orc_kappa(P));
+    return ((int64_t)zone & 1) ? 0 : 1;
   }
   if (P->kind == ORC_FZP_EXACT) {
     /* Eq. 3: r^2 = n lambda f + n^2 lambda^2/4  =>  n(r) = 2 (sqrt(f^2 + r^2) - f) / lambda */

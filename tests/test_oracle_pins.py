@@ -351,3 +351,36 @@ def test_phase_fzp_direct_equals_czt(oracle_mod):
     g = O.Geometry(D=0.15e-3, f=0.75e-3, lam=lam, M=24, p=lam * 5 / 8, kind=O.FZP_PHASE, levels=4)
     assert g.N < 400
     assert rel(O.field_direct(g), O.field_czt(g)) < 1e-10
+
+
+@pytest.mark.parametrize("nz", [7, 8])
+def test_centre_configurations_on_axis(oracle_mod, nz):
+    """The two centre configurations of the binary plate (Fig. 18 engine).  On
+    the axis each paraxial zone k contributes the closed form
+    e^{ikf}/(i lambda f) * (lambda f / i)(e^{i pi (k+1)} - e^{i pi k}) = 2 (-1)^k e^{ikf}
+    (the zone integral of the Eq. 2 chirp over r_k^2 = k lambda f .. (k+1) lambda f),
+    so with nz zones inside R the negative-centred plate (odd zones open) gives
+    -2 floor(nz/2) e^{ikf} and the positive-centred one (even zones, the centre
+    among them) +2 ceil(nz/2) e^{ikf}: opposite signs, and a magnitude ratio
+    that tells an odd zone count from an even one.  The two masks are
+    complements inside the aperture disc, so their fields sum to the clear
+    pupil's exactly.  16 samples per outermost zone width keep the
+    discretisation error near 1e-3 of a zone's contribution."""
+    O = oracle_mod
+    lam, f = 500e-9, 0.02
+    D = 2 * math.sqrt(nz * lam * f)
+    kw = dict(D=D, f=f, lam=lam, M=16, p=lam * f / D / 8, dx=lam * f / (16 * D))
+    gn = O.Geometry(kind=O.FZP_PARAXIAL, **kw)
+    gp = O.Geometry(kind=O.FZP_POSITIVE, **kw)
+    gc = O.Geometry(kind=O.CIRC, **kw)
+    Un, Up, Uc = O.field_separable(gn), O.field_separable(gp), O.field_separable(gc)
+    assert rel(Un + Up, Uc) < 1e-12
+    ikf = np.exp(2j * math.pi * f / lam)
+    c = gn.M // 2
+    assert abs(Un[c, c] / ikf - (-2 * (nz // 2))) < 0.02
+    assert abs(Up[c, c] / ikf - 2 * ((nz + 1) // 2)) < 0.02
+    assert abs(Uc[c, c] / ikf - 2 * (nz % 2)) < 0.02
+    # the exported masks: complements inside the disc, the centre pixel open
+    mn, mp, mc = (O.mask_rows(g, 0, g.N) for g in (gn, gp, gc))
+    assert np.array_equal(mn + mp, mc)
+    assert mp[gp.c, gp.c] == 1 and mn[gn.c, gn.c] == 0
