@@ -71,7 +71,7 @@ KERNEL_SOURCES = {
 }
 TRAFFIC = {
     ("fzp-d0.25m", "dense"): (823.07e9 + 98.34e9,
-                              "e987a310af8108608feea313d0292e73a30ec353ab0595edca1e72dc7e434083"),
+                              "7fe520cf515069d95c1e4a70f8965855d0904d0328f65ebd7aada067177ba309"),
 }
 METRIC = "aperture Gsamples/s into 512² ROI, split-BF16 vs FP32 CZT at ≤1e-4 PSF error"
 UNIT = "Gsamples/s"

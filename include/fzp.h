@@ -126,6 +126,12 @@ typedef struct fzp_params {
                           even L: L = 2 as one +-1 mask, L >= 4 as L/2 passes of
                           masks with values -1, 0, +1 (exact in BF16) whose
                           fields are summed with the weights of Re T and Im T */
+  int32_t centre_open; /* centre configuration of the binary amplitude plate
+                          (Fig. 18 engine): 0 = negative-centred, odd zones open,
+                          the centre zone opaque (Sec. 4.1's plate); 1 =
+                          positive-centred, even zones open.  Must be 0 for a
+                          phase plate (levels >= 2), where it would only shift
+                          every level by one phase; other values are invalid */
 } fzp_params;
 
 /* Opaque plan: geometry, zone-threshold table, chirp / kernel tables and the
@@ -160,7 +166,7 @@ typedef struct fzp_plan_info {
   int32_t levels;        /* phase levels L (0: binary amplitude FZP)               */
   int32_t passes;        /* dense form: signed-mask passes per row chunk (1, or L/2
                             for a phase plate with L >= 4)                         */
-  int32_t reserved;
+  int32_t centre_open;   /* 1: positive-centred binary plate (even zones open)     */
 } fzp_plan_info;
 
 /* Metrics of Fig. 2 Stage 4 / Fig. 18 Stage 5. */

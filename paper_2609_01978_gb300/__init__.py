@@ -47,7 +47,7 @@ class Params(ctypes.Structure):
                 ("form", ctypes.c_int32), ("pitch", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("stripe_rows", ctypes.c_int32), ("deform", ctypes.POINTER(Deform)),
                 ("promote", ctypes.c_int32), ("row_batch", ctypes.c_int32), ("cluster", ctypes.c_int32),
-                ("levels", ctypes.c_int32)]
+                ("levels", ctypes.c_int32), ("centre_open", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -58,7 +58,7 @@ class PlanInfo(ctypes.Structure):
                 ("fft_length", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
                 ("promote", ctypes.c_int32), ("row_batch", ctypes.c_int32), ("chunk_rows", ctypes.c_int64),
                 ("cluster", ctypes.c_int32), ("fft_inner", ctypes.c_int32), ("ctas", ctypes.c_int32),
-                ("levels", ctypes.c_int32), ("passes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("levels", ctypes.c_int32), ("passes", ctypes.c_int32), ("centre_open", ctypes.c_int32)]
 
 
 class Metrics(ctypes.Structure):
@@ -165,11 +165,12 @@ class Plan:
     def __init__(self, D: float, f: float, lam: float, M: int, pitch: float, dx: float = 0.0, N: int = 0,
                  form: int = FORM_AUTO, precision: int = PREC_FP32, stripe_rows: int = 0,
                  deform: Optional[Deform] = None, promote: int = 0, row_batch: int = 0, cluster: int = 0,
-                 levels: int = 0):
+                 levels: int = 0, centre_open: int = 0):
         self._deform = deform
         p = Params(D=D, f=f, lam=lam, dx=dx, N=N, M=M, form=form, pitch=pitch, precision=precision,
                    stripe_rows=stripe_rows, deform=ctypes.pointer(deform) if deform is not None else None,
-                   promote=promote, row_batch=row_batch, cluster=cluster, levels=levels)
+                   promote=promote, row_batch=row_batch, cluster=cluster, levels=levels,
+                   centre_open=centre_open)
         h = ctypes.c_void_p()
         _check(lib().fzp_plan(ctypes.byref(p), ctypes.byref(h)))
         self._h = h
@@ -239,7 +240,7 @@ class Batch:
                             precision=pr.get("precision", PREC_AUTO_1E4), stripe_rows=pr.get("stripe_rows", 0),
                             deform=ctypes.pointer(d) if d is not None else None, promote=pr.get("promote", 0),
                             row_batch=pr.get("row_batch", 0), cluster=pr.get("cluster", 0),
-                            levels=pr.get("levels", 0))
+                            levels=pr.get("levels", 0), centre_open=pr.get("centre_open", 0))
         h = ctypes.c_void_p()
         _check(lib().fzp_batch_plan(arr, n, ctypes.byref(h)))
         self._h = h

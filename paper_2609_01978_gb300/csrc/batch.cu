@@ -48,9 +48,10 @@ std::mutex g_tune_mu;
 std::map<std::string, Choice> g_tune;
 bool g_tune_loaded = false;
 
-std::string tune_key(int64_t N, int M, bool deformed, int levels) {
+std::string tune_key(int64_t N, int M, bool deformed, int levels, int centre_open) {
   char buf[96];
-  snprintf(buf, sizeof(buf), "N=%lld,M=%d,deformed=%d,levels=%d", (long long)N, M, deformed ? 1 : 0, levels);
+  snprintf(buf, sizeof(buf), "N=%lld,M=%d,deformed=%d,levels=%d,centre_open=%d", (long long)N, M, deformed ? 1 : 0,
+           levels, centre_open);
   return buf;
 }
 
@@ -137,7 +138,7 @@ fzp_status autotune(const fzp_params* in, fzp_params* chosen, fzp_plan_t* keep) 
   fzp_status st = validate_and_derive(&probe, geo);
   if (st != FZP_OK) return st;
   const bool deformed = in->deform != nullptr;
-  const std::string key = tune_key(geo.N, geo.M, deformed, geo.levels);
+  const std::string key = tune_key(geo.N, geo.M, deformed, geo.levels, geo.mg.centre_open);
   *chosen = *in;
   std::lock_guard<std::mutex> lock(g_tune_mu);
   tune_load();

@@ -173,7 +173,7 @@ __device__ __forceinline__ typename Cplx<R>::T aperture(const RowArgs& a, int64_
     v = cis_turns<R>(-(double)q / (double)a.mg.levels);
     if (!a.has_deform) return v;
   } else {
-    if ((z & 1) == 0) return v;  // binary amplitude: open on odd zones
+    if (((z ^ a.mg.centre_open) & 1) == 0) return v;  // binary amplitude: odd zones open (even: positive-centred)
     v.x = 1;
     if (!a.has_deform) return v;
   }

@@ -47,6 +47,7 @@ struct MaskGeom {
   const int64_t* thr; // device: thr[m-1] = S_m, m = 1..nthr
   int64_t nthr;
   int levels;         // 0: binary amplitude (open on odd zones); L >= 2: phase level = zone mod L
+  int centre_open;    // binary amplitude: 1 = open on even zones (positive-centred)
 };
 
 // zone(s) for 0 <= s <= sR (the zone rate kappa is kappa_L for phase plates).
@@ -69,7 +70,7 @@ __device__ __forceinline__ int64_t zone_of(int64_t s, const MaskGeom& g) {
 __device__ __forceinline__ bool mask_open(int64_t dj, int64_t di, const MaskGeom& g) {
   const int64_t s = dj * dj + di * di;
   if (s > g.sR) return false;
-  return (zone_of(s, g) & 1) != 0;
+  return ((zone_of(s, g) ^ g.centre_open) & 1) != 0;
 }
 
 // --------------------------------------------------------------------------

@@ -111,7 +111,11 @@ fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
   if (in->deform && (in->deform->n_ridges < 0 || in->deform->n_ridges > 3))
     return set_error(FZP_E_INVALID, "deform.n_ridges must be in [0, 3]");
   if (in->levels < 0 || in->levels > 64) return set_error(FZP_E_INVALID, "levels must be in [0, 64]");
+  if (in->centre_open != 0 && in->centre_open != 1) return set_error(FZP_E_INVALID, "centre_open must be 0 or 1");
+  if (in->centre_open && in->levels >= 2)
+    return set_error(FZP_E_INVALID, "centre_open applies to the binary amplitude plate (levels 0 or 1)");
   P.levels = in->levels >= 2 ? in->levels : 0;
+  P.mg.centre_open = in->centre_open;
   const double lf = in->lambda * in->f;
   P.D = in->D; P.f = in->f; P.lambda = in->lambda; P.p = in->pitch; P.M = in->M;
   // Fig. 2 / Fig. 18 Stage 1: dx_in = Lambda_edge / (S_samp max(L, 2)), Lambda_edge =
@@ -173,6 +177,13 @@ fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
       mp.wi = std::sin(2.0 * M_PI * k / L);
       P.passes.push_back(mp);
     }
+  }
+  if (P.form == FZP_FORM_DENSE && P.mg.centre_open) {
+    // positive-centred binary plate: one pass of the generator's level mode,
+    // +1 where the zone index is even (level 0 of 2) inside the disc
+    MaskPass mp;
+    mp.pos = 1ull;
+    P.passes.push_back(mp);
   }
   if (in->deform) {
     if (P.form == FZP_FORM_DENSE)
@@ -320,6 +331,7 @@ fzp_status fzp_plan_info_get(fzp_plan_t plan, fzp_plan_info* out) {
   out->ctas = P.form == FZP_FORM_DENSE ? P.dn.max_ctas : 0;
   out->levels = P.levels;
   out->passes = P.passes.empty() ? 1 : (int32_t)P.passes.size();
+  out->centre_open = P.mg.centre_open;
   out->device_bytes = P.device_bytes;
   return FZP_OK;
 }
@@ -358,9 +370,11 @@ fzp_status fzp_aperture_mask(fzp_plan_t plan, int64_t row_begin, int64_t row_end
                      (long long)row_end, (long long)P.N);
   if (row_end == row_begin) return FZP_OK;
   uint8_t* out = reinterpret_cast<uint8_t*>(d_mask);
-  // the dense form exports through its own row walker (amplitude plates); level
-  // maps of phase plates come from the per-sample rule
-  return P.form == FZP_FORM_DENSE && P.levels < 2
+  // the dense form exports through its own row walker (negative-centred
+  // amplitude plates); level maps of phase plates and positive-centred plates,
+  // which the dense form generates in its level mode, come from the
+  // per-sample rule
+  return P.form == FZP_FORM_DENSE && P.levels < 2 && !P.mg.centre_open
              ? dense_mask(P, row_begin, row_end - row_begin, out, (cudaStream_t)stream)
              : bluestein_mask(P, row_begin, row_end - row_begin, out, (cudaStream_t)stream);
 }

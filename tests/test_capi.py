@@ -3,6 +3,7 @@ every function include/fzp.h declares, and rejects invalid input before it
 touches the device."""
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -46,6 +47,8 @@ def test_exports_every_declared_symbol(fzp):
     (dict(dx=2e-6), "Eq. 6"),
     (dict(form=7), "form"),
     (dict(precision=9), "precision"),
+    (dict(centre_open=2), "centre_open"),
+    (dict(centre_open=1, levels=4), "binary amplitude"),
 ])
 def test_invalid_parameters_rejected(fzp, kw, frag):
     base = dict(D=1e-3, f=5e-3, lam=632.8e-9, M=64, pitch=0.4e-6)
@@ -76,3 +79,31 @@ def test_null_arguments(fzp):
     assert L.fzp_metrics(None, None, None, None) == fzp.FZP_E_INVALID
     assert L.fzp_plan_destroy(None) == fzp.FZP_OK
     assert b"NULL" in L.fzp_last_error() or L.fzp_last_error() != b""
+
+
+def test_struct_layouts_match_header(fzp, tmp_path):
+    """Every ctypes mirror of a struct in include/fzp.h has the C compiler's
+    size and field offsets (the binding marshals by layout, not by name)."""
+    import ctypes
+    pairs = [("fzp_deform", fzp.Deform), ("fzp_params", fzp.Params), ("fzp_plan_info", fzp.PlanInfo),
+             ("fzp_metrics_t", fzp.Metrics), ("fzp_profile_t", fzp.Profile)]
+    rename = {"lam": "lambda"}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fzp.h"', "int main(void) {"]
+    for cname, cls in pairs:
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            c = rename.get(fname, fname)
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {c}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        a, b, v = line.split()
+        got[(a, b)] = int(v)
+    for cname, cls in pairs:
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
