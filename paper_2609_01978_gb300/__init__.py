@@ -323,10 +323,13 @@ class SurrogateNet:
 
 
 def metrics_noalloc(field, D: float, f: float, lam: float, M: int, pitch: float, dx: float = 0.0, N: int = 0,
-                    stream=None) -> dict:
+                    levels: int = 0, centre_open: int = 0, stream=None) -> dict:
     """fzp_metrics_noalloc: the metric extractor without a plan and without any
-    device allocation (scratch in a static device array; M <= 512)."""
-    p = Params(D=D, f=f, lam=lam, dx=dx, N=N, M=M, form=0, pitch=pitch, precision=0, stripe_rows=0, deform=None)
+    device allocation (scratch in a static device array; M <= 512).  `levels`
+    enters through the default dx (Fig. 18 Stage 1); the aperture count does
+    not depend on the plate's levels or centre configuration."""
+    p = Params(D=D, f=f, lam=lam, dx=dx, N=N, M=M, form=0, pitch=pitch, precision=0, stripe_rows=0, deform=None,
+               levels=levels, centre_open=centre_open)
     m = Metrics()
     _check(lib().fzp_metrics_noalloc(ctypes.byref(p), _ptr(field), _stream(stream), ctypes.byref(m)))
     return m.as_dict()

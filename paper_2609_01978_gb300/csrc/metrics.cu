@@ -315,9 +315,13 @@ extern "C" fzp_status fzp_metrics_noalloc(const fzp_params* in, const void* d_fi
     return set_error(FZP_E_INVALID, "M = %d outside the static scratch of fzp_metrics_noalloc "
                      "(a power of two in [64, %d])", in->M, kNoAllocMaxM);
   if (in->N < 0 || (in->N > 0 && (in->N % 2) == 0)) return set_error(FZP_E_INVALID, "N must be 0 or odd");
-  // grids as fzp_plan derives them (Fig. 2 Stage 1-2)
+  if (in->levels < 0 || in->levels > 64) return set_error(FZP_E_INVALID, "levels must be in [0, 64]");
+  if (in->centre_open != 0 && in->centre_open != 1) return set_error(FZP_E_INVALID, "centre_open must be 0 or 1");
+  // grids as fzp_plan derives them (Fig. 2 / Fig. 18 Stage 1-2): dx_in =
+  // lambda f / (2 D max(L, 2)); the aperture disc does not depend on the
+  // plate's levels or centre configuration
   const double lf = in->lambda * in->f;
-  const double dx = in->dx > 0 ? in->dx : lf / (4.0 * in->D);
+  const double dx = in->dx > 0 ? in->dx : lf / (2.0 * (in->levels > 2 ? in->levels : 2) * in->D);
   int64_t N = in->N;
   if (N == 0) {
     const double n = std::ceil(in->D / dx);

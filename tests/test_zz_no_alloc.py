@@ -61,3 +61,20 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(env):
     with pytest.raises(fzp.FzpError) as ei:
         fzp.metrics_noalloc(U, D=4e-3, f=20e-3, lam=632.8e-9, M=1024, pitch=0.2e-6)
     assert ei.value.status == fzp.FZP_E_INVALID and "static scratch" in str(ei.value)
+
+
+@pytest.mark.parametrize("levels,centre_open", [(4, 0), (0, 1)])
+def test_noalloc_phase_and_positive_plates(env, levels, centre_open):
+    """A 4-level phase plate (default dx = lambda f / (2 D L), Fig. 18 Stage 1)
+    and a positive-centred plate: the same grid and aperture count as the plan,
+    so the same metrics."""
+    fzp, torch = env
+    kw = dict(D=2e-3, f=10e-3, lam=632.8e-9, M=128, pitch=632.8e-9 * 5 / 8, levels=levels, centre_open=centre_open)
+    with fzp.Plan(form=fzp.FORM_BLUESTEIN, precision=fzp.PREC_FP32, **kw) as plan:
+        U = torch.empty((128, 128), dtype=torch.complex128, device="cuda:0")
+        plan.propagate_roi(0, plan.info["N"], U)
+        ref = plan.metrics(U)
+    got = fzp.metrics_noalloc(U, **kw)
+    assert got["aperture_count"] == ref["aperture_count"]
+    for k in KEYS:
+        assert abs(got[k] / ref[k] - 1) < 1e-9, (k, got[k], ref[k])
