@@ -338,12 +338,12 @@ FZP_API fzp_status fzp_selftest_wait_timeout(uint32_t limit_us, void* stream);
  * by the same device code that feeds the plan's row transform (Fig. 2 Stage 2:
  * open where the paraxial zone index floor(r^2/(lambda f)) is odd and
  * r <= R_eff; even instead of odd for a positive-centred plate), for
- * inspection and testing.  The dense form's generator walks zone thresholds
- * along each row; the Bluestein form's evaluates each sample.  For an L-level
- * phase plate (levels >= 2) the level map: 1 + q inside the aperture (q = the
- * phase level, Fig. 18 Stage 3), 0 outside.  Level maps and positive-centred
- * masks come from the per-sample rule in both forms (the dense form generates
- * them in its level mode, which has no export of its own).
+ * inspection and testing.  The Bluestein form evaluates each sample; the
+ * dense form exports through the generator its row pass launches: the row
+ * walker (single-CTA launches), the block-wise generator (2- and 4-CTA
+ * clusters) or the level mode (phase plates with L >= 4, positive-centred
+ * plates).  For an L-level phase plate (levels >= 2) the level map: 1 + q
+ * inside the aperture (q = the phase level, Fig. 18 Stage 3), 0 outside.
  *   d_mask  device uint8, (row_end - row_begin) * N, row-major.
  * Errors: FZP_E_INVALID (range outside [0, N], NULL). */
 FZP_API fzp_status fzp_aperture_mask(fzp_plan_t plan, int64_t row_begin, int64_t row_end, void* d_mask,

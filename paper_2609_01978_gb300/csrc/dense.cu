@@ -762,15 +762,74 @@ __global__ void k_build_A(int M, int64_t N, int64_t kblocks, int npairs, int64_t
   }
 }
 
-// The generator of k_dense (walker), one row per thread, to bytes.
-__global__ void k_mask_rows(MaskGeom mg, int64_t N, int64_t j0, int64_t rows, uint8_t* out) {
+// What a mask export writes per sample (fzp_aperture_mask of a dense plan).
+enum MaskExport {
+  EXPORT_BITS = 0,    // binary amplitude plate: 1 on open samples
+  EXPORT_SIGNED = 1,  // binary phase plate (L = 2): 1 + zone parity inside the disc, 0 outside
+  EXPORT_LEVELS = 2,  // level-mode plate (L >= 4): 1 + q inside the disc, q the level
+  EXPORT_EVEN = 3     // positive-centred plate (level mode, L = 2): 1 on level 0
+};
+
+// The generator of single-CTA k_dense launches (walker), one row per thread,
+// to bytes (EXPORT_BITS or EXPORT_SIGNED).
+__global__ void k_mask_rows(MaskGeom mg, int64_t N, int64_t j0, int64_t rows, int mode, uint8_t* out) {
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
     Walker w;
     walker_init(w, j0 + r, INT64_MAX, mg);
     uint32_t state = 0;
     for (int64_t i0 = 0; i0 < N; i0 += 32) {
       const uint32_t bits = walker_bits(w, i0, state, mg.thr);
-      for (int k = 0; k < 32 && i0 + k < N; ++k) out[r * N + i0 + k] = (uint8_t)((bits >> k) & 1u);
+      const uint32_t disc = mode == EXPORT_SIGNED ? disc_bits(w, i0) : 0xFFFFFFFFu;
+      for (int k = 0; k < 32 && i0 + k < N; ++k) {
+        const uint32_t b = (bits >> k) & 1u;
+        out[r * N + i0 + k] = (uint8_t)(((disc >> k) & 1u) ? (mode == EXPORT_SIGNED ? 1u + b : b) : 0u);
+      }
+    }
+  }
+}
+
+// The block-wise generators of k_dense (cluster launches, and every
+// level-mode pass) to bytes: one warp per 32 consecutive rows, a lane per
+// row, as the kernel's generator warps run them.  Bits come from block_finish
+// (EXPORT_BITS, EXPORT_SIGNED) or from block_values with the one-level set
+// {q} for each level q (EXPORT_LEVELS; EXPORT_EVEN takes q = 0 only).  Every
+// loop bound is uniform across the warp, as the warp-wide block functions
+// require; lanes past the last row walk an empty row and write nothing.
+__global__ void k_mask_blocks(MaskGeom mg, int64_t N, int64_t j0, int64_t rows, int mode, int lmod, uint8_t* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const bool level = mode >= EXPORT_LEVELS;
+  const int nq = mode == EXPORT_LEVELS ? lmod : 1;
+  for (int64_t r0 = warp * 32; r0 < rows; r0 += nwarps * 32) {
+    const int64_t r = r0 + lane;
+    Walker w;
+    walker_init(w, j0 + r, j0 + rows, mg, level);
+    for (int64_t i0 = 0; i0 < N; i0 += BK) {
+      BlockPrep p;
+      block_prep(w, i0, mg, p);
+      uint8_t v[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = 0;
+      if (!level) {
+        const uint32_t bits = block_finish(w, i0, mg, p);
+        const uint32_t disc = mode == EXPORT_SIGNED ? disc_bits(w, i0) : 0xFFFFFFFFu;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const uint32_t b = (bits >> k) & 1u;
+          v[k] = (uint8_t)(((disc >> k) & 1u) ? (mode == EXPORT_SIGNED ? 1u + b : b) : 0u);
+        }
+      } else {
+        for (int q = 0; q < nq; ++q) {
+          uint32_t P, Q;
+          block_values(w, i0, mg, p, lmod, 1ull << q, 0ull, P, Q);
+#pragma unroll
+          for (int k = 0; k < 32; ++k)
+            if ((P >> k) & 1u) v[k] = (uint8_t)(mode == EXPORT_LEVELS ? 1 + q : 1);
+        }
+      }
+      if (r < rows)
+        for (int k = 0; k < 32 && i0 + k < N; ++k) out[r * N + i0 + k] = v[k];
     }
   }
 }
@@ -864,8 +923,20 @@ fzp_status dense_build_tables(Plan& P) {
   return dense_fill_tables(P, 0);
 }
 
+// Export through the generator that the plan's row pass runs: the level
+// mode for plates with passes (L >= 4, positive-centred), the block-wise
+// generator for cluster launches, the walker for single-CTA launches.
 fzp_status dense_mask(Plan& P, int64_t j0, int64_t rows, uint8_t* out, cudaStream_t s) {
-  k_mask_rows<<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(P.mg, P.N, j0, rows, out);
+  const bool level = !P.passes.empty();
+  const int mode = level ? (P.mg.centre_open ? EXPORT_EVEN : EXPORT_LEVELS)
+                         : (P.levels == 2 ? EXPORT_SIGNED : EXPORT_BITS);
+  if (level || P.dn.cluster > 1) {
+    const int64_t warps = (rows + 31) / 32;
+    const unsigned grid = (unsigned)std::min<int64_t>((warps + 3) / 4, 65535);
+    k_mask_blocks<<<grid, 128, 0, s>>>(P.mg, P.N, j0, rows, mode, P.levels > 0 ? P.levels : 2, out);
+  } else {
+    k_mask_rows<<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(P.mg, P.N, j0, rows, mode, out);
+  }
   P.launches += 1;
   FZP_CUDA_TRY(cudaGetLastError());
   return FZP_OK;

@@ -370,11 +370,9 @@ fzp_status fzp_aperture_mask(fzp_plan_t plan, int64_t row_begin, int64_t row_end
                      (long long)row_end, (long long)P.N);
   if (row_end == row_begin) return FZP_OK;
   uint8_t* out = reinterpret_cast<uint8_t*>(d_mask);
-  // the dense form exports through its own row walker (negative-centred
-  // amplitude plates); level maps of phase plates and positive-centred plates,
-  // which the dense form generates in its level mode, come from the
-  // per-sample rule
-  return P.form == FZP_FORM_DENSE && P.levels < 2 && !P.mg.centre_open
+  // each form exports through the generator its row pass runs (the dense
+  // form: walker, block-wise generator or level mode, as the plan launches it)
+  return P.form == FZP_FORM_DENSE
              ? dense_mask(P, row_begin, row_end - row_begin, out, (cudaStream_t)stream)
              : bluestein_mask(P, row_begin, row_end - row_begin, out, (cudaStream_t)stream);
 }
