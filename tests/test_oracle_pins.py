@@ -384,3 +384,107 @@ def test_centre_configurations_on_axis(oracle_mod, nz):
     mn, mp, mc = (O.mask_rows(g, 0, g.N) for g in (gn, gp, gc))
     assert np.array_equal(mn + mp, mc)
     assert mp[gp.c, gp.c] == 1 and mn[gn.c, gn.c] == 0
+
+
+# --------------------------------------------------------------------------
+# Membrane deformation (config 4's model; reading of the wrinkle and ridges)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("theta,axis", [(0.0, 1), (math.pi / 2, 0)])
+def test_wrinkle_tilt_shifts_the_focus(oracle_mod, theta, axis):
+    """A wrinkle whose period is 1000 R is a tilt over the aperture:
+    phi = (4 pi / lambda) A 2 pi (u cos theta + v sin theta) / period, and a
+    linear aperture phase shifts the focal intensity by (4 pi A f / period)
+    (cos theta, sin theta) exactly (the Eq. 2 output chirp has unit modulus).
+    A is chosen for a shift of 3 ROI samples, so the deformed lens's
+    intensity is the flat lens's moved by 3 samples along x (theta = 0) or y
+    (theta = pi/2).  The sine's curvature costs about 1e-5."""
+    O = oracle_mod
+    lam, f, D = 632.8e-9, 2.5e-3, 0.5e-3
+    p = 0.4e-6
+    period = 1000 * D / 2
+    A = 3 * p * period / (4 * math.pi * f)
+    kw = dict(D=D, f=f, lam=lam, M=32, p=p, kind=O.LENS)
+    I0 = np.abs(O.field_separable(O.Geometry(**kw))) ** 2
+    I1 = np.abs(O.field_separable(O.Geometry(deform=O.Deform(amp=A, period=period, theta=theta), **kw))) ** 2
+    if axis == 1:
+        a, b = I1[:, 3:], I0[:, :-3]
+    else:
+        a, b = I1[3:, :], I0[:-3, :]
+    assert rel(a, b) < 1e-4
+    # and not the unshifted pattern (the test would pass trivially for A = 0)
+    assert rel(I1, I0) > 0.1
+
+
+def _centre_row_phase(O, g):
+    a = O.aperture_rows(g, g.c, g.c + 1)[0]
+    u = (np.arange(g.N) - g.c) * g.dx
+    inside = np.abs(a) > 0
+    return u[inside], np.angle(a[inside])
+
+
+def test_ridge_profile_height_width_and_orientation(oracle_mod):
+    """A crease ridge at alpha = pi/2 (the line runs along v through px): along
+    the centre row the aperture phase is a bump of peak (4 pi / lambda) h at
+    u = px whose half-maximum points lie width/2 on either side (width is the
+    FWHM, reading 10); along v it is constant (the row 40 samples below gives
+    the same profile).  A clear pupil, so the phase is the deformation's."""
+    O = oracle_mod
+    lam = 632.8e-9
+    D, f = 4e-3, 20e-3
+    R = D / 2
+    px, width, h = R / 4, R / 3, lam / 8
+    g = O.Geometry(D=D, f=f, lam=lam, M=16, p=1e-6, kind=O.CIRC,
+                   deform=O.Deform(ridges=[(px, 0.3 * R, math.pi / 2, h, width)]))
+    u, ph = _centre_row_phase(O, g)
+    k = int(np.argmax(ph))
+    assert abs(ph[k] - 4 * math.pi / lam * h) < 1e-6
+    assert abs(u[k] - px) <= g.dx
+    half = ph[k] / 2
+    # half-maximum crossings by linear interpolation on each flank
+    left = np.where((ph[:-1] < half) & (ph[1:] >= half))[0][0]
+    right = np.where((ph[:-1] >= half) & (ph[1:] < half))[0][-1]
+    ul = u[left] + (half - ph[left]) / (ph[left + 1] - ph[left]) * g.dx
+    ur = u[right] + (half - ph[right]) / (ph[right + 1] - ph[right]) * g.dx
+    assert abs((ur - ul) / width - 1) < 1e-4
+    assert abs((ur + ul) / 2 - px) < 1e-3 * width
+    # constant along the crease direction
+    b = O.aperture_rows(g, g.c - 40, g.c - 39)[0]
+    a = O.aperture_rows(g, g.c, g.c + 1)[0]
+    both = (np.abs(a) > 0) & (np.abs(b) > 0)
+    assert np.max(np.abs(np.angle(a[both]) - np.angle(b[both]))) < 1e-12
+
+
+def test_wrinkle_profile_period_amplitude_and_taper(oracle_mod):
+    """A wrinkle at theta = 0 with taper tau: along the centre row the phase
+    is a sine of period `period` (zeros every period/2 from the axis), whose
+    envelope is (4 pi / lambda) A at the axis and (1 - tau) of that at the rim
+    (reading 10's taper 1 - tau (r/R)^2); along v it is constant up to the
+    taper."""
+    O = oracle_mod
+    lam = 632.8e-9
+    D, f = 4e-3, 20e-3
+    R = D / 2
+    A, period, tau = lam / 16, R / 2.5, 0.5
+    g = O.Geometry(D=D, f=f, lam=lam, M=16, p=1e-6, kind=O.CIRC,
+                   deform=O.Deform(amp=A, period=period, theta=0.0, taper=tau))
+    u, ph = _centre_row_phase(O, g)
+    amp0 = 4 * math.pi / lam * A
+    # zeros: sign changes of the phase, interpolated, at multiples of period/2
+    s = np.where(np.sign(ph[:-1]) * np.sign(ph[1:]) < 0)[0]
+    zeros = u[s] - ph[s] / (ph[s + 1] - ph[s]) * g.dx
+    half = period / 2
+    assert len(zeros) >= 8
+    assert np.max(np.abs(zeros / half - np.round(zeros / half))) < 1e-3
+    # the crest nearest the axis (u = period/4) carries the axis envelope, the
+    # outermost samples the rim envelope
+    crest = np.argmin(np.abs(u - period / 4))
+    assert abs(ph[crest] / amp0 - 1) < 0.02 + (period / 4 / R) ** 2 * tau
+    # envelope |phi| / |sin|: (1 - tau) at the rim, 1 - tau/4 at half the
+    # radius (a taper linear in r would give 1 - tau/2 there)
+    sn = np.abs(np.sin(2 * math.pi * u / period))
+    env = np.abs(ph) / sn.clip(1e-3)
+    for lo, hi, target, tol in [(0.97, 1.0, 1 - tau, 0.04), (0.45, 0.55, 1 - tau / 4, 0.03)]:
+        ok = (np.abs(u) >= lo * R) & (np.abs(u) <= hi * R) & (sn > 0.3)
+        assert ok.sum() > 2
+        assert np.max(np.abs(env[ok] / amp0 - target)) < tol, (lo, hi)
