@@ -488,3 +488,49 @@ def test_wrinkle_profile_period_amplitude_and_taper(oracle_mod):
         ok = (np.abs(u) >= lo * R) & (np.abs(u) <= hi * R) & (sn > 0.3)
         assert ok.sum() > 2
         assert np.max(np.abs(env[ok] / amp0 - target)) < tol, (lo, hi)
+
+
+@pytest.mark.parametrize("kind,L", [("amp", 0), ("pos", 0), ("phase", 4), ("phase", 8)])
+def test_mask_rule_against_exact_arithmetic(oracle_mod, kind, L):
+    """The mask rule against exact rational arithmetic on the same doubles:
+    a sample is inside iff s dx^2 <= R^2 and its zone (level step) is
+    floor(s dx^2 / (lambda f)) (times L/2 for an L-level plate, Fig. 18
+    Stage 3).  Rounding of the oracle's IEEE products may decide only samples
+    within 1e-9 of a boundary; every other sample must agree exactly."""
+    from fractions import Fraction
+    O = oracle_mod
+    kw = dict(D=0.5e-3, f=2.5e-3, lam=632.8e-9, M=8, p=1e-6)
+    if kind == "amp":
+        g = O.Geometry(kind=O.FZP_PARAXIAL, **kw)
+    elif kind == "pos":
+        g = O.Geometry(kind=O.FZP_POSITIVE, **kw)
+    else:
+        g = O.Geometry(kind=O.FZP_PHASE, levels=L, **kw)
+    mask = O.mask_rows(g, 0, g.N)
+    d = np.arange(g.N, dtype=np.int64) - g.c
+    S = d[:, None] ** 2 + d[None, :] ** 2
+    uniq, inv = np.unique(S, return_inverse=True)
+    dx2, R2 = Fraction(g.dx) ** 2, Fraction(g.R) ** 2
+    rate = dx2 / (Fraction(g.lam) * Fraction(g.f)) * (Fraction(L, 2) if kind == "phase" else 1)
+    eps = Fraction(1, 10 ** 9)
+    expect = np.full(len(uniq), -1, dtype=np.int64)  # -1: within eps of a boundary
+    for k, s in enumerate(uniq.tolist()):
+        a = s * dx2
+        if abs(a - R2) <= R2 * eps:
+            continue
+        z = s * rate
+        step = z.numerator // z.denominator
+        if z - step < eps or z - step > 1 - eps:
+            continue
+        if a > R2:
+            expect[k] = 0
+        elif kind == "amp":
+            expect[k] = step % 2
+        elif kind == "pos":
+            expect[k] = 1 - step % 2
+        else:
+            expect[k] = 1 + step % L
+    e = expect[inv.reshape(S.shape)]
+    decided = e >= 0
+    assert decided.mean() > 0.99
+    assert np.array_equal(mask[decided].astype(np.int64), e[decided]), (kind, L)
