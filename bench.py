@@ -445,7 +445,7 @@ def main():
         h2d = 0
         for _ in range(args.e2e_steps):
             with fzp.Plan(**params) as p2:
-                h2d = 8 * p2.info["n_thresholds"] + 96
+                h2d = 8 * p2.info["n_thresholds"]  # the zone-threshold table, the plan's one upload
                 p2.propagate_roi(r0, r0 + rows, U, stream=stream)
                 host.copy_(U, non_blocking=True)
                 p2.metrics(U, stream=stream)
@@ -455,8 +455,10 @@ def main():
             t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
             pg.all_reduce(t, op=pg.ReduceOp.MAX)
             e2e_s = float(t.item())
+        # read back: the complex128 field, the metric extractor's 1024-double
+        # result block and its 4-byte error word
         e2e = {"value": ws * rows * N / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": M * M * 16 + 8 * 28,
+               "d2h_bytes_per_step": M * M * 16 + 8 * 1024 + 4,
                "note": "fzp_plan + fzp_propagate_roi + field to pinned host + fzp_metrics + fzp_plan_destroy"}
     plan.close()
 
