@@ -51,3 +51,20 @@ def test_bluestein_flop_model_and_traffic_keying():
     assert bench._traffic("fzp-d1m", "dense") is None  # nothing captured for this workload
     t = bench._traffic("fzp-d0.25m", "dense")
     assert t is None or t > 1e9  # reported only while the sources hash to the capture
+
+
+def test_reference_arm_under_torchrun_prints_on_rank0_only():
+    """Launched as N ranks (torchrun's environment), the reference arm runs on
+    rank 0 alone; the other ranks exit 0 without work or output."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--workload",
+           "fzp-d0.05m", "--steps", "1", "--warmup", "0", "--ref-rows", "2"]
+    outs = {}
+    for rank in (0, 1):
+        env = dict(os.environ, WORLD_SIZE="2", RANK=str(rank), LOCAL_RANK=str(rank))
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT, env=env)
+        assert r.returncode == 0, r.stderr[-2000:]
+        outs[rank] = [l for l in r.stdout.splitlines() if l.strip()]
+    assert outs[1] == []
+    assert len(outs[0]) == 1
+    d = json.loads(outs[0][0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2
