@@ -8,7 +8,10 @@ imports the product: the two share no code.
 What lives here
 ---------------
 * ``Geometry`` -- the sampling grids of Fig. 2, Stage 1 (dx_in, N forced odd,
-  centred input grid, ROI grid) and the zone count of Eq. 3.
+  centred input grid, ROI grid) and the zone count of Eq. 3; the aperture
+  kinds: binary plate (negative- or positive-centred), exact-radius plate,
+  L-level phase plate, ideal lens, clear pupil, each with an optional
+  membrane deformation ``Deform``.
 * ``field_direct`` (O1, Eq. 1 literally), ``field_separable`` (O2, Eq. 2 as
   K T K^T) and ``field_czt`` (O3, Bluestein CZT rows then columns, Fig. 2) --
   thin ctypes wrappers over ``fzp_oracle.c``.
