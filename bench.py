@@ -71,7 +71,7 @@ KERNEL_SOURCES = {
 }
 TRAFFIC = {
     ("fzp-d0.25m", "dense"): (823.07e9 + 98.34e9,
-                              "0555e18f8fab63cf83632a37885c44be8eddb89a8614d426870450b3310566db"),
+                              "d356299ae7132297e56c43436390ef7695f065076395d89b1ebccbbf82f3bfa3"),
 }
 METRIC = "aperture Gsamples/s into 512² ROI, split-BF16 vs FP32 CZT at ≤1e-4 PSF error"
 UNIT = "Gsamples/s"

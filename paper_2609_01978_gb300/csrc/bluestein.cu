@@ -616,14 +616,10 @@ fzp_status layout_t(Plan& P, FormSizes* out) {
   out->tab = sizeof(C) * (b.L + twN + P.M + 4096);
   out->Z = sizeof(C) * b.L * (b.L1 > 1 ? b.rows : 1);  // row 0 also serves the table build
   out->G = b.L1 > 1 ? sizeof(C) * b.L1 * P.M * b.rows : 0;
-  static bool attrs = false;
-  if (!attrs) {
-    // 64 KiB covers every FP32 case; FP64 at L1 = 4096 needs ~96 KiB
-    FZP_CUDA_TRY(cudaFuncSetAttribute(k_f1<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    FZP_CUDA_TRY(cudaFuncSetAttribute(k_f2<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(C) * Traits<R>::L2MAX)));
-    attrs = true;
-  }
+  // 64 KiB covers every FP32 case; FP64 at L1 = 4096 needs ~96 KiB
+  static std::atomic<uint64_t> attr_f1{0}, attr_f2{0};
+  FZP_CUDA_TRY(smem_attr_once((const void*)k_f1<R>, 200 * 1024, attr_f1));
+  FZP_CUDA_TRY(smem_attr_once((const void*)k_f2<R>, (int)(sizeof(C) * Traits<R>::L2MAX), attr_f2));
   return FZP_OK;
 }
 

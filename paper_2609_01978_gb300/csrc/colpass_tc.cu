@@ -343,11 +343,8 @@ bool column_pass_tc_applies(const Plan& P) {
 }
 
 fzp_status column_pass_tc(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    FZP_CUDA_TRY(cudaFuncSetAttribute(k_colpass_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)colpass_tc_smem()));
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  FZP_CUDA_TRY(smem_attr_once((const void*)k_colpass_tc, (int)colpass_tc_smem(), attr));
   ColTcArgs a{};
   a.C1 = P.d_C1;
   a.c1_stride = P.chunk_rows;

@@ -874,13 +874,10 @@ fzp_status dense_layout(Plan& P, FormSizes* out) {
   FZP_CUDA_TRY(cudaGetDevice(&dev));
   FZP_CUDA_TRY(cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev));
   out->A = (size_t)d.npairs * (size_t)d.kblocks * A_BYTES;
-  static bool attrs = false;
-  if (!attrs) {
-    FZP_CUDA_TRY(cudaFuncSetAttribute(k_dense<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem_bytes()));
-    FZP_CUDA_TRY(cudaFuncSetAttribute(k_dense<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem_bytes()));
-    FZP_CUDA_TRY(cudaFuncSetAttribute(k_dense<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem_bytes()));
-    attrs = true;
-  }
+  static std::atomic<uint64_t> attr1{0}, attr2{0}, attr4{0};
+  FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<1>, (int)dense_smem_bytes(), attr1));
+  FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<2>, (int)dense_smem_bytes(), attr2));
+  FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<4>, (int)dense_smem_bytes(), attr4));
   // The kernel is persistent: launch only CTAs that are resident at once.  A
   // cluster must fit in one GPC, so with clusters fewer than all SMs may hold one.
   d.max_ctas = d.num_sms;

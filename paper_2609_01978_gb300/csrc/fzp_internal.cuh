@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <utility>
 #include <vector>
 
@@ -33,6 +34,20 @@ fzp_status set_error(fzp_status st, const char* fmt, ...);
                               "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
                               __FILE__, __LINE__);                                      \
   } while (0)
+
+// Dynamic shared memory above 48 KiB is an attribute of a kernel on one
+// device: set it on each device that launches the kernel, once.  `done` holds
+// a bit per device ordinal (ordinals from 64 up set it at every call).
+inline cudaError_t smem_attr_once(const void* kernel, int bytes, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
 
 // --------------------------------------------------------------------------
 // Mask geometry: exact binary FZP rule (paraxial radii, centre opaque)

@@ -440,13 +440,10 @@ fzp_status fzp_surrogate_create(int n_in, int hidden, int n_hidden_layers, int n
     surrogate_release(S);
     return set_error(FZP_E_OOM, "surrogate allocation failed");
   }
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_gemm_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM) != cudaSuccess) {
-      surrogate_release(S);
-      return set_error(FZP_E_CUDA, "cudaFuncSetAttribute(k_gemm_tn)");
-    }
-    attr = true;
+  static std::atomic<uint64_t> attr{0};
+  if (smem_attr_once((const void*)k_gemm_tn, GEMM_SMEM, attr) != cudaSuccess) {
+    surrogate_release(S);
+    return set_error(FZP_E_CUDA, "cudaFuncSetAttribute(k_gemm_tn)");
   }
   // weights ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)); biases zero
   for (const Layer& ly : S->L)
