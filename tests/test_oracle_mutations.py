@@ -1,0 +1,120 @@
+"""Planted mistakes in the oracle, on the CPU, in a scratch copy of it.
+
+Each mutation is a plausible error in a part of the oracle that the GPU path
+is compared against (a sign, a factor, a dropped square, a swapped axis, a
+wrong parity); each must make at least one of the oracle's pins fail.  This
+shows that the pins tie the oracle to the paper and to the mathematics, not
+only to itself.  The unmutated copy passes the same pins (the harness works).
+"""
+import importlib.util
+import os
+import shutil
+import sys
+
+import pytest
+
+import test_oracle_pins as pins
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle")
+
+# (name, exact source text, replacement, pins that must catch it)
+MUTATIONS = [
+    ("negative plate opens even zones",
+     "    return ((int64_t)zone & 1) ? 1 : 0;\n  }\n  if (P->kind == ORC_FZP_POSITIVE)",
+     "    return ((int64_t)zone & 1) ? 0 : 1;\n  }\n  if (P->kind == ORC_FZP_POSITIVE)",
+     [(pins.test_mask_structure, ()), (pins.test_centre_configurations_on_axis, (7,))]),
+    ("positive plate equals the negative one",
+     "    return ((int64_t)zone & 1) ? 0 : 1;",
+     "    return ((int64_t)zone & 1) ? 1 : 0;",
+     [(pins.test_centre_configurations_on_axis, (7,))]),
+    ("level rate kappa L instead of kappa L / 2",
+     "const double kL = orc_kappa(P) * (0.5 * (double)P->levels);",
+     "const double kL = orc_kappa(P) * ((double)P->levels);",
+     [(pins.test_binary_phase_is_disc_minus_twice_amplitude, ()), (pins.test_phase_fzp_efficiency_ladder, (4,))]),
+    ("phase plate focuses the -1 order",
+     "a = cexp(-I * 2.0 * M_PI * (double)orc_level(P, j, i) / (double)P->levels);",
+     "a = cexp(I * 2.0 * M_PI * (double)orc_level(P, j, i) / (double)P->levels);",
+     [(pins.test_phase_fzp_efficiency_ladder, (4,))]),
+    ("lens phase of the wrong sign",
+     "if (P->kind == ORC_LENS) a = cexp(-I * M_PI",
+     "if (P->kind == ORC_LENS) a = cexp(I * M_PI",
+     [(pins.test_ideal_lens_gives_airy, ())]),
+    ("Bluestein pre-chirp of the wrong sign",
+     "cexp(-I * M_PI * omega * (double)n * (double)n);",
+     "cexp(I * M_PI * omega * (double)n * (double)n);",
+     [(pins.test_o1_o2_o3_agree, ("fzp",)), (pins.test_czt_dft_special_case, (16,))]),
+    ("output chirp dropped from O2",
+     "      acc *= pre * cexp(I * M_PI * (x * x + y * y) / lf);",
+     "      acc *= pre;",
+     [(pins.test_o1_o2_o3_agree, ("fzp",))]),
+    ("deformation phase 2 pi / lambda instead of 4 pi / lambda",
+     "a *= cexp(I * (4.0 * M_PI / P->lambda)",
+     "a *= cexp(I * (2.0 * M_PI / P->lambda)",
+     [(pins.test_wrinkle_tilt_shifts_the_focus, (0.0, 1)),
+      (pins.test_ridge_profile_height_width_and_orientation, ())]),
+    ("deformation phase of the wrong sign",
+     "a *= cexp(I * (4.0 * M_PI / P->lambda)",
+     "a *= cexp(-I * (4.0 * M_PI / P->lambda)",
+     [(pins.test_wrinkle_tilt_shifts_the_focus, (0.0, 1))]),
+    ("crease normal along the line",
+     "double nx = -sin(d->ridge_alpha[k]), ny = cos(d->ridge_alpha[k]);",
+     "double nx = cos(d->ridge_alpha[k]), ny = sin(d->ridge_alpha[k]);",
+     [(pins.test_ridge_profile_height_width_and_orientation, ())]),
+    ("ridge sigma = width / 2",
+     "double sigma = d->ridge_width[k] / (2.0 * sqrt(2.0 * log(2.0)));",
+     "double sigma = d->ridge_width[k] / 2.0;",
+     [(pins.test_ridge_profile_height_width_and_orientation, ())]),
+    ("taper linear in r",
+     "(1.0 - d->taper * r2);",
+     "(1.0 - d->taper * sqrt(r2));",
+     [(pins.test_wrinkle_profile_period_amplitude_and_taper, ())]),
+    ("wrinkle axes swapped",
+     "(u * cos(d->theta) + v * sin(d->theta))",
+     "(u * sin(d->theta) + v * cos(d->theta))",
+     [(pins.test_wrinkle_tilt_shifts_the_focus, (0.0, 1))]),
+]
+
+
+def _copy(tmp_path, tag, old=None, new=None):
+    d = tmp_path / f"oracle_{tag}"
+    d.mkdir()
+    shutil.copy(os.path.join(SRC, "__init__.py"), d / "__init__.py")
+    src = open(os.path.join(SRC, "fzp_oracle.c")).read()
+    if old is not None:
+        assert src.count(old) == 1, f"mutation target not unique: {old!r}"
+        src = src.replace(old, new)
+    (d / "fzp_oracle.c").write_text(src)
+    spec = importlib.util.spec_from_file_location(f"oracle_{tag}", d / "__init__.py",
+                                                  submodule_search_locations=[str(d)])
+    mod = importlib.util.module_from_spec(spec)
+    sys.modules[spec.name] = mod  # dataclasses look their module up here
+    spec.loader.exec_module(mod)
+    mod.build(force=True)
+    return mod
+
+
+def _fails(fn, mod, args):
+    """The pin does not pass: an assertion fails, or the mutated oracle's
+    output is so far off that the pin's extractor cannot run (a FWHM with no
+    half-maximum crossing).  The control copy shows the pins run cleanly."""
+    try:
+        fn(mod, *args)
+    except (AssertionError, ValueError, RuntimeError, FloatingPointError):
+        return True
+    return False
+
+
+def test_unmutated_copy_passes(tmp_path):
+    mod = _copy(tmp_path, "control")
+    for _, _, _, checks in MUTATIONS:
+        for fn, args in checks:
+            assert not _fails(fn, mod, args), fn.__name__
+
+
+@pytest.mark.parametrize("k", range(len(MUTATIONS)), ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_fails_a_pin(tmp_path, k):
+    name, old, new, checks = MUTATIONS[k]
+    mod = _copy(tmp_path, f"m{k}", old, new)
+    caught = [fn.__name__ for fn, args in checks if _fails(fn, mod, args)]
+    assert caught, f"no pin caught: {name}"
