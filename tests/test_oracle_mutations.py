@@ -18,73 +18,98 @@ import test_oracle_pins as pins
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle")
 
-# (name, exact source text, replacement, pins that must catch it)
+# (file, name, exact source text, replacement, pins that must catch it): "c" is
+# fzp_oracle.c, "py" the extractor and closed forms in __init__.py
 MUTATIONS = [
-    ("negative plate opens even zones",
+    ("c", "negative plate opens even zones",
      "    return ((int64_t)zone & 1) ? 1 : 0;\n  }\n  if (P->kind == ORC_FZP_POSITIVE)",
      "    return ((int64_t)zone & 1) ? 0 : 1;\n  }\n  if (P->kind == ORC_FZP_POSITIVE)",
      [(pins.test_mask_structure, ()), (pins.test_centre_configurations_on_axis, (7,))]),
-    ("positive plate equals the negative one",
+    ("c", "positive plate equals the negative one",
      "    return ((int64_t)zone & 1) ? 0 : 1;",
      "    return ((int64_t)zone & 1) ? 1 : 0;",
      [(pins.test_centre_configurations_on_axis, (7,))]),
-    ("level rate kappa L instead of kappa L / 2",
+    ("c", "level rate kappa L instead of kappa L / 2",
      "const double kL = orc_kappa(P) * (0.5 * (double)P->levels);",
      "const double kL = orc_kappa(P) * ((double)P->levels);",
      [(pins.test_binary_phase_is_disc_minus_twice_amplitude, ()), (pins.test_phase_fzp_efficiency_ladder, (4,))]),
-    ("phase plate focuses the -1 order",
+    ("c", "phase plate focuses the -1 order",
      "a = cexp(-I * 2.0 * M_PI * (double)orc_level(P, j, i) / (double)P->levels);",
      "a = cexp(I * 2.0 * M_PI * (double)orc_level(P, j, i) / (double)P->levels);",
      [(pins.test_phase_fzp_efficiency_ladder, (4,))]),
-    ("lens phase of the wrong sign",
+    ("c", "lens phase of the wrong sign",
      "if (P->kind == ORC_LENS) a = cexp(-I * M_PI",
      "if (P->kind == ORC_LENS) a = cexp(I * M_PI",
      [(pins.test_ideal_lens_gives_airy, ())]),
-    ("Bluestein pre-chirp of the wrong sign",
+    ("c", "Bluestein pre-chirp of the wrong sign",
      "cexp(-I * M_PI * omega * (double)n * (double)n);",
      "cexp(I * M_PI * omega * (double)n * (double)n);",
      [(pins.test_o1_o2_o3_agree, ("fzp",)), (pins.test_czt_dft_special_case, (16,))]),
-    ("output chirp dropped from O2",
+    ("c", "output chirp dropped from O2",
      "      acc *= pre * cexp(I * M_PI * (x * x + y * y) / lf);",
      "      acc *= pre;",
      [(pins.test_o1_o2_o3_agree, ("fzp",))]),
-    ("deformation phase 2 pi / lambda instead of 4 pi / lambda",
+    ("c", "deformation phase 2 pi / lambda instead of 4 pi / lambda",
      "a *= cexp(I * (4.0 * M_PI / P->lambda)",
      "a *= cexp(I * (2.0 * M_PI / P->lambda)",
      [(pins.test_wrinkle_tilt_shifts_the_focus, (0.0, 1)),
       (pins.test_ridge_profile_height_width_and_orientation, ())]),
-    ("deformation phase of the wrong sign",
+    ("c", "deformation phase of the wrong sign",
      "a *= cexp(I * (4.0 * M_PI / P->lambda)",
      "a *= cexp(-I * (4.0 * M_PI / P->lambda)",
      [(pins.test_wrinkle_tilt_shifts_the_focus, (0.0, 1))]),
-    ("crease normal along the line",
+    ("c", "crease normal along the line",
      "double nx = -sin(d->ridge_alpha[k]), ny = cos(d->ridge_alpha[k]);",
      "double nx = cos(d->ridge_alpha[k]), ny = sin(d->ridge_alpha[k]);",
      [(pins.test_ridge_profile_height_width_and_orientation, ())]),
-    ("ridge sigma = width / 2",
+    ("c", "ridge sigma = width / 2",
      "double sigma = d->ridge_width[k] / (2.0 * sqrt(2.0 * log(2.0)));",
      "double sigma = d->ridge_width[k] / 2.0;",
      [(pins.test_ridge_profile_height_width_and_orientation, ())]),
-    ("taper linear in r",
+    ("c", "taper linear in r",
      "(1.0 - d->taper * r2);",
      "(1.0 - d->taper * sqrt(r2));",
      [(pins.test_wrinkle_profile_period_amplitude_and_taper, ())]),
-    ("wrinkle axes swapped",
+    ("c", "wrinkle axes swapped",
      "(u * cos(d->theta) + v * sin(d->theta))",
      "(u * sin(d->theta) + v * cos(d->theta))",
      [(pins.test_wrinkle_tilt_shifts_the_focus, (0.0, 1))]),
+    ("py", "main-lobe energy with p instead of p^2",
+     "lobe = I[r <= g.r_null()].sum() * p * p",
+     "lobe = I[r <= g.r_null()].sum() * p",
+     [(pins.test_ideal_lens_gives_airy, ()), (pins.test_phase_fzp_efficiency_ladder, (2,))]),
+    ("py", "incident power with dx instead of dx^2",
+     "P_in = p_in_count * g.dx ** 2",
+     "P_in = p_in_count * g.dx",
+     [(pins.test_ideal_lens_gives_airy, ())]),
+    ("py", "cut-off frequency R / (lambda f)",
+     "nu_cut = 2.0 * g.R / (g.lam * g.f)",
+     "nu_cut = g.R / (g.lam * g.f)",
+     [(pins.test_ideal_lens_gives_airy, ())]),
+    ("py", "MTF bins spread over twice the Nyquist frequency",
+     "q = (4 * bins * bins * r2) // (M * M)",
+     "q = (bins * bins * r2) // (M * M)",
+     [(pins.test_mtf_extractor_gaussian, ())]),
+    ("py", "Airy FWHM closed form without pi",
+     "        t = math.pi * v\n        return (2 * j1(t) / t) ** 2 - 0.5",
+     "        t = v\n        return (2 * j1(t) / t) ** 2 - 0.5",
+     [(pins.test_closed_forms_match_printed_values, ())]),
+    ("py", "circular-pupil MTF with a dropped square root",
+     "(math.acos(v) - v * math.sqrt(1.0 - v * v))",
+     "(math.acos(v) - v * (1.0 - v * v))",
+     [(pins.test_ideal_lens_gives_airy, ())]),
 ]
 
 
-def _copy(tmp_path, tag, old=None, new=None):
+def _copy(tmp_path, tag, which=None, old=None, new=None):
     d = tmp_path / f"oracle_{tag}"
     d.mkdir()
-    shutil.copy(os.path.join(SRC, "__init__.py"), d / "__init__.py")
-    src = open(os.path.join(SRC, "fzp_oracle.c")).read()
-    if old is not None:
-        assert src.count(old) == 1, f"mutation target not unique: {old!r}"
-        src = src.replace(old, new)
-    (d / "fzp_oracle.c").write_text(src)
+    for fn, key in (("__init__.py", "py"), ("fzp_oracle.c", "c")):
+        src = open(os.path.join(SRC, fn)).read()
+        if which == key:
+            assert src.count(old) == 1, f"mutation target not unique: {old!r}"
+            src = src.replace(old, new)
+        (d / fn).write_text(src)
     spec = importlib.util.spec_from_file_location(f"oracle_{tag}", d / "__init__.py",
                                                   submodule_search_locations=[str(d)])
     mod = importlib.util.module_from_spec(spec)
@@ -107,14 +132,14 @@ def _fails(fn, mod, args):
 
 def test_unmutated_copy_passes(tmp_path):
     mod = _copy(tmp_path, "control")
-    for _, _, _, checks in MUTATIONS:
+    for _, _, _, _, checks in MUTATIONS:
         for fn, args in checks:
             assert not _fails(fn, mod, args), fn.__name__
 
 
-@pytest.mark.parametrize("k", range(len(MUTATIONS)), ids=[m[0] for m in MUTATIONS])
+@pytest.mark.parametrize("k", range(len(MUTATIONS)), ids=[m[1] for m in MUTATIONS])
 def test_planted_mistake_fails_a_pin(tmp_path, k):
-    name, old, new, checks = MUTATIONS[k]
-    mod = _copy(tmp_path, f"m{k}", old, new)
+    which, name, old, new, checks = MUTATIONS[k]
+    mod = _copy(tmp_path, f"m{k}", which, old, new)
     caught = [fn.__name__ for fn, args in checks if _fails(fn, mod, args)]
     assert caught, f"no pin caught: {name}"
