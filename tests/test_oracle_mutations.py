@@ -143,3 +143,75 @@ def test_planted_mistake_fails_a_pin(tmp_path, k):
     mod = _copy(tmp_path, f"m{k}", which, old, new)
     caught = [fn.__name__ for fn, args in checks if _fails(fn, mod, args)]
     assert caught, f"no pin caught: {name}"
+
+
+# The FP64 surrogate reference (oracle/surrogate.py) against its pins in
+# test_oracle_surrogate.py, which read the module through their global `S`.
+SURROGATE_MUTATIONS = [
+    ("BF16 rounding by truncation",
+     "rounded = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000",
+     "rounded = u & 0xFFFF0000",
+     ["test_bf16_rounding_matches_torch"]),
+    ("SiLU derivative taken as the sigmoid's",
+     "return s * (1.0 + z * (1.0 - s))",
+     "return s * (1.0 - s)",
+     ["test_silu_and_its_derivative", "test_gradients_match_central_differences"]),
+    ("MSE gradient without its factor 2",
+     "G = 2.0 * (yhat - Y) / (B * n_out)",
+     "G = (yhat - Y) / (B * n_out)",
+     ["test_gradients_match_central_differences"]),
+    ("bias gradient averaged over the batch",
+     "grads[l] = (r(G).T @ r(H[l]), G.sum(axis=0))",
+     "grads[l] = (r(G).T @ r(H[l]), G.mean(axis=0))",
+     ["test_gradients_match_central_differences"]),
+    ("AdamW without bias correction",
+     "c1, c2 = 1 - b1 ** t, 1 - b2 ** t",
+     "c1, c2 = 1.0, 1.0",
+     ["test_adamw_matches_torch"]),
+    ("AdamW without weight decay",
+     "(np.sqrt(vW / c2) + eps) + wd * W)",
+     "(np.sqrt(vW / c2) + eps))",
+     ["test_adamw_matches_torch"]),
+]
+
+
+def _surrogate_copy(tmp_path, tag, old=None, new=None):
+    src = open(os.path.join(SRC, "surrogate.py")).read()
+    if old is not None:
+        assert src.count(old) == 1, f"mutation target not unique: {old!r}"
+        src = src.replace(old, new)
+    f = tmp_path / f"surrogate_{tag}.py"
+    f.write_text(src)
+    spec = importlib.util.spec_from_file_location(f"surrogate_{tag}", f)
+    mod = importlib.util.module_from_spec(spec)
+    sys.modules[spec.name] = mod
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _run_with(tos, mod, name):
+    saved = tos.S
+    tos.S = mod
+    try:
+        getattr(tos, name)()
+    except (AssertionError, ValueError, FloatingPointError):
+        return True
+    finally:
+        tos.S = saved
+    return False
+
+
+def test_surrogate_unmutated_copy_passes(tmp_path):
+    import test_oracle_surrogate as tos
+    mod = _surrogate_copy(tmp_path, "control")
+    for _, _, _, names in SURROGATE_MUTATIONS:
+        for name in names:
+            assert not _run_with(tos, mod, name), name
+
+
+@pytest.mark.parametrize("k", range(len(SURROGATE_MUTATIONS)), ids=[m[0] for m in SURROGATE_MUTATIONS])
+def test_surrogate_planted_mistake_fails_a_pin(tmp_path, k):
+    import test_oracle_surrogate as tos
+    name, old, new, names = SURROGATE_MUTATIONS[k]
+    mod = _surrogate_copy(tmp_path, f"m{k}", old, new)
+    assert any(_run_with(tos, mod, n) for n in names), f"no pin caught: {name}"
