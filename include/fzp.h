@@ -187,9 +187,13 @@ typedef struct fzp_metrics_t {
 /* Build a plan (Fig. 2 Stage 1-2; Fig. 18 Stage 1-2): validate `params`,
  * derive the grids, build the zone-threshold table and the form's tables,
  * and allocate the workspace.  Synchronises the device.  On failure *out is
- * NULL and nothing is leaked.  Errors: FZP_E_INVALID (bad parameters,
- * Eq. 6 violated, M out of range), FZP_E_OOM, FZP_E_CUDA, FZP_E_UNSUPPORTED
- * (e.g. dense form with FP64 precision). */
+ * NULL and nothing is leaked.  If the row intermediate of one chunk cannot be
+ * allocated, the chunk is halved (down to 256 rows) and the allocation
+ * retried; fzp_plan_info_get reports the chunk that was allocated.  For
+ * tests, the environment variable FZP_FAULT_ALLOC_LIMIT (bytes) makes larger
+ * row-intermediate requests fail as out of memory on the host.  Errors:
+ * FZP_E_INVALID (bad parameters, Eq. 6 violated, M out of range), FZP_E_OOM,
+ * FZP_E_CUDA, FZP_E_UNSUPPORTED (e.g. dense form with FP64 precision). */
 FZP_API fzp_status fzp_plan(const fzp_params* params, fzp_plan_t* out);
 
 /* Copy the plan description into *out (host memory). */

@@ -1,8 +1,10 @@
 // plan.cu -- C ABI entry points, parameter validation, grids and the exact
 // zone-threshold table (Fig. 2 Stage 1-2; Fig. 18 Stage 1-2).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -235,6 +237,15 @@ fzp_status chunk_passes(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
   return st;
 }
 
+// cudaMalloc of a plan's row intermediate.  Host-side fault injection for
+// tests: with the environment variable FZP_FAULT_ALLOC_LIMIT set to a byte
+// count, larger requests fail as out of memory without reaching the device.
+cudaError_t workspace_malloc(void** p, size_t bytes) {
+  const char* lim = std::getenv("FZP_FAULT_ALLOC_LIMIT");
+  if (lim && *lim && bytes > (size_t)std::strtoull(lim, nullptr, 10)) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+
 // Rows per row-pass chunk: requested (multiple of 256), else as many as an
 // 8 GiB row intermediate holds; never more than the grid (rounded to 256).
 int64_t chunk_rows_for(const Plan& P) {
@@ -285,11 +296,26 @@ fzp_status fzp_plan(const fzp_params* params, fzp_plan_t* out) {
     const int64_t M2 = (2 * (int64_t)P->M + 511) / 512 * 512;
     P->chunk_rows = chunk_rows_for(*P);
     P->c1_rows = M2;
-    const int64_t rows = P->chunk_rows;
+    // The row intermediate of one chunk.  When it cannot be allocated the
+    // chunk is halved (down to 256 rows) and the allocation retried, as the
+    // paper's engine halves its row batch on a GPU out-of-memory error
+    // (Fig. 18 Stage 2); only then is FZP_E_OOM returned.
+    const size_t esz = P->precision == FZP_PREC_FP64 ? sizeof(double) : sizeof(float);
     cudaError_t e = cudaSuccess;
-    if (P->precision == FZP_PREC_FP64) e = cudaMalloc(&P->d_C1d, (size_t)(M2 * rows) * sizeof(double));
-    else e = cudaMalloc(&P->d_C1, (size_t)(M2 * rows) * sizeof(float));
-    P->device_bytes += (size_t)(M2 * rows) * (P->precision == FZP_PREC_FP64 ? 8 : 4);
+    while (true) {
+      const size_t bytes = (size_t)(M2 * P->chunk_rows) * esz;
+      void* c1 = nullptr;
+      e = workspace_malloc(&c1, bytes);
+      if (e == cudaSuccess) {
+        if (P->precision == FZP_PREC_FP64) P->d_C1d = static_cast<double*>(c1);
+        else P->d_C1 = static_cast<float*>(c1);
+        P->device_bytes += bytes;
+        break;
+      }
+      if (e != cudaErrorMemoryAllocation || P->chunk_rows <= 256) break;
+      cudaGetLastError();
+      P->chunk_rows = std::max<int64_t>(256, (P->chunk_rows / 2 + 255) / 256 * 256);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&P->d_Uacc, (size_t)P->M * P->M * sizeof(double2));
     if (e == cudaSuccess) e = cudaMalloc(&P->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&P->d_metrics, 8192 * sizeof(double) + (size_t)P->M * P->M * sizeof(double2));
