@@ -196,6 +196,28 @@ typedef struct fzp_metrics_t {
  * FZP_E_CUDA, FZP_E_UNSUPPORTED (e.g. dense form with FP64 precision). */
 FZP_API fzp_status fzp_plan(const fzp_params* params, fzp_plan_t* out);
 
+/* The host part of fzp_plan alone: validate `params`, derive the grids (Fig. 2
+ * and Fig. 18 Stage 1) and check the zone-rule limits, without any CUDA call
+ * or allocation (it runs on a machine without a GPU), and describe the plan
+ * that fzp_plan would build: N, c, the Eq. 3 zone count, the threshold count,
+ * dx, R_eff, kappa, x0, M, form, precision, chunk rows, FFT length (Bluestein),
+ * promotion length (dense), levels, passes, centre configuration.  Fields
+ * that depend on the device (fft_inner, ctas, device_bytes, an automatic
+ * cluster size, row_batch) are 0, and so are the form-specific fields when the
+ * precision is FZP_PREC_AUTO_1E4 (form reported as FZP_FORM_AUTO).  The chunk
+ * is the one fzp_plan tries first.  Errors: as fzp_plan's validation. */
+FZP_API fzp_status fzp_plan_query(const fzp_params* params, fzp_plan_info* out);
+
+/* The zone-threshold table that fzp_plan builds on the host and uploads
+ * (Sec. 2.2, Eq. 4; the exact mask rule): S_m = min{s : floor(fl(s kappa_L))
+ * >= m} for m = 1 .. count, s the integer squared distance from the axis in
+ * samples, kappa_L the zone-step rate (kappa, or kappa L / 2 for an L-level
+ * plate).  Writes *count and the first min(capacity, count) entries to `out`
+ * (host memory; NULL with capacity 0 asks for the count).  No CUDA call.
+ * Errors: as fzp_plan's validation; FZP_E_INVALID for a NULL count or a NULL
+ * out with capacity > 0. */
+FZP_API fzp_status fzp_zone_thresholds(const fzp_params* params, int64_t* out, int64_t capacity, int64_t* count);
+
 /* Copy the plan description into *out (host memory). */
 FZP_API fzp_status fzp_plan_info_get(fzp_plan_t plan, fzp_plan_info* out);
 

@@ -93,6 +93,9 @@ def lib() -> ctypes.CDLL:
         sig = {
             "fzp_plan": [ctypes.POINTER(Params), ctypes.POINTER(vp)],
             "fzp_plan_info_get": [vp, ctypes.POINTER(PlanInfo)],
+            "fzp_plan_query": [ctypes.POINTER(Params), ctypes.POINTER(PlanInfo)],
+            "fzp_zone_thresholds": [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_int64), i64,
+                                    ctypes.POINTER(ctypes.c_int64)],
             "fzp_plan_destroy": [vp],
             "fzp_propagate_roi": [vp, i64, i64, vp, i32, vp],
             "fzp_intensity": [vp, vp, vp, vp],
@@ -320,6 +323,34 @@ class SurrogateNet:
             self.close()
         except Exception:
             pass
+
+
+def _params(D, f, lam, M, pitch, dx=0.0, N=0, form=FORM_AUTO, precision=PREC_FP32, stripe_rows=0, promote=0,
+            row_batch=0, cluster=0, levels=0, centre_open=0) -> Params:
+    return Params(D=D, f=f, lam=lam, dx=dx, N=N, M=M, form=form, pitch=pitch, precision=precision,
+                  stripe_rows=stripe_rows, deform=None, promote=promote, row_batch=row_batch, cluster=cluster,
+                  levels=levels, centre_open=centre_open)
+
+
+def plan_query(**kw) -> dict:
+    """fzp_plan_query: the plan description fzp_plan would produce (keyword
+    arguments of Plan, without deform), from host code alone -- no GPU needed."""
+    p = _params(**kw)
+    inf = PlanInfo()
+    _check(lib().fzp_plan_query(ctypes.byref(p), ctypes.byref(inf)))
+    return {k: getattr(inf, k) for k, _ in inf._fields_}
+
+
+def zone_thresholds(**kw):
+    """fzp_zone_thresholds: the host-built zone-threshold table S_m (numpy int64)."""
+    import numpy as np
+    p = _params(**kw)
+    n = ctypes.c_int64()
+    _check(lib().fzp_zone_thresholds(ctypes.byref(p), None, 0, ctypes.byref(n)))
+    out = np.zeros(n.value, dtype=np.int64)
+    _check(lib().fzp_zone_thresholds(ctypes.byref(p), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                     out.size, ctypes.byref(n)))
+    return out
 
 
 def metrics_noalloc(field, D: float, f: float, lam: float, M: int, pitch: float, dx: float = 0.0, N: int = 0,

@@ -341,6 +341,65 @@ fzp_status fzp_plan(const fzp_params* params, fzp_plan_t* out) {
   return FZP_OK;
 }
 
+// Host part of a plan: validation, grids and the zone-rule limits, without
+// any CUDA call.  Returns the disc limit and the last zone step through *sR
+// and *zmax.
+static fzp_status plan_host(const fzp_params* params, Plan& P, int64_t* sR, int64_t* zmax) {
+  fzp_status st = validate_and_derive(params, P);
+  if (st != FZP_OK) return st;
+  *sR = disc_limit(P.dx2, P.R2);
+  *zmax = zone_host(*sR, P.kappa_mask);
+  if (*sR >= (1ll << 46) || *zmax + 1 >= (1ll << 24))
+    return set_error(FZP_E_UNSUPPORTED, "aperture too large for the exact zone rule (s_R=%lld, zones=%lld)",
+                     (long long)*sR, (long long)*zmax);
+  if (!(std::ldexp(P.kappa_mask, 64) < 18446744073709551616.0))
+    return set_error(FZP_E_INVALID, "kappa >= 1: grid far too coarse");
+  return FZP_OK;
+}
+
+fzp_status fzp_plan_query(const fzp_params* params, fzp_plan_info* out) {
+  if (!params || !out) return set_error(FZP_E_INVALID, "NULL argument");
+  Plan P;
+  int64_t sR = 0, zmax = 0;
+  const fzp_status st = plan_host(params, P, &sR, &zmax);
+  if (st != FZP_OK) return st;
+  *out = fzp_plan_info{};
+  out->N = P.N; out->c = P.c; out->total_zones = P.total_zones; out->n_thresholds = zmax + 2;
+  out->dx = P.dx; out->R = P.R; out->kappa = P.kappa; out->x0 = P.x0;
+  out->M = P.M;
+  const bool tuned = params->precision == FZP_PREC_AUTO_1E4;  // form chosen by measurement
+  out->form = tuned ? FZP_FORM_AUTO : P.form;
+  out->precision = P.precision;
+  out->stripe_rows = P.stripe_rows;
+  out->chunk_rows = chunk_rows_for(P);
+  if (!tuned && P.form == FZP_FORM_BLUESTEIN) {
+    int64_t L = 1;
+    while (L < P.N + P.M - 1) L <<= 1;
+    out->fft_length = L;
+  }
+  out->promote = !tuned && P.form == FZP_FORM_DENSE ? (P.promote_req > 0 ? P.promote_req : 128) : 0;
+  out->cluster = !tuned && P.form == FZP_FORM_DENSE ? P.cluster_req : 0;
+  out->levels = P.levels;
+  out->passes = P.passes.empty() ? 1 : (int32_t)P.passes.size();
+  out->centre_open = P.mg.centre_open;
+  return FZP_OK;
+}
+
+fzp_status fzp_zone_thresholds(const fzp_params* params, int64_t* out, int64_t capacity, int64_t* count) {
+  if (!params || !count) return set_error(FZP_E_INVALID, "NULL argument");
+  if (capacity < 0 || (capacity > 0 && !out)) return set_error(FZP_E_INVALID, "bad output buffer");
+  Plan P;
+  int64_t sR = 0, zmax = 0;
+  const fzp_status st = plan_host(params, P, &sR, &zmax);
+  if (st != FZP_OK) return st;
+  std::vector<int64_t> S;
+  thresholds(P.kappa_mask, zmax + 2, S);
+  *count = (int64_t)S.size();
+  const int64_t n = std::min<int64_t>(capacity, *count);
+  for (int64_t k = 0; k < n; ++k) out[k] = S[(size_t)k];
+  return FZP_OK;
+}
+
 fzp_status fzp_plan_info_get(fzp_plan_t plan, fzp_plan_info* out) {
   if (!plan || !out) return set_error(FZP_E_INVALID, "NULL argument");
   const Plan& P = *plan;
