@@ -191,7 +191,11 @@ typedef struct fzp_metrics_t {
  * allocated, the chunk is halved (down to 256 rows) and the allocation
  * retried; fzp_plan_info_get reports the chunk that was allocated.  For
  * tests, the environment variable FZP_FAULT_ALLOC_LIMIT (bytes) makes larger
- * row-intermediate requests fail as out of memory on the host.  Errors:
+ * row-intermediate requests fail as out of memory on the host.
+ * Size limits (FZP_E_UNSUPPORTED beyond them): the exact zone rule needs the
+ * squared disc radius in samples s_R < 2^46 (N up to about 1.67e7 for a
+ * full-aperture plate) and fewer than 2^24 zone steps; the Bluestein form
+ * needs N + M - 1 <= 2^24 (its FFT length, a power of two).  Errors:
  * FZP_E_INVALID (bad parameters, Eq. 6 violated, M out of range), FZP_E_OOM,
  * FZP_E_CUDA, FZP_E_UNSUPPORTED (e.g. dense form with FP64 precision). */
 FZP_API fzp_status fzp_plan(const fzp_params* params, fzp_plan_t* out);
