@@ -375,6 +375,8 @@ fzp_status fzp_plan_query(const fzp_params* params, fzp_plan_info* out) {
   if (!tuned && P.form == FZP_FORM_BLUESTEIN) {
     int64_t L = 1;
     while (L < P.N + P.M - 1) L <<= 1;
+    // the four-step split L = L1 L2 with L1 <= L2 <= 4096 (bluestein.cu)
+    if (L > (1ll << 24)) return set_error(FZP_E_UNSUPPORTED, "FFT length %lld above %lld", (long long)L, 1ll << 24);
     out->fft_length = L;
   }
   out->promote = !tuned && P.form == FZP_FORM_DENSE ? (P.promote_req > 0 ? P.promote_req : 128) : 0;

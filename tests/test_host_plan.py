@@ -134,3 +134,22 @@ def test_threshold_export_buffer_rules(fzp):
     assert L.fzp_zone_thresholds(ctypes.byref(p), buf, 3, ctypes.byref(n)) == fzp.FZP_OK
     full = fzp.zone_thresholds(D=4e-3, f=20e-3, lam=LAM, M=256, pitch=0.2e-6)
     assert list(buf) == list(full[:3]) and n.value == len(full)
+
+
+def test_query_size_limits(fzp):
+    """The zone rule's s_R < 2^46 and the Bluestein FFT length <= 2^24: a
+    5 m plate sampled to N = 16,700,001 passes, N = 16,800,001 does not (s_R
+    above 2^46); N = 16,777,001 (N + M - 1 above 2^24, s_R still below 2^46)
+    is refused to the Bluestein form but not to the dense one."""
+    lam, D, f = 532e-9, 5.0, 25.0
+    kw = dict(D=D, f=f, lam=lam, M=512, pitch=lam * 5 / 8)
+    ok = fzp.plan_query(dx=D / 16_700_001, form=fzp.FORM_DENSE, precision=fzp.PREC_SPLIT_BF16, **kw)
+    assert ok["N"] == 16_700_001
+    with pytest.raises(fzp.FzpError) as e:
+        fzp.plan_query(dx=D / 16_800_001, form=fzp.FORM_DENSE, precision=fzp.PREC_SPLIT_BF16, **kw)
+    assert e.value.status == fzp.FZP_E_UNSUPPORTED and "zone rule" in str(e.value)
+    big = fzp.plan_query(dx=D / 16_777_001, form=fzp.FORM_DENSE, precision=fzp.PREC_SPLIT_BF16, **kw)
+    assert big["N"] == 16_777_001
+    with pytest.raises(fzp.FzpError) as e:
+        fzp.plan_query(dx=D / 16_777_001, form=fzp.FORM_BLUESTEIN, precision=fzp.PREC_FP32, **kw)
+    assert e.value.status == fzp.FZP_E_UNSUPPORTED and "FFT length" in str(e.value)
