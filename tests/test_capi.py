@@ -107,3 +107,30 @@ def test_struct_layouts_match_header(fzp, tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_other_entry_points_validate_before_the_device(fzp):
+    """Batch, surrogate and no-allocation metric calls reject bad arguments on
+    the host (these run here, with no GPU)."""
+    import ctypes
+    L = fzp.lib()
+    h = ctypes.c_void_p()
+    assert L.fzp_batch_plan(None, 1, ctypes.byref(h)) == fzp.FZP_E_INVALID
+    good = fzp._params(D=1e-3, f=5e-3, lam=632.8e-9, M=64, pitch=0.4e-6)
+    arr = (fzp.Params * 1)(good)
+    assert L.fzp_batch_plan(arr, 0, ctypes.byref(h)) == fzp.FZP_E_INVALID and not h.value
+    bad = fzp._params(D=-1.0, f=5e-3, lam=632.8e-9, M=64, pitch=0.4e-6)
+    arr = (fzp.Params * 2)(bad, good)
+    assert L.fzp_batch_plan(arr, 2, ctypes.byref(h)) == fzp.FZP_E_INVALID and not h.value
+    assert b"positive" in L.fzp_last_error()
+    for sizes in [(0, 512, 3, 4114, 256), (8, 512, 0, 4114, 256), (8, 512, 3, 4114, 0), (8, 70000, 3, 4, 4)]:
+        assert L.fzp_surrogate_create(*sizes, 0, ctypes.byref(h)) == fzp.FZP_E_INVALID and not h.value
+    host = (ctypes.c_double * 2)()
+    for kw in (dict(M=1024), dict(M=100), dict(N=1000, M=64), dict(levels=70, M=64)):
+        base = dict(D=1e-3, f=5e-3, lam=632.8e-9, pitch=0.4e-6)
+        base.update(kw)
+        with pytest.raises(fzp.FzpError) as e:
+            fzp.metrics_noalloc(ctypes.addressof(host), **base)
+        assert e.value.status == fzp.FZP_E_INVALID
+    assert L.fzp_batch_destroy(None) == fzp.FZP_OK
+    assert L.fzp_surrogate_destroy(None) == fzp.FZP_OK
