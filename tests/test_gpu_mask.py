@@ -124,3 +124,29 @@ def test_dense_level_maps_table_grids(env, table):
             got = _export(fzp, torch, plan, j0, j0 + 3, g.N)
             ref = O.mask_rows(g, j0, j0 + 3)
             assert np.array_equal(got, ref), (table, j0, int(np.sum(got != ref)))
+
+
+@pytest.mark.parametrize("D", [1.0, 5.0])
+def test_dense_walker_export_large_grids(env, D):
+    """The row walker of single-CTA launches (the automatic choice for M <= 128)
+    far from the axis, where the boundary distances reach a ~ N/2 and its
+    approximate square root needs its full correction range: D = 1 m at
+    f/# = 5 (N = 1,264,223) and Table 5's grid (N = 15,037,595, L = 2 level
+    map), rows through the axis, at mid radius and near the edge."""
+    fzp, torch, O = env
+    if D == 1.0:
+        lam = 632.8e-9
+        g = O.Geometry(D=D, f=5 * D, lam=lam, M=64, p=lam * 5 / 8)
+        extra = {}
+    else:
+        lam, f = 532e-9, 25.0
+        g = O.Geometry(D=D, f=f, lam=lam, M=64, p=lam * 5 / 8, dx=lam * f / (D / 2) / 16, kind=O.FZP_PHASE,
+                       levels=2)
+        extra = dict(dx=g.dx, levels=2)
+    with fzp.Plan(D=g.D, f=g.f, lam=g.lam, M=g.M, pitch=g.p, N=g.N, form=fzp.FORM_DENSE,
+                  precision=fzp.PREC_SPLIT_BF16, cluster=1, **extra) as plan:
+        assert plan.info["cluster"] == 1 and plan.info["N"] == g.N
+        for j0 in [g.c - 1, g.c // 2, g.N // 50]:
+            got = _export(fzp, torch, plan, j0, j0 + 3, g.N)
+            ref = O.mask_rows(g, j0, j0 + 3)
+            assert np.array_equal(got, ref), (D, j0, int(np.sum(got != ref)))
