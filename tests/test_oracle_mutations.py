@@ -74,6 +74,10 @@ MUTATIONS = [
      "(u * cos(d->theta) + v * sin(d->theta))",
      "(u * sin(d->theta) + v * cos(d->theta))",
      [(pins.test_wrinkle_tilt_shifts_the_focus, (0.0, 1))]),
+    ("py", "FWHM peak taken as the on-axis sample (no parabola)",
+     "peak = y0 - 0.125 * (yp - ym) ** 2 / den if den != 0 else y0",
+     "peak = y0",
+     [(pins.test_fwhm_extractor_off_sample_peak, (0.45,))]),
     ("py", "main-lobe energy with p instead of p^2",
      "lobe = I[r <= g.r_null()].sum() * p * p",
      "lobe = I[r <= g.r_null()].sum() * p",

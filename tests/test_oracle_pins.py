@@ -280,6 +280,18 @@ def test_fwhm_extractor_gaussian(oracle_mod):
     assert abs(fw / (2 * math.sqrt(2 * math.log(2)) * sigma) - 1) < 2e-4
 
 
+@pytest.mark.parametrize("off", [0.3, 0.45])
+def test_fwhm_extractor_off_sample_peak(oracle_mod, off):
+    """A Gaussian whose peak falls between samples (0.3 and 0.45 of a sample
+    from the on-axis one): the 3-point parabola (Fig. 18 'parabolic peak')
+    recovers the peak height, so the spline crossings give the FWHM within
+    1e-4; taking the on-axis sample as the peak would widen it by 1-3e-3."""
+    M, sigma = 128, 5.0
+    x = np.arange(M) - M // 2 - off
+    fw = oracle_mod.fwhm_row(np.exp(-x ** 2 / (2 * sigma ** 2)), 1.0)
+    assert abs(fw / (2 * math.sqrt(2 * math.log(2)) * sigma) - 1) < 1e-4
+
+
 def test_mtf_extractor_gaussian(oracle_mod):
     """A Gaussian PSF has a Gaussian OTF, exp(-2 pi^2 sigma^2 nu^2); each radial
     bin must hold the mean of that closed form over the FFT samples whose
