@@ -78,6 +78,10 @@ MUTATIONS = [
      "peak = y0 - 0.125 * (yp - ym) ** 2 / den if den != 0 else y0",
      "peak = y0",
      [(pins.test_fwhm_extractor_off_sample_peak, (0.45,))]),
+    ("py", "MTF samples at q nu_cut / 16 instead of (q + 1/2) nu_cut / 16",
+     "mtf_at(centres, mean, (q + 0.5) * nu_cut / 16)",
+     "mtf_at(centres, mean, q * nu_cut / 16)",
+     [(pins.test_ideal_lens_gives_airy, ())]),
     ("py", "main-lobe energy with p instead of p^2",
      "lobe = I[r <= g.r_null()].sum() * p * p",
      "lobe = I[r <= g.r_null()].sum() * p",
