@@ -90,3 +90,63 @@ def test_ceil_sqrt46_corrections_cover_the_approximate_root():
         r = (root * (1 + rel)).astype(np.float32)
         got = _ceil_sqrt46_from(np.floor(r).astype(np.uint32), ts)
         assert np.array_equal(got, want), rel
+
+
+def _zone_of(s: int, K64: int, thr, nthr: int) -> int:
+    """The device's zone_of in exact integers: the high word of the 64 x 64-bit
+    product s K64, and the threshold table where the product lies within 2^-17
+    below or 2^-28 above an integer (the low word's window)."""
+    prod = s * K64
+    z, lo = prod >> 64, prod & ((1 << 64) - 1)
+    if lo < (1 << 36) or lo >= 0xFFFF800000000000:
+        if z >= 1 and thr[z - 1] > s:
+            z -= 1
+        elif z < nthr and thr[z] <= s:
+            z += 1
+    return z
+
+
+def test_device_zone_rule_equals_the_ieee_rule():
+    """Reading 2's exactness argument, checked on the CPU: the fixed-point
+    product with its threshold-table window gives floor(fl(s kappa_L)) for
+    every s tried -- random s over the disc and s at, just below and just
+    above sampled thresholds, on config 1, the 5 m plate, and the grids of
+    Table 1 (L = 16) and Table 5 (L = 2), up to s near 2^45.6.  The table is
+    the library's own (fzp_zone_thresholds) and K64 = floor(kappa_L 2^64)."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2609_01978_gb300 as fzp
+    rng = np.random.default_rng(3)
+    lam1, lam2 = 632.8e-9, 532e-9
+    cases = [
+        dict(D=4e-3, f=20e-3, lam=lam1),
+        dict(D=5.0, f=25.0, lam=lam1),
+        dict(D=1.0, f=5.0, lam=lam2, levels=16, dx=lam2 * 5.0 / 0.5 / 64),
+        dict(D=5.0, f=25.0, lam=lam2, levels=2, dx=lam2 * 25.0 / 2.5 / 16),
+    ]
+    for kw in cases:
+        kw = dict(kw, M=256, pitch=kw["lam"] * 5 / 8)
+        q = fzp.plan_query(**kw)
+        thr = [int(x) for x in fzp.zone_thresholds(**kw)]
+        L = kw.get("levels", 0)
+        rate = q["kappa"] * (0.5 * L if L >= 2 else 1.0)
+        K64 = math.floor(math.ldexp(rate, 64))
+        dx2, R2 = q["dx"] ** 2, q["R"] ** 2
+        sR = int(R2 // dx2)
+        while float(sR + 1) * dx2 <= R2:
+            sR += 1
+        samples = [0, 1, sR, sR - 1] + [int(x) for x in rng.integers(0, sR, 20_000)]
+        for m in rng.integers(1, len(thr) - 1, 5_000):
+            S = thr[m - 1]
+            samples += [S - 1, S, S + 1]
+        in_window = 0
+        for s in samples:
+            if 0 <= s <= sR:
+                assert _zone_of(s, K64, thr, len(thr)) == math.floor(float(s) * rate), (kw, s)
+                lo = (s * K64) & ((1 << 64) - 1)
+                in_window += lo < (1 << 36) or lo >= 0xFFFF800000000000
+        assert in_window > 100, in_window  # the table's window was exercised
+        assert sR > (1 << 40) or kw["D"] < 1
