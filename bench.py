@@ -14,12 +14,18 @@ lambda = 632.8 nm, f/# = 5 (f = 1.25 m), 4 samples per outermost zone width
 lambda f/# / 8 = 0.3955 um, centred on the focus.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--form dense|bluestein]
-                  [--impl ours|reference] [--workload fzp-d0.25m|fzp-d1m|...|fzp-d5m]
-                  [--plain-rows R] [--e2e-steps E]
+                  [--impl ours|reference] [--workload NAME] [--rows R]
+                  [--plain-rows R] [--e2e-steps E] [--no-plain] [--no-cpu-baseline]
+                  [--ref-rows R] [--instances I]
 
---plain-rows R times the plain FP32 form on the R aperture rows around the
-centre instead of all N (its cost per row does not depend on the row), for
-the large-D workloads; --e2e-steps 0 leaves out the end-to-end leg.
+Workloads: fzp-d0.05m (small case for profiler captures), fzp-d0.25m,
+fzp-d1m ... fzp-d5m (the D sweep at f/# = 5), fzp-t1 ... fzp-t5 (the phase
+plates of Tables 1-5 on their own grids), membranes (a batch of the seeded
+deformed membranes, autotuned per instance, one CUDA graph per step).
+--rows R times R central aperture rows per step (a sample, named in the
+config); --plain-rows R does the same for the plain FP32 form (its cost per
+row does not depend on the row); --e2e-steps 0 leaves out the end-to-end leg;
+--ref-rows sets the oracle's rows per step in the reference arm.
 
 Under torchrun (N > 1) every rank propagates its own copy of the aperture
 (independent problems: weak scaling, no collective on the data path); rank 0
