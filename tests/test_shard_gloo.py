@@ -69,3 +69,25 @@ def test_two_rank_gloo_sum_equals_full_field():
     g = O.Geometry(D=4e-3 / 4, f=20e-3 / 4, lam=632.8e-9, M=64, p=0.3e-6)
     ref = O.field_czt(g)
     assert np.linalg.norm(U - ref) / np.linalg.norm(ref) < 1e-12
+
+
+def test_chord_weights_count_the_aperture(oracle_mod):
+    """The shard balance weights (samples of each row inside the disc) sum to
+    the oracle's aperture count, and the weighted split gives each of four
+    ranks close to a quarter of the open samples."""
+    from paper_2609_01978_gb300.shard import chord_weights, row_ranges
+    O = oracle_mod
+    for D, f in [(4e-3, 20e-3), (0.05, 0.25)]:
+        g = O.Geometry(D=D, f=f, lam=632.8e-9, M=64, p=0.3e-6)
+        dx2, R2 = g.dx * g.dx, g.R * g.R
+        sR = int(R2 // dx2)
+        while (sR + 1) * dx2 <= R2:
+            sR += 1
+        while sR * dx2 > R2:
+            sR -= 1
+        w = chord_weights(g.N, g.c, sR)
+        assert sum(w) == O.count_aperture(g)
+        rr = row_ranges(g.N, 4, w)
+        share = [sum(w[a:b]) / sum(w) for a, b in rr]
+        assert rr[0][0] == 0 and rr[-1][1] == g.N
+        assert max(abs(x - 0.25) for x in share) < 2.0 * max(w) / sum(w) + 1e-12
