@@ -153,3 +153,29 @@ def test_query_size_limits(fzp):
     with pytest.raises(fzp.FzpError) as e:
         fzp.plan_query(dx=D / 16_777_001, form=fzp.FORM_BLUESTEIN, precision=fzp.PREC_FP32, **kw)
     assert e.value.status == fzp.FZP_E_UNSUPPORTED and "FFT length" in str(e.value)
+
+
+def test_query_random_geometries(fzp, oracle_mod):
+    """200 random plates (D from 1 mm to 5 m, f/# from 2 to 20, 450-700 nm,
+    levels 0-16, optional explicit dx at 1-8x the Nyquist spacing): the
+    library's grid and zone count equal the oracle's."""
+    O = oracle_mod
+    rng = np.random.default_rng(2026)
+    for _ in range(200):
+        D = float(10 ** rng.uniform(-3, math.log10(5.0)))
+        fnum = float(rng.uniform(2, 20))
+        lam = float(rng.uniform(450e-9, 700e-9))
+        L = int(rng.choice([0, 0, 2, 3, 4, 8, 16]))
+        f = fnum * D
+        dx = 0.0
+        if rng.uniform() < 0.5:
+            dx = lam * f / (2 * D) / float(rng.uniform(1.0, 8.0))
+        N_est = D / (dx if dx else lam * f / (2 * D * max(L, 2)))
+        if N_est > 3e6:
+            continue  # keep the oracle's own grid arithmetic quick
+        kind = O.FZP_PHASE if L >= 2 else O.FZP_PARAXIAL
+        g = O.Geometry(D=D, f=f, lam=lam, M=64, p=lam * fnum / 8, dx=dx or None, kind=kind, levels=L)
+        q = fzp.plan_query(D=D, f=f, lam=lam, M=64, pitch=lam * fnum / 8, dx=dx, levels=L)
+        assert q["N"] == g.N and q["c"] == g.c, (D, fnum, lam, L, dx)
+        assert q["dx"] == pytest.approx(g.dx, rel=1e-15) and q["R"] == pytest.approx(g.R, rel=1e-15)
+        assert q["total_zones"] == g.total_zones()
