@@ -147,7 +147,9 @@ class Geometry:
     pixel c = (N-1)/2 sits on the optical axis.  Aperture radius
     R_eff = min(D/2, lambda f / (2 dx_in)) (Fig. 2, Stage 2).
     ROI (Fig. 2, Stage 1, decoupled): M samples at pitch p; reading taken here:
-    x_m = (m - M/2) p so that sample M/2 is on the axis.
+    x_m = (m - M/2) p so that sample M/2 is on the axis, unless ``x0`` gives
+    the first ROI coordinate (the same on both axes: x_m = x0 + m p,
+    y_n = x0 + n p, the A of Eq. 10 taken from the first ROI coordinate).
     """
     D: float
     f: float
@@ -159,6 +161,7 @@ class Geometry:
     kind: int = FZP_PARAXIAL
     deform: Optional[Deform] = None
     levels: int = 0  # FZP_PHASE: phase levels L (>= 2)
+    x0: Optional[float] = None  # first ROI coordinate, both axes (None: centred on the focus)
 
     def __post_init__(self):
         if self.kind == FZP_PHASE and self.levels < 2:
@@ -175,7 +178,8 @@ class Geometry:
         if self.N % 2 == 0:
             raise ValueError("N must be odd (centred grid)")
         self.R = min(self.D / 2.0, self.lam * self.f / (2.0 * self.dx))
-        self.x0 = -(self.M // 2) * self.p
+        if self.x0 is None:
+            self.x0 = -(self.M // 2) * self.p
         self._deform_c = self.deform.to_c() if self.deform is not None else None
 
     @property

@@ -74,6 +74,14 @@ MUTATIONS = [
      "(u * cos(d->theta) + v * sin(d->theta))",
      "(u * sin(d->theta) + v * cos(d->theta))",
      [(pins.test_wrinkle_tilt_shifts_the_focus, (0.0, 1))]),
+    ("c", "aperture count drops the on-axis sample of each row",
+     "    total += 2 * lo + 1;",
+     "    total += 2 * lo;",
+     [(pins.test_count_aperture_is_the_disc_lattice_count, (4e-3, 20e-3, None))]),
+    ("c", "aperture count with a strict rim inequality",
+     "if ((double)(dj * dj + mid * mid) * dx2 <= R2) lo = mid;",
+     "if ((double)(dj * dj + mid * mid) * dx2 < R2) lo = mid;",
+     [(pins.test_count_aperture_is_the_disc_lattice_count, (2000 * 2.0 ** -20, 20e-3, 2.0 ** -20))]),
     ("py", "FWHM peak taken as the on-axis sample (no parabola)",
      "peak = y0 - 0.125 * (yp - ym) ** 2 / den if den != 0 else y0",
      "peak = y0",

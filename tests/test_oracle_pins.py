@@ -62,7 +62,7 @@ def _tiny(oracle_mod, **kw):
     return oracle_mod.Geometry(**base)
 
 
-@pytest.mark.parametrize("case", ["fzp", "fzp_oddM", "fzp_exact", "lens", "deform", "offaxis_pitch"])
+@pytest.mark.parametrize("case", ["fzp", "fzp_oddM", "fzp_exact", "lens", "deform", "offaxis_pitch", "offaxis_roi"])
 def test_o1_o2_o3_agree(oracle_mod, case):
     O = oracle_mod
     if case == "fzp":
@@ -77,8 +77,11 @@ def test_o1_o2_o3_agree(oracle_mod, case):
         d = O.Deform(amp=632.8e-9 / 4, period=1.3e-4, theta=0.7, taper=0.4,
                      ridges=[(1e-5, -2e-5, 0.3, 632.8e-9 / 8, 3e-5), (-4e-5, 0.0, 2.0, -632.8e-9 / 10, 5e-5)])
         g = _tiny(O, deform=d)
-    else:
+    elif case == "offaxis_pitch":
         g = _tiny(O, M=10, p=1.1e-6)
+    else:  # ROI whose first sample is off the centred grid by 3.3 pitches on both axes
+        g = _tiny(O, M=12, p=0.5e-6, x0=-2.7 * 0.5e-6)
+        assert abs(g.coords_out()[0] + 2.7 * 0.5e-6) < 1e-20
     u1 = O.field_direct(g)
     assert rel(O.field_separable(g), u1) < 1e-12
     assert rel(O.field_czt(g), u1) < 1e-12
@@ -240,6 +243,45 @@ def test_mask_structure(oracle_mod):
     r_flip = flips * g.dx
     r_m = np.sqrt(np.arange(1, len(flips) + 1) * g.lam * g.f)
     assert np.all(np.abs(r_flip - r_m) <= g.dx)
+
+
+def _disc_limit_exact(dx, R):
+    """Largest integer s with fl(s dx^2) <= fl(R^2): the disc rule of Fig. 2
+    Stage 2 on squared sample distances, found from the exact quotient and
+    settled by the same IEEE products (Python floats)."""
+    from fractions import Fraction
+    dx2, R2 = dx * dx, R * R
+    s = int(Fraction(R2) / Fraction(dx2))
+    while float(s + 1) * dx2 <= R2:
+        s += 1
+    while s > 0 and float(s) * dx2 > R2:
+        s -= 1
+    return s
+
+
+@pytest.mark.parametrize("D,f,dx", [(4e-3, 20e-3, None), (0.02, 0.1, None), (0.05, 0.25, None),
+                                    (2000 * 2.0 ** -20, 20e-3, 2.0 ** -20)])
+def test_count_aperture_is_the_disc_lattice_count(oracle_mod, D, f, dx):
+    """P_in = (samples inside R_eff) dx^2 (Fig. 2 Stage 2, reading 5).  The
+    oracle counts by bisection on each row; the count must equal the number
+    of lattice points (a, b) with a^2 + b^2 <= s_R (Gauss's circle count,
+    summed row by row with exact integer square roots), and, on config 1's
+    grid, the number of open samples of the clear pupil's per-sample mask.
+    A count that drops the on-axis column of each row (2 lo instead of
+    2 lo + 1) fails here; so does a strict inequality at the rim, on the grid
+    with dx = 2^-20 m and R = 1000 dx, where R^2 / dx^2 = 10^6 exactly and
+    samples such as (600, 800) lie on the rim."""
+    O = oracle_mod
+    g = O.Geometry(D=D, f=f, lam=632.8e-9, M=8, p=1e-6, dx=dx)
+    sR = _disc_limit_exact(g.dx, g.R)
+    b = math.isqrt(sR)
+    lattice = sum(2 * math.isqrt(sR - a * a) + 1 for a in range(-b, b + 1))
+    assert O.count_aperture(g) == lattice, (D, O.count_aperture(g), lattice)
+    if D == 4e-3:
+        gc = O.Geometry(D=D, f=f, lam=632.8e-9, M=8, p=1e-6, kind=O.CIRC)
+        assert int(O.mask_rows(gc, 0, gc.N).sum(dtype=np.int64)) == lattice
+        # the disc of Fig. 2 Stage 2 holds pi R^2 / dx^2 samples to O(R / dx)
+        assert abs(lattice * g.dx ** 2 / (math.pi * g.R ** 2) - 1) < 4 * g.dx / g.R
 
 
 def test_total_zones_eq3(oracle_mod):
