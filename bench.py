@@ -8,15 +8,16 @@ accumulation, the output chirp / prefactor epilogue, and the metric extractor
 (FWHM, DE, MTF).  The metric is aperture samples (N^2 per step) per second into
 a 512^2 ROI.
 
-Workload (default "fzp-d0.25m"): binary amplitude FZP, D = 0.25 m,
-lambda = 632.8 nm, f/# = 5 (f = 1.25 m), 4 samples per outermost zone width
-(dx = 0.791 um, N = 316,057 per side, 9.99e10 samples), ROI 512^2 at
-lambda f/# / 8 = 0.3955 um, centred on the focus.
+Workload (default "fzp-d1m", the first plate of the D sweep at f/# = 5):
+binary amplitude FZP, D = 1.0 m, lambda = 632.8 nm, f/# = 5 (f = 5 m), 4
+samples per outermost zone width (dx = 0.791 um, N = 1,264,223 per side,
+1.60e12 samples), ROI 512^2 at lambda f/# / 8 = 0.3955 um, centred on the
+focus.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--form dense|bluestein]
                   [--impl ours|reference] [--workload NAME] [--rows R]
                   [--plain-rows R] [--e2e-steps E] [--no-plain] [--no-cpu-baseline]
-                  [--ref-rows R] [--instances I]
+                  [--ref-rows R] [--instances I] [--replicas]
 
 Workloads: fzp-d0.05m (small case for profiler captures), fzp-d0.25m,
 fzp-d1m ... fzp-d5m (the D sweep at f/# = 5), fzp-t1 ... fzp-t5 (the phase
@@ -24,12 +25,20 @@ plates of Tables 1-5 on their own grids), membranes (a batch of the seeded
 deformed membranes, autotuned per instance, one CUDA graph per step).
 --rows R times R central aperture rows per step (a sample, named in the
 config); --plain-rows R does the same for the plain FP32 form (its cost per
-row does not depend on the row); --e2e-steps 0 leaves out the end-to-end leg;
---ref-rows sets the oracle's rows per step in the reference arm.
+row does not depend on the row; default: all rows up to D = 0.25 m, 16,384
+central rows above); --e2e-steps 0 leaves out the end-to-end leg; --ref-rows
+sets the oracle's rows per step in the reference arm.
 
-Under torchrun (N > 1) every rank propagates its own copy of the aperture
-(independent problems: weak scaling, no collective on the data path); rank 0
-prints the line with the max time over ranks.
+The cpu_baseline leg also checks parity: the oracle's FP64 field of its timed
+row sample against both GPU forms' fields of the same rows (relative L2 of I,
+tolerance 1e-4), outside the timed region.
+
+Under torchrun (N > 1) the aperture is split into contiguous row ranges of
+about equal open-sample count, one per rank; each rank propagates its range
+and one all_reduce sums the M x M fields (strong scaling: the whole job is
+one aperture).  With --replicas every rank propagates the whole aperture
+instead (independent problems, weak scaling).  Rank 0 prints the line with
+the max time over ranks.
 """
 from __future__ import annotations
 
@@ -69,8 +78,6 @@ WORKLOADS = {
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the dominant kernel, from a one-pass ncu capture of this workload; reported
 # only while the kernel's sources hash to what was captured (null otherwise).
-# Summaries and commands: profiles/dense_splitbf16_fzp-d0.25m_launches.md and
-# profiles/bluestein_fp32_fzp-d0.25m_launches.md.
 KERNEL_SOURCES = {
     "dense": ["dense.cu", "tc_ptx.cuh", "fzp_internal.cuh"],
     "bluestein": ["bluestein.cu", "fzp_internal.cuh"],
@@ -297,6 +304,11 @@ def run_reference(args, wl):
 
 
 def cpu_baseline(wl, budget_s: float = 15.0) -> dict:
+    """The oracle (O3, FP64, all host cores) on a sample of central rows grown
+    until one evaluation takes at least half the budget.  Also returns the
+    sample's rows and intensity (private keys, for the parity check) and the
+    closed forms the full-aperture metrics are read against."""
+    import numpy as np
     import oracle as O
     g = _oracle_geometry(O, wl)
     # grow the sample until one evaluation takes at least half the budget (small
@@ -305,14 +317,40 @@ def cpu_baseline(wl, budget_s: float = 15.0) -> dict:
     while True:
         j0 = g.c - rows // 2
         t0 = time.perf_counter()
-        O.field_czt(g, j0, j0 + rows)
+        U = O.field_czt(g, j0, j0 + rows)
         dt = time.perf_counter() - t0
         if dt >= 0.5 * budget_s or rows >= g.N:
             break
         rows = min(g.N, max(2 * rows, int(rows * budget_s / max(dt, 1e-3))))
     return {"value": rows * g.N / dt / 1e9, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
             "sample": f"{rows} central aperture rows of N = {g.N} (row + column CZT, FP64), {dt:.1f} s",
-            "seconds": dt}
+            "seconds": dt, "_rows": (j0, j0 + rows), "_I": np.abs(U) ** 2,
+            "_airy_fwhm": O.airy_fwhm_factor() * g.lam * g.f / (2 * g.R),
+            "_lobe_de": O.airy_encircled(O.AIRY_NULL) * (O.phase_fzp_efficiency(g.levels) if g.levels
+                                                         else O.binary_fzp_efficiency())}
+
+
+def _rel_l2(a, b):
+    import numpy as np
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+def _rows_intensity(fzp, torch, plan, M, j0, j1, stream, dev):
+    U = torch.empty((M, M), dtype=torch.complex128, device=dev)
+    plan.propagate_roi(j0, j1, U, stream=stream)
+    I = torch.empty((M, M), dtype=torch.float64, device=dev)
+    plan.intensity(U, I, stream=stream)
+    torch.cuda.synchronize(dev)
+    return I.cpu().numpy()
+
+
+def disc_samples(N: int, c: int, s_R: int, j0: int, j1: int) -> int:
+    """Aperture samples inside the disc on rows [j0, j1): per row the chord
+    2 floor(sqrt(s_R - dj^2)) + 1 (integer arithmetic; dj = j - c)."""
+    import math
+    b = math.isqrt(s_R)
+    lo, hi = max(j0, c - b), min(j1, c + b + 1)
+    return sum(2 * math.isqrt(s_R - (j - c) ** 2) + 1 for j in range(lo, hi))
 
 
 def main():
@@ -321,13 +359,16 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fzp-d0.25m", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="fzp-d1m", choices=sorted(WORKLOADS))
     ap.add_argument("--form", default="dense", choices=["dense", "bluestein"])
     ap.add_argument("--ref-rows", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 Bluestein form")
-    ap.add_argument("--plain-rows", type=int, default=0, help="rows of the plain form's timed sample (0: all)")
+    ap.add_argument("--plain-rows", type=int, default=-1,
+                    help="rows of the plain form's timed sample (0: all; -1: all up to N = 316,057, else 16,384)")
+    ap.add_argument("--replicas", action="store_true",
+                    help="N > 1: every rank propagates the whole aperture (weak scaling) instead of its rows")
     ap.add_argument("--instances", type=int, default=16, help="membranes workload: instances per batch")
     ap.add_argument("--rows", type=int, default=0,
                     help="time only this many central aperture rows per step (a sample; 0: all N)")
@@ -374,15 +415,24 @@ def main():
     plan = fzp.Plan(**params)
     info = plan.info
     N = info["N"]
-    rows = N if args.rows <= 0 else min(N, args.rows)  # timed rows per step
+    rows = N if args.rows <= 0 else min(N, args.rows)  # timed rows per step (all ranks together)
     r0 = (N - rows) // 2
+    sharded = ws > 1 and not args.replicas
+    j0, j1 = r0, r0 + rows  # this rank's rows
+    if sharded:
+        from paper_2609_01978_gb300 import shard
+        w = shard.chord_weights(N, info["c"], info["s_R"])[r0:r0 + rows]
+        a, b = shard.row_ranges(rows, ws, w)[rank]
+        j0, j1 = r0 + a, r0 + b
     stream = torch.cuda.current_stream(dev)
     U = torch.empty((M, M), dtype=torch.complex128, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MiB > L2 (129 MB)
 
     def step():
         flush.fill_(1.0)  # evict L2 between steps
-        plan.propagate_roi(r0, r0 + rows, U, stream=stream)
+        plan.propagate_roi(j0, j1, U, stream=stream)
+        if sharded:
+            pg.all_reduce(U)  # the one exchange: sum of the ranks' partial fields
         return plan.metrics(U, stream=stream)
 
     for _ in range(args.warmup):
@@ -413,21 +463,26 @@ def main():
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         ms = float(t.item())
-    value = ws * args.steps * rows * N / (ms / 1e3) / 1e9
+    value = (1 if sharded else ws) * args.steps * rows * N / (ms / 1e3) / 1e9
 
     # roofline of the dominant kernel, from CUDA events on its own stream
     peaks, peak_kind = _peaks()
     avg_ms = prof["dominant_ms"] / max(1, prof["dominant_launches"])
     if args.form == "dense":
         # algorithmic work of the contraction: 2 real rows (Re, Im) x M outputs x
-        # 2 flops x 2 split terms per aperture sample = 8 M flops per sample and
-        # mask pass (a phase plate with L >= 4 takes L/2 passes)
+        # 2 flops x 2 split terms per aperture sample inside the disc = 8 M
+        # flops per such sample and mask pass (a phase plate with L >= 4 takes
+        # L/2 passes); samples outside the disc carry no work and are skipped
         launches = max(1, prof["dominant_launches"])
-        flops_launch = 8.0 * M * rows * N * info["passes"] * args.steps / launches
+        inside = disc_samples(N, info["c"], info["s_R"], j0, j1)
+        flops_launch = 8.0 * M * inside * info["passes"] * args.steps / launches
         achieved = flops_launch / (avg_ms / 1e3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": _traffic(args.workload, "dense"), "kernel": prof["dominant_name"], "peak_source": peak_kind + " bf16 sustained"}
+                "traffic": _traffic(args.workload, "dense"), "kernel": prof["dominant_name"],
+                "peak_source": peak_kind + " bf16 sustained",
+                "work": "8 M flops per aperture sample inside the disc and mask pass",
+                "disc_samples_per_launch": inside * args.steps / launches}
     else:
         launches = max(1, prof["dominant_launches"])
         rows_per_launch = rows * args.steps / launches
@@ -452,7 +507,9 @@ def main():
         for _ in range(args.e2e_steps):
             with fzp.Plan(**params) as p2:
                 h2d = 8 * p2.info["n_thresholds"]  # the zone-threshold table, the plan's one upload
-                p2.propagate_roi(r0, r0 + rows, U, stream=stream)
+                p2.propagate_roi(j0, j1, U, stream=stream)
+                if sharded:
+                    pg.all_reduce(U)
                 host.copy_(U, non_blocking=True)
                 p2.metrics(U, stream=stream)
                 torch.cuda.synchronize(dev)
@@ -463,16 +520,33 @@ def main():
             e2e_s = float(t.item())
         # read back: the complex128 field, the metric extractor's 1024-double
         # result block and its 4-byte error word
-        e2e = {"value": ws * rows * N / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": (1 if sharded else ws) * rows * N / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": M * M * 16 + 8 * 1024 + 4,
                "note": "fzp_plan + fzp_propagate_roi + field to pinned host + fzp_metrics + fzp_plan_destroy"}
+
+    # the oracle on the host cores (cpu_baseline), and parity: the oracle's
+    # FP64 field of its timed rows against this form's field of the same rows
+    cb, parity = None, None
+    if ws == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(wl)
+        pa, pb_ = cb.pop("_rows")
+        Iref = cb.pop("_I")
+        parity = {"rows": [pa, pb_], "oracle": "O3 (Bluestein CZT rows then columns, FP64) on the cpu_baseline sample",
+                  "tolerance": 1e-4,
+                  f"rel_l2_I_{args.form}": _rel_l2(_rows_intensity(fzp, torch, plan, M, pa, pb_, stream, dev), Iref)}
+        airy, lobe = cb.pop("_airy_fwhm"), cb.pop("_lobe_de")
+        if rows == N:
+            parity["full_aperture_vs_closed_forms"] = {
+                "fwhm_x_over_airy_minus_1": m["fwhm_x"] / airy - 1,
+                "de_lobe_over_ee_efficiency_minus_1": m["de_lobe"] / lobe - 1}
     plan.close()
 
     # the plain FP32 Bluestein form on the same workload (the metric compares
     # the split-BF16 dense form with it): one warm and one timed step
     plain = None
     if args.form == "dense" and not args.no_plain:
-        rows = N if args.plain_rows <= 0 else min(N, args.plain_rows)
+        prow = args.plain_rows if args.plain_rows >= 0 else (0 if N <= 316057 else 16384)
+        rows = N if prow <= 0 else min(N, prow)
         r0 = (N - rows) // 2
         with fzp.Plan(**dict(params, form=fzp.FORM_BLUESTEIN, precision=fzp.PREC_FP32)) as pb:
             pb.propagate_roi(r0, r0 + rows, U, stream=stream)
@@ -484,6 +558,10 @@ def main():
             e1.record(stream)
             torch.cuda.synchronize(dev)
             pms = e0.elapsed_time(e1)
+            if parity is not None:
+                pa, pb_ = parity["rows"]
+                parity["rel_l2_I_bluestein_fp32"] = _rel_l2(
+                    _rows_intensity(fzp, torch, pb, M, pa, pb_, stream, dev), Iref)
         plain = {"form": "bluestein", "dtype": "f32", "value": rows * N / (pms / 1e3) / 1e9, "unit": UNIT,
                  "ms_per_step": pms, "rows": rows}
         if rows == N:
@@ -494,16 +572,20 @@ def main():
             pg.destroy_process_group()
         return
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "strong" if sharded else "weak",
            "vs_baseline": None, "dtype": dtype, "data": "synthetic (procedural binary zone plate)",
            "config": _config(args, wl, N),
            "roofline": roof, "e2e": e2e, "gpu_launches": prof["kernel_launches"], "clocks": clocks,
            "metrics_last_step": {k: m[k] for k in ("fwhm_x", "de_lobe", "mtf_half_cut")}}
+    if sharded:
+        out["config"]["parallelism"] = f"rows split over {ws} ranks by open-sample count, one all_reduce per step"
     if plain:
         out["plain_fp32"] = plain
         out["speedup_vs_plain_fp32"] = value / plain["value"]
-    if ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(wl)
+    if cb is not None:
+        out["cpu_baseline"] = cb
+        out["parity"] = parity
     _print(out)
     if pg:
         pg.destroy_process_group()

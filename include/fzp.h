@@ -11,7 +11,8 @@
  *                   * e^{-2 pi i (x_m u_i + y_n v_j)/(lambda f)},           I = |U|^2
  *
  * with the aperture grid u_i = (i - c) dx, c = (N-1)/2 (N odd, Fig. 2 Stage 1),
- * the ROI grid x_m = (m - M/2) p (sample M/2 on the axis), T the binary FZP
+ * the ROI grid x_m = (m - M/2) p (sample M/2 on the axis; or x_m = x0 + m p,
+ * y_n = y0 + n p for an off-axis ROI, see fzp_params.roi_origin), T the binary FZP
  * mask (open where floor(r^2/(lambda f)) is odd and r <= R_eff, Fig. 2 Stage 2,
  * paraxial radii of Eq. 4, centre zone opaque) and phi an optional membrane
  * deformation phase (4 pi / lambda) w(u, v).  With fzp_params.levels = L >= 2
@@ -132,6 +133,17 @@ typedef struct fzp_params {
                           positive-centred, even zones open.  Must be 0 for a
                           phase plate (levels >= 2), where it would only shift
                           every level by one phase; other values are invalid */
+  int32_t roi_origin;  /* 0: ROI centred on the focus, x_m = (m - M/2) p and
+                          y_n = (n - M/2) p.  1: the first ROI sample is at
+                          (x0, y0): x_m = x0 + m p, y_n = y0 + n p (Eq. 10's A
+                          from the first ROI coordinate, Sec. 2.6).  Both forms
+                          use one kernel matrix for the two axes, so x0 must
+                          equal y0 (FZP_E_UNSUPPORTED otherwise); fzp_metrics
+                          reads the focus at the ROI centre and rejects an
+                          off-axis plan with FZP_E_UNSUPPORTED.  Other values
+                          are invalid                                          */
+  int32_t reserved;    /* must be 0                                            */
+  double x0, y0;       /* first ROI coordinates [m] when roi_origin = 1 (finite) */
 } fzp_params;
 
 /* Opaque plan: geometry, zone-threshold table, chirp / kernel tables and the
@@ -148,7 +160,7 @@ typedef struct fzp_plan_info {
   double dx;             /* aperture pitch [m]                                     */
   double R;              /* aperture radius R_eff = min(D/2, lambda f/(2 dx)) [m]  */
   double kappa;          /* dx^2 / (lambda f): zone index = floor(s kappa)         */
-  double x0;             /* first ROI coordinate [m]                               */
+  double x0;             /* first ROI coordinate [m] (both axes)                   */
   int32_t M;             /* ROI samples per side                                   */
   int32_t form;          /* resolved fzp_form                                      */
   int32_t precision;     /* fzp_precision                                          */
@@ -167,6 +179,9 @@ typedef struct fzp_plan_info {
   int32_t passes;        /* dense form: signed-mask passes per row chunk (1, or L/2
                             for a phase plate with L >= 4)                         */
   int32_t centre_open;   /* 1: positive-centred binary plate (even zones open)     */
+  int32_t reserved;
+  int64_t s_R;           /* largest squared distance from the axis, in samples, of a
+                            sample inside the aperture disc (fl(s_R dx^2) <= fl(R^2)) */
 } fzp_plan_info;
 
 /* Metrics of Fig. 2 Stage 4 / Fig. 18 Stage 5. */
@@ -249,6 +264,30 @@ FZP_API fzp_status fzp_intensity(fzp_plan_t plan, const void* d_field, void* d_i
  * Also reports any device-side timeout recorded by earlier calls on this plan
  * (FZP_E_TIMEOUT). */
 FZP_API fzp_status fzp_metrics(fzp_plan_t plan, const void* d_field, void* stream, fzp_metrics_t* out);
+
+/* Run outputs of the simulation engine (Fig. 18, RETURN: result, text report
+ * and JSON sidecar in a run folder, read against the analytic references).
+ * Runs fzp_metrics on d_field (a full ROI field of this plan), then writes
+ *   <run_dir>/result_<tag>.npy   I = |U|^2, M x M float64, NumPy .npy 1.0
+ *   <run_dir>/report_<tag>.txt   problem, grids, metrics, references, timing
+ *   <run_dir>/result_<tag>.json  the same as one JSON object
+ * References: FWHM against the Airy value 1.0289939 lambda f / (2 R_eff) and
+ * the outermost zone width lambda f / (2 R_eff); main-lobe DE against
+ * EE(r_null) eta with EE(r_null) = 0.8377850 and eta = 1/pi^2 (binary
+ * amplitude) or sinc^2(1/L) (L-level phase, the level ladder); MTF at
+ * nu_cut/2 against the clear pupil's 0.3910022.
+ *   d_field       device complex128 M*M (input).
+ *   t_propagate_s the caller's propagation time [s], reported with the
+ *                 throughput N^2 / t (0: not timed).
+ *   run_dir       existing directory (host string); tag: letters, digits,
+ *                 '-', '_', '.' only.  Existing files of the same tag are
+ *                 overwritten.
+ *   stream        cudaStream_t; the call synchronises it.
+ *   out           optional (NULL): receives the metrics.
+ * Errors: FZP_E_INVALID (NULL, bad tag, a file that cannot be written),
+ * FZP_E_UNSUPPORTED (off-axis ROI, as fzp_metrics), FZP_E_CUDA, FZP_E_TIMEOUT. */
+FZP_API fzp_status fzp_report_write(fzp_plan_t plan, const void* d_field, double t_propagate_s, const char* run_dir,
+                                    const char* tag, void* stream, fzp_metrics_t* out);
 
 /* ---- Batches: many apertures in one CUDA graph ----------------------------
  *

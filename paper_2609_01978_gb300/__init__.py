@@ -47,7 +47,8 @@ class Params(ctypes.Structure):
                 ("form", ctypes.c_int32), ("pitch", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("stripe_rows", ctypes.c_int32), ("deform", ctypes.POINTER(Deform)),
                 ("promote", ctypes.c_int32), ("row_batch", ctypes.c_int32), ("cluster", ctypes.c_int32),
-                ("levels", ctypes.c_int32), ("centre_open", ctypes.c_int32)]
+                ("levels", ctypes.c_int32), ("centre_open", ctypes.c_int32), ("roi_origin", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("x0", ctypes.c_double), ("y0", ctypes.c_double)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -58,7 +59,8 @@ class PlanInfo(ctypes.Structure):
                 ("fft_length", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
                 ("promote", ctypes.c_int32), ("row_batch", ctypes.c_int32), ("chunk_rows", ctypes.c_int64),
                 ("cluster", ctypes.c_int32), ("fft_inner", ctypes.c_int32), ("ctas", ctypes.c_int32),
-                ("levels", ctypes.c_int32), ("passes", ctypes.c_int32), ("centre_open", ctypes.c_int32)]
+                ("levels", ctypes.c_int32), ("passes", ctypes.c_int32), ("centre_open", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("s_R", ctypes.c_int64)]
 
 
 class Metrics(ctypes.Structure):
@@ -116,6 +118,8 @@ def lib() -> ctypes.CDLL:
             "fzp_surrogate_train_step": [vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, vp, vp],
             "fzp_surrogate_destroy": [vp],
             "fzp_profile_read": [vp, ctypes.POINTER(Profile)],
+            "fzp_report_write": [vp, vp, ctypes.c_double, ctypes.c_char_p, ctypes.c_char_p, vp,
+                                 ctypes.POINTER(Metrics)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -153,6 +157,11 @@ def _stream(s) -> Optional[int]:
     return s.cuda_stream
 
 
+def _origin(x0):
+    """(roi_origin, x0, y0) of fzp_params: None keeps the ROI centred on the focus."""
+    return (0, 0.0, 0.0) if x0 is None else (1, float(x0), float(x0))
+
+
 def make_deform(amp=0.0, period=1e-2, theta=0.0, taper=0.0, ridges=()) -> Deform:
     d = Deform()
     d.amp, d.period, d.theta, d.taper = amp, period, theta, taper
@@ -168,12 +177,14 @@ class Plan:
     def __init__(self, D: float, f: float, lam: float, M: int, pitch: float, dx: float = 0.0, N: int = 0,
                  form: int = FORM_AUTO, precision: int = PREC_FP32, stripe_rows: int = 0,
                  deform: Optional[Deform] = None, promote: int = 0, row_batch: int = 0, cluster: int = 0,
-                 levels: int = 0, centre_open: int = 0):
+                 levels: int = 0, centre_open: int = 0, x0: Optional[float] = None):
+        """x0: first ROI coordinate on both axes (None: the ROI centred on the focus)."""
         self._deform = deform
+        org, ox, oy = _origin(x0)
         p = Params(D=D, f=f, lam=lam, dx=dx, N=N, M=M, form=form, pitch=pitch, precision=precision,
                    stripe_rows=stripe_rows, deform=ctypes.pointer(deform) if deform is not None else None,
                    promote=promote, row_batch=row_batch, cluster=cluster, levels=levels,
-                   centre_open=centre_open)
+                   centre_open=centre_open, roi_origin=org, x0=ox, y0=oy)
         h = ctypes.c_void_p()
         _check(lib().fzp_plan(ctypes.byref(p), ctypes.byref(h)))
         self._h = h
@@ -194,6 +205,14 @@ class Plan:
     def metrics(self, field, stream=None) -> dict:
         m = Metrics()
         _check(lib().fzp_metrics(self._h, _ptr(field), _stream(stream), ctypes.byref(m)))
+        return m.as_dict()
+
+    def report(self, field, run_dir: str, tag: str, t_propagate_s: float = 0.0, stream=None) -> dict:
+        """fzp_report_write: metrics of `field`, then result_<tag>.npy (I),
+        report_<tag>.txt and result_<tag>.json in `run_dir` (Fig. 18 run outputs)."""
+        m = Metrics()
+        _check(lib().fzp_report_write(self._h, _ptr(field), float(t_propagate_s), run_dir.encode(), tag.encode(),
+                                      _stream(stream), ctypes.byref(m)))
         return m.as_dict()
 
     def aperture_mask(self, row_begin: int, row_end: int, out, stream=None):
@@ -238,12 +257,14 @@ class Batch:
         for k, pr in enumerate(problems):
             d = pr.get("deform")
             self._keep.append(d)
+            org, ox, oy = _origin(pr.get("x0"))
             arr[k] = Params(D=pr["D"], f=pr["f"], lam=pr["lam"], dx=pr.get("dx", 0.0), N=pr.get("N", 0), M=pr["M"],
                             form=pr.get("form", FORM_AUTO), pitch=pr["pitch"],
                             precision=pr.get("precision", PREC_AUTO_1E4), stripe_rows=pr.get("stripe_rows", 0),
                             deform=ctypes.pointer(d) if d is not None else None, promote=pr.get("promote", 0),
                             row_batch=pr.get("row_batch", 0), cluster=pr.get("cluster", 0),
-                            levels=pr.get("levels", 0), centre_open=pr.get("centre_open", 0))
+                            levels=pr.get("levels", 0), centre_open=pr.get("centre_open", 0),
+                            roi_origin=org, x0=ox, y0=oy)
         h = ctypes.c_void_p()
         _check(lib().fzp_batch_plan(arr, n, ctypes.byref(h)))
         self._h = h
@@ -326,10 +347,11 @@ class SurrogateNet:
 
 
 def _params(D, f, lam, M, pitch, dx=0.0, N=0, form=FORM_AUTO, precision=PREC_FP32, stripe_rows=0, promote=0,
-            row_batch=0, cluster=0, levels=0, centre_open=0) -> Params:
+            row_batch=0, cluster=0, levels=0, centre_open=0, x0=None) -> Params:
+    org, ox, oy = _origin(x0)
     return Params(D=D, f=f, lam=lam, dx=dx, N=N, M=M, form=form, pitch=pitch, precision=precision,
                   stripe_rows=stripe_rows, deform=None, promote=promote, row_batch=row_batch, cluster=cluster,
-                  levels=levels, centre_open=centre_open)
+                  levels=levels, centre_open=centre_open, roi_origin=org, x0=ox, y0=oy)
 
 
 def plan_query(**kw) -> dict:
@@ -358,7 +380,21 @@ def metrics_noalloc(field, D: float, f: float, lam: float, M: int, pitch: float,
     """fzp_metrics_noalloc: the metric extractor without a plan and without any
     device allocation (scratch in a static device array; M <= 512).  `levels`
     enters through the default dx (Fig. 18 Stage 1); the aperture count does
-    not depend on the plate's levels or centre configuration."""
+    not depend on the plate's levels or centre configuration.
+
+    `field` is a torch tensor (complex128, contiguous, M*M elements, on the
+    current CUDA device) or a raw device address (int) that the caller vouches
+    for; a tensor that does not fit the call is refused here, before the
+    kernels read M*M samples from it."""
+    if not isinstance(field, int):
+        import torch
+        if not (field.is_cuda and field.dtype == torch.complex128 and field.is_contiguous()
+                and field.numel() == M * M):
+            raise ValueError("metrics_noalloc: field must be a contiguous complex128 CUDA tensor of M*M "
+                             f"= {M * M} elements (got {tuple(field.shape)} {field.dtype} on {field.device})")
+        if field.device.index != torch.cuda.current_device():
+            raise ValueError(f"metrics_noalloc: field is on {field.device}, the current device is "
+                             f"cuda:{torch.cuda.current_device()}")
     p = Params(D=D, f=f, lam=lam, dx=dx, N=N, M=M, form=0, pitch=pitch, precision=0, stripe_rows=0, deform=None,
                levels=levels, centre_open=centre_open)
     m = Metrics()

@@ -4,11 +4,12 @@
 //
 // For aperture row j the row transform is
 //   C[j, m] = sum_i x_i K[m, i],  x_i = T[j, i] e^{i phi[j, i]},
-//   K[m, i] = exp(2 pi i theta(m, i)),  theta = di^2 kappa/2 - (m - M/2) di delta.
+//   K[m, i] = exp(2 pi i theta(m, i)),  theta = di^2 kappa/2 - (m - msh) di delta
+// (msh = -x0/p: M/2 for the ROI centred on the focus).
 // With m i = (m^2 + i^2 - (m - i)^2) / 2 (Bluestein):
 //   theta(m, i) = pre(i) + post(m) + delta (m - i)^2 / 2,
-//   pre(i)  = di^2 kappa/2 - delta i^2/2 + delta (M/2) i,
-//   post(m) = -delta m^2/2 + delta m c - delta (M/2) c,
+//   pre(i)  = di^2 kappa/2 - delta i^2/2 + delta msh i,
+//   post(m) = -delta m^2/2 + delta m c - delta msh c,
 // so C[j, .] = e^{2 pi i post} .* (y * h)[0..M) with y_i = x_i e^{2 pi i pre(i)} and
 // the chirp h_k = e^{i pi delta k^2}, k in (-N, M): one linear convolution of
 // length >= N + M - 1, done as FFT_L, pointwise product with FFT_L(h), IFFT_L.
@@ -508,19 +509,20 @@ __global__ void __launch_bounds__(256) k_f3(RowArgs a) {
 
 // Tables: pre(i), post(m)/L, convolution chirp v (length L), twiddles.
 template <typename R>
-__global__ void k_tables(int64_t N, int M, int64_t L, int64_t c, double kappa, double delta, void* pre, void* post,
+__global__ void k_tables(int64_t N, int M, double msh, int64_t L, int64_t c, double kappa, double delta, void* pre,
+                         void* post,
                          void* v, void* tw, int twN, void* twL) {
   using C = typename Cplx<R>::T;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < L; t += stride) {
     if (t < N) {
       const double di = (double)(t - c), ti = (double)t;
-      const double ph = di * di * (0.5 * kappa) - (0.5 * delta) * (ti * ti) + delta * (double)(M / 2) * ti;
+      const double ph = di * di * (0.5 * kappa) - (0.5 * delta) * (ti * ti) + delta * msh * ti;
       reinterpret_cast<C*>(pre)[t] = cis_turns<R>(ph);
     }
     if (t < M) {
       const double tm = (double)t;
-      const double ph = -(0.5 * delta) * tm * tm + delta * tm * (double)c - delta * (double)(M / 2) * (double)c;
+      const double ph = -(0.5 * delta) * tm * tm + delta * tm * (double)c - delta * msh * (double)c;
       C z = cis_turns<R>(ph);
       z.x /= (R)L; z.y /= (R)L;
       reinterpret_cast<C*>(post)[t] = z;
@@ -631,7 +633,7 @@ fzp_status fill_tables_t(Plan& P, cudaStream_t s) {
   b.d_tw = reinterpret_cast<C*>(b.d_tab) + b.L;
   b.d_post = reinterpret_cast<C*>(b.d_tw) + twN;
   b.d_twL = reinterpret_cast<C*>(b.d_post) + P.M;
-  k_tables<R><<<1024, 256, 0, s>>>(P.N, P.M, b.L, P.c, P.kappa, P.delta, b.d_pre, b.d_post, b.d_tab, b.d_tw, twN,
+  k_tables<R><<<1024, 256, 0, s>>>(P.N, P.M, P.msh, b.L, P.c, P.kappa, P.delta, b.d_pre, b.d_post, b.d_tab, b.d_tw, twN,
                                    b.d_twL);
   FZP_CUDA_TRY(cudaGetLastError());
   // H = FFT_L(v) in the [k1][k2] order: F1 (table mode) + F2 (forward only) into Z row 0, then copy.

@@ -6,7 +6,7 @@
 //   U[n, m]     = Pre e^{i pi (x_m^2 + y_n^2)/(lambda f)} Uacc[n, m],
 //   Pre         = e^{i k f} dx^2 / (i lambda f)              (Eq. 2)
 //
-// K[n, j] = exp(2 pi i (A_j - n B_j)) with A_j = dj^2 kappa/2 + (M/2) dj delta and
+// K[n, j] = exp(2 pi i (A_j - n B_j)) with A_j = dj^2 kappa/2 + msh dj delta and
 // B_j = dj delta (turns, dj = j - c).  A_j and B_j are reduced in FP64 once per
 // row j; for the FP32 path B_j is split as hi + lo with hi a multiple of 2^-14
 // so that n * hi is exact in FP32 for n < 1024.
@@ -23,6 +23,7 @@ struct ColArgs {
   int64_t c, j0, rows, c1_stride;
   int M;
   double kappa, delta;
+  double msh;     // ROI shift in pitches: y_n = (n - msh) p
   double wr, wi;  // weight of this pass's field (1, 0 for a single-pass plate)
 };
 
@@ -32,7 +33,7 @@ template <> struct RowPhase<double> { double a, b; };
 
 __device__ __forceinline__ void row_phase(const ColArgs& g, int64_t j, RowPhase<float>& rp) {
   const double dj = (double)(j - g.c);
-  const double A = dj * dj * (0.5 * g.kappa) + (double)(g.M / 2) * dj * g.delta;
+  const double A = dj * dj * (0.5 * g.kappa) + g.msh * dj * g.delta;
   const double fb = frac_turns(dj * g.delta);
   const double hi = rint(fb * 16384.0) / 16384.0;
   rp.fa = (float)frac_turns(A);
@@ -41,7 +42,7 @@ __device__ __forceinline__ void row_phase(const ColArgs& g, int64_t j, RowPhase<
 }
 __device__ __forceinline__ void row_phase(const ColArgs& g, int64_t j, RowPhase<double>& rp) {
   const double dj = (double)(j - g.c);
-  rp.a = frac_turns(dj * dj * (0.5 * g.kappa) + (double)(g.M / 2) * dj * g.delta);
+  rp.a = frac_turns(dj * dj * (0.5 * g.kappa) + g.msh * dj * g.delta);
   rp.b = frac_turns(dj * g.delta);
 }
 
@@ -128,12 +129,12 @@ __global__ void __launch_bounds__(256) k_colpass(ColArgs g, const R* __restrict_
     }
 }
 
-__global__ void k_epilogue(int M, double p, double lf, double f_over_lambda, double amp, const double2* __restrict__ Uacc,
-                           double2* __restrict__ out, int accumulate) {
+__global__ void k_epilogue(int M, double msh, double p, double lf, double f_over_lambda, double amp,
+                           const double2* __restrict__ Uacc, double2* __restrict__ out, int accumulate) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= M * M) return;
   const int n = t / M, m = t % M;
-  const double xm = (double)(m - M / 2), yn = (double)(n - M / 2);
+  const double xm = (double)m - msh, yn = (double)n - msh;
   // e^{ikf} (1/i) e^{i pi (x^2 + y^2)/(lambda f)}: turns f/lambda - 1/4 + (x^2 + y^2)/(2 lambda f)
   const double ph = frac_turns(f_over_lambda) - 0.25 + (xm * xm + yn * yn) * (p * p) / (2.0 * lf);
   double2 w = cis_turns_d(ph);
@@ -156,7 +157,7 @@ __global__ void k_intensity(int64_t count, const double2* __restrict__ U, double
 }  // namespace
 
 fzp_status column_pass(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
-  ColArgs g{P.c, j0, rows, P.chunk_rows, P.M, P.kappa, P.delta, 1.0, 0.0};
+  ColArgs g{P.c, j0, rows, P.chunk_rows, P.M, P.kappa, P.delta, P.msh, 1.0, 0.0};
   if (P.pass_index >= 0) {
     g.wr = P.passes[P.pass_index].wr;
     g.wi = P.passes[P.pass_index].wi;
@@ -172,7 +173,7 @@ fzp_status column_pass(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
 fzp_status epilogue(Plan& P, void* d_field, int accumulate, cudaStream_t s) {
   const double lf = P.lambda * P.f;
   const int count = P.M * P.M;
-  k_epilogue<<<(count + 255) / 256, 256, 0, s>>>(P.M, P.p, lf, P.f / P.lambda, P.dx2 / lf, P.d_Uacc,
+  k_epilogue<<<(count + 255) / 256, 256, 0, s>>>(P.M, P.msh, P.p, lf, P.f / P.lambda, P.dx2 / lf, P.d_Uacc,
                                                  reinterpret_cast<double2*>(d_field), accumulate);
   P.launches += 1;
   FZP_CUDA_TRY(cudaGetLastError());

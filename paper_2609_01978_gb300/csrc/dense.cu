@@ -2,7 +2,8 @@
 //
 // The kernel of Eq. 2 is separable (Sec. 2.6), so the focal-plane field is
 //   U = Pre chirp_out .* (K T K^T),   K[m, i] = exp(2 pi i theta(m, i)),
-//   theta(m, i) = di^2 kappa/2 - (m - M/2) di delta   (turns),
+//   theta(m, i) = di^2 kappa/2 - (m - msh) di delta   (turns; msh = M/2 for the
+//   ROI centred on the focus, -x0/p otherwise),
 // and the row pass C1 = K T^T is a real GEMM with
 //   A = [Re K; Im K] (2M x N, split as K = K_hi + K_lo, both BF16),
 //   B = T (aperture rows x N, binary: exact in BF16),
@@ -369,6 +370,28 @@ __device__ __forceinline__ uint32_t disc_bits(const Walker& w, int64_t i0) {
   return a & b;
 }
 
+// K blocks [klo, khi) of stripe s that meet the aperture disc: every row's
+// chord lies inside the chord of the stripe's row nearest the axis, so blocks
+// outside that chord multiply zero mask columns only and are skipped.  At
+// least one block (a stripe with no row on the disc still writes its zero
+// rows of C1).  Every role of the kernel derives the same range.
+__device__ __forceinline__ void stripe_kspan(const DenseArgs& a, int64_t s, int64_t& klo, int64_t& khi) {
+  const int64_t jb = a.j_begin + s * BN;
+  const int64_t je = jb + BN < a.j_end ? jb + BN : a.j_end;
+  const int64_t c = a.mg.c;
+  const int64_t jn = c < jb ? jb : (c >= je ? je - 1 : c);
+  const int64_t t = a.mg.sR - (jn - c) * (jn - c);
+  if (t < 0) {
+    klo = c / BK < a.kblocks ? c / BK : a.kblocks - 1;
+    khi = klo + 1;
+    return;
+  }
+  const int64_t b = isqrt_floor(t);
+  klo = c - b > 0 ? (c - b) / BK : 0;
+  khi = (c + b) / BK + 1 < a.kblocks ? (c + b) / BK + 1 : a.kblocks;
+  if (khi <= klo) khi = klo + 1;
+}
+
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
   uint32_t d;
   asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
@@ -462,7 +485,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
   const int64_t n_items = a.n_stripes * (a.npairs / CL);  // units of this cluster
   const int64_t u0 = blockIdx.x / CL, ustep = gridDim.x / CL;
   const int64_t nkb = a.kblocks;
-  const int64_t nchunk = (nkb + a.promote - 1) / a.promote;
   const uint32_t a_bytes = a.hi_only ? A_BYTES / 2 : A_BYTES;
 
   if (warp == LOAD_WARP) {
@@ -476,7 +498,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
       for (int64_t it = u0; it < n_items && !*abort_flag; it += ustep) {
         const int64_t pr = (it / a.n_stripes) * CL + rk;
         const uint8_t* Ap = a.A + pr * nkb * A_BYTES;
-        for (int64_t kb = 0; kb < nkb; ++kb) {
+        int64_t klo, khi;
+        stripe_kspan(a, it % a.n_stripes, klo, khi);
+        for (int64_t kb = klo; kb < khi; ++kb) {
           if (!(CL > 1 ? mbar_wait_cl(&empty[stage], phase ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 1)
                        : mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 1)))
             break;
@@ -504,11 +528,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
       uint32_t phase = 0, accph = 0;
       bool ok = true;
       for (int64_t it = u0; it < n_items && ok; it += ustep) {
-        for (int64_t ch = 0; ch < nchunk && ok; ++ch) {
+        int64_t klo, khi;
+        stripe_kspan(a, it % a.n_stripes, klo, khi);
+        const int64_t nch = (khi - klo + a.promote - 1) / a.promote;
+        for (int64_t ch = 0; ch < nch && ok; ++ch) {
           // the epilogue has drained both accumulators of the previous chunk
           if (!mbar_wait(accEmpty, accph ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 2)) { ok = false; break; }
           tc_fence_after();
-          const int64_t kb0 = ch * a.promote, kb1 = kb0 + a.promote < nkb ? kb0 + a.promote : nkb;
+          const int64_t kb0 = klo + ch * a.promote, kb1 = kb0 + a.promote < khi ? kb0 + a.promote : khi;
           for (int64_t kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait(&fullA[stage], phase, abort_flag, a.err, ERR_TIMEOUT_BASE + 3) ||
                 !(CL > 1 ? mbar_wait_cl(&fullB[stage], phase, abort_flag, a.err, ERR_TIMEOUT_BASE + 4)
@@ -558,22 +585,34 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
     const int sw = (row & 7) >> 1;
     const bool leader = wr == 0 && lane == 0;
     const int64_t my_units = u0 < n_items ? (n_items - u0 + ustep - 1) / ustep : 0;
-    const int64_t nblk = my_units * nkb;  // the CTA's global K blocks, in MMA order
     int last[STAGES];  // leader: phase of the last peer copy expected on each stage
 #pragma unroll
     for (int s2 = 0; s2 < STAGES; ++s2) last[s2] = -1;
     Walker w;
     uint32_t state = 0;  // CL = 1: open state of the sequential walk
     int64_t cur_unit = -1;
-    int64_t ui = 0, kb = ph;  // G = ui * nkb + kb, advanced without division
-    while (kb >= nkb && nkb > 0) { kb -= nkb; ++ui; }
+    // The CTA's K blocks in MMA order: unit ui (its stripe's span [klo, klo +
+    // nlen)), block offset t within it; block G of the sequence (G = ph, ph +
+    // CL, ...) sits on stage G % STAGES like the loader's and the issuer's.
+    int64_t ui = 0, t = ph, klo = 0, nlen = 1;
+    auto unit_span = [&](int64_t u) {
+      int64_t hi;
+      stripe_kspan(a, (u0 + u * ustep) % a.n_stripes, klo, hi);
+      nlen = hi - klo;
+    };
+    if (my_units > 0) unit_span(0);
+    while (ui < my_units && t >= nlen) {
+      t -= nlen;
+      if (++ui < my_units) unit_span(ui);
+    }
     // block-wise generation (clusters, and every phase-plate pass): the next
     // own block's events and thresholds are prepared (its load issued) before
     // the current block is finished
     const bool prefetch = CL > 1 || a.level_mode;
     BlockPrep pre{}, cur{};
     bool have_pre = false;
-    for (int64_t G = ph; G < nblk; G += CL) {
+    for (int64_t G = ph; ui < my_units; G += CL) {
+      const int64_t kb = klo + t;
       const int stage = (int)(G & (STAGES - 1));
       const uint32_t phase = (uint32_t)((G / STAGES) & 1);
       if (ui != cur_unit) {
@@ -586,7 +625,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
       if (prefetch) {
         if (!have_pre) block_prep(w, kb * BK, a.mg, pre);
         cur = pre;
-        have_pre = kb + CL < nkb;
+        have_pre = t + CL < nlen;
         if (have_pre) block_prep(w, (kb + CL) * BK, a.mg, pre);
       }
       // One thread per phase waits for the stage; the phase's warps take its
@@ -636,8 +675,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
         }
         if (lane == 0) mbar_arrive(&fullB[stage]);
       }
-      kb += CL;
-      while (kb >= nkb) { kb -= nkb; ++ui; }
+      t += CL;
+      while (ui < my_units && t >= nlen) {
+        t -= nlen;
+        if (++ui < my_units) unit_span(ui);
+      }
     }
     if constexpr (CL > 1) {
       if (leader && *abort_flag) {
@@ -667,7 +709,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
       const bool live = (pr * TILES + q) * 64 < (int64_t)a.M;
       const int x0 = (int)(a.j_begin + s * BN - a.c1_j0);       // C1 column of the stripe's first row
       const int y0 = (int)((pr * TILES + q) * BM + (warp & 3) * 32);  // C1 row of lane 0
-      for (int64_t ch = 0; ch < nchunk; ++ch) {
+      int64_t klo, khi;
+      stripe_kspan(a, s, klo, khi);
+      const int64_t nch = (khi - klo + a.promote - 1) / a.promote;
+      for (int64_t ch = 0; ch < nch; ++ch) {
         // thread 0 waits for the accumulators; the 8 warps meet at a named barrier
         if (threadIdx.x == 0) epi_ok[accph] = mbar_wait(accFull, accph, abort_flag, a.err, ERR_TIMEOUT_BASE + 6) ? 1 : 0;
         named_bar_sync(1 + 4, EPI_WARPS * 32);
@@ -718,8 +763,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
 //   (r/8)*512 + (r%8)*64 + ((k/8) ^ ((r%8)/2))*16 + (k%8)*2.
 // Tile t holds Re K for m = 64t + r (r < 64) and Im K for m = 64t + r - 64 (r >= 64);
 // tiles with 64t >= M are zero (padding to an even count).
-__global__ void k_build_A(int M, int64_t N, int64_t kblocks, int npairs, int64_t c, double kappa, double delta,
-                          uint8_t* A) {
+__global__ void k_build_A(int M, double msh, int64_t N, int64_t kblocks, int npairs, int64_t c, double kappa,
+                          double delta, uint8_t* A) {
   const int64_t K = kblocks * BK;
   const int64_t total = (int64_t)npairs * TILES * BM * (K / 8);  // one thread per 8 consecutive k
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -743,7 +788,7 @@ __global__ void k_build_A(int M, int64_t N, int64_t kblocks, int npairs, int64_t
         float v = 0.f;
         if (i < N && m < M) {
           const double di = (double)(i - c);
-          const double th = di * di * (0.5 * kappa) - (double)(m - M / 2) * di * delta;
+          const double th = di * di * (0.5 * kappa) - ((double)m - msh) * di * delta;
           const float2 kk = cis_turns_f(th);
           v = im ? kk.y : kk.x;
         }
@@ -904,7 +949,7 @@ fzp_status dense_layout(Plan& P, FormSizes* out) {
 
 fzp_status dense_fill_tables(Plan& P, cudaStream_t s) {
   Dense& d = P.dn;
-  k_build_A<<<8 * d.num_sms, 256, 0, s>>>(P.M, P.N, d.kblocks, d.npairs, P.c, P.kappa, P.delta,
+  k_build_A<<<8 * d.num_sms, 256, 0, s>>>(P.M, P.msh, P.N, d.kblocks, d.npairs, P.c, P.kappa, P.delta,
                                           reinterpret_cast<uint8_t*>(d.d_A));
   P.launches += 1;
   FZP_CUDA_TRY(cudaGetLastError());

@@ -2,9 +2,10 @@
 //
 // Notation (Eq. 2 and Fig. 2):
 //   aperture sample (j, i), i, j in [0, N), centred index di = i - c, c = (N-1)/2,
-//   u_i = di * dx;  ROI sample (n, m), x_m = (m - M/2) p.
+//   u_i = di * dx;  ROI sample (n, m), x_m = (m - msh) p, msh = -x0 / p
+//   (msh = M/2 for the ROI centred on the focus).
 //   Row kernel K[m, i] = exp(2 pi i theta(m, i)) with the phase in turns
-//     theta(m, i) = di^2 kappa / 2 - (m - M/2) di delta,
+//     theta(m, i) = di^2 kappa / 2 - (m - msh) di delta,
 //     kappa = dx^2 / (lambda f),  delta = p dx / (lambda f)   (Eq. 2, Eq. 10).
 //   The same matrix serves the column pass (the grids of both axes coincide):
 //     U = Pre * chirp_out .* (K T K^T).
@@ -176,6 +177,7 @@ struct Dense {
 struct Plan {
   // problem
   double D, f, lambda, dx, R, p, x0;
+  double msh = 0;  // ROI shift in pitches: x_m = (m - msh) p (M/2 when centred)
   int64_t N, c;
   int M;
   int form, precision, stripe_rows;
@@ -253,5 +255,8 @@ __host__ __device__ __forceinline__ int c1_row_im(int m) { return (m >> 6) * 128
 struct fzp_plan_s : public fzp::Plan {};
 
 namespace fzp {
+// Host part of fzp_plan (validation, grids, zone-rule limits; no CUDA call):
+// fills P and returns the disc limit s_R and the last zone step.
+fzp_status plan_host(const fzp_params* params, Plan& P, int64_t* sR, int64_t* zmax);
 fzp_status autotune(const fzp_params* in, fzp_params* chosen, fzp_plan_t* keep);
 }

@@ -199,48 +199,46 @@ __global__ void k_fwhm(int M, double p, const double2* __restrict__ U, double* w
 
 }  // namespace
 
-fzp_status metrics(Plan& P, const void* d_field, cudaStream_t s, fzp_metrics_t* out) {
-  const int M = P.M;
+// The extractor's kernels on `scr` (sums, counts and bins cleared first),
+// then the scratch header copied to h[] (host); the caller synchronises.
+static fzp_status extract_enqueue(int M, double p, double rnull, int64_t N, int64_t c, int64_t sR,
+                                  const double2* U, double* scr, double* h, cudaStream_t s) {
   int logM = 0;
   while ((1 << logM) < M) ++logM;
-  if ((1 << logM) != M) return set_error(FZP_E_UNSUPPORTED, "metrics need a power-of-two M (got %d)", M);
-  const double2* U = reinterpret_cast<const double2*>(d_field);
-  double* scr = P.d_metrics;
   double2* F = reinterpret_cast<double2*>(scr + S_FFT + 6 * 1024);
-  const double lf = P.lambda * P.f;
-  const double rnull = AIRY_NULL * lf / (2.0 * P.R);
   FZP_CUDA_TRY(cudaMemsetAsync(scr, 0, S_FFT * sizeof(double), s));
-  k_sums<<<256, 256, 0, s>>>(M, P.p, rnull * rnull, U, scr);
-  k_count<<<256, 256, 0, s>>>(P.N, P.c, P.mg.sR, scr);
+  k_sums<<<256, 256, 0, s>>>(M, p, rnull * rnull, U, scr);
+  k_count<<<256, 256, 0, s>>>(N, c, sR, scr);
   k_fft_rows<<<M, 256, M * sizeof(double2), s>>>(M, logM, U, F);
   k_fft_cols<<<M, 256, M * sizeof(double2), s>>>(M, logM, F, scr);
-  k_fwhm<<<2, 32, 0, s>>>(M, P.p, U, scr + S_FFT, scr);
-  P.launches += 5;
+  k_fwhm<<<2, 32, 0, s>>>(M, p, U, scr + S_FFT, scr);
   FZP_CUDA_TRY(cudaGetLastError());
-  double h[S_FFT];
-  FZP_CUDA_TRY(cudaMemcpyAsync(h, scr, sizeof(h), cudaMemcpyDeviceToHost, s));
-  int err = 0;
-  FZP_CUDA_TRY(cudaMemcpyAsync(&err, P.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-  FZP_CUDA_TRY(cudaStreamSynchronize(s));
-  if (err) return set_error(FZP_E_TIMEOUT, "a device-side wait timed out (code %d); results are invalid", err);
+  FZP_CUDA_TRY(cudaMemcpyAsync(h, scr, S_FFT * sizeof(double), cudaMemcpyDeviceToHost, s));
+  return FZP_OK;
+}
+
+// Host post-processing of the scratch header h[] into the metrics: DE over
+// P_in = count dx^2, Strehl, and the radial MTF read at nu_cut/2 and at the
+// 16 sample frequencies (linear interpolation between bin centres).
+static void extract_finish(const double* h, double p, double R2, double lf, double dx2, fzp_metrics_t* out) {
   const double sum = h[S_SUM], lobe = h[S_LOBE];
   int64_t count;
   memcpy(&count, &h[S_COUNT], sizeof(count));
-  const double pin = (double)count * P.dx2;
+  const double pin = (double)count * dx2;
   out->aperture_count = count;
   out->p_in = pin;
-  out->p_in_disc = 3.14159265358979323846 * P.R2;
-  out->de_lobe = lobe * P.p * P.p / pin;
-  out->de_roi = sum * P.p * P.p / pin;
+  out->p_in_disc = 3.14159265358979323846 * R2;
+  out->de_lobe = lobe * p * p / pin;
+  out->de_roi = sum * p * p / pin;
   out->fwhm_x = h[S_OUT];
   out->fwhm_y = h[S_OUT + 1];
   out->peak = h[S_OUT + 2];
-  const double ip = 3.14159265358979323846 * P.R2 / lf;
+  const double ip = 3.14159265358979323846 * R2 / lf;
   out->strehl = out->peak / (ip * ip);
   // radial MTF: bin means normalised by |OTF(0,0)| = sum I
   double centre[NBINS], mean[NBINS];
   int nb = 0;
-  const double nyq = 1.0 / (2.0 * P.p);
+  const double nyq = 1.0 / (2.0 * p);
   for (int b = 0; b < NBINS; ++b) {
     int64_t c;
     memcpy(&c, &h[S_BINCNT + b], sizeof(c));
@@ -259,9 +257,27 @@ fzp_status metrics(Plan& P, const void* d_field, cudaStream_t s, fzp_metrics_t* 
     const double t = (nu - centre[i]) / (centre[i + 1] - centre[i]);
     return mean[i] + t * (mean[i + 1] - mean[i]);
   };
-  const double nucut = 2.0 * P.R / lf;
+  const double nucut = 2.0 * std::sqrt(R2) / lf;
   out->mtf_half_cut = interp(0.5 * nucut);
   for (int q = 0; q < 16; ++q) out->mtf16[q] = interp((q + 0.5) * nucut / 16.0);
+}
+
+fzp_status metrics(Plan& P, const void* d_field, cudaStream_t s, fzp_metrics_t* out) {
+  const int M = P.M;
+  if ((M & (M - 1)) != 0) return set_error(FZP_E_UNSUPPORTED, "metrics need a power-of-two M (got %d)", M);
+  if (P.msh != (double)(M / 2))
+    return set_error(FZP_E_UNSUPPORTED, "metrics read the focus at the ROI centre: the plan's ROI is off axis");
+  const double lf = P.lambda * P.f;
+  double h[S_FFT];
+  fzp_status st = extract_enqueue(M, P.p, AIRY_NULL * lf / (2.0 * P.R), P.N, P.c, P.mg.sR,
+                                  reinterpret_cast<const double2*>(d_field), P.d_metrics, h, s);
+  if (st != FZP_OK) return st;
+  P.launches += 5;
+  int err = 0;
+  FZP_CUDA_TRY(cudaMemcpyAsync(&err, P.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FZP_CUDA_TRY(cudaStreamSynchronize(s));
+  if (err) return set_error(FZP_E_TIMEOUT, "a device-side wait timed out (code %d); results are invalid", err);
+  extract_finish(h, P.p, P.R2, lf, P.dx2, out);
   return FZP_OK;
 }
 
@@ -296,10 +312,6 @@ fzp_status noalloc_scratch(double** out) {
   return FZP_OK;
 }
 
-double fl_mul(int64_t s, double a) {
-  volatile double prod = (double)s * a;
-  return prod;
-}
 }  // namespace
 
 }  // namespace fzp
@@ -308,92 +320,28 @@ extern "C" fzp_status fzp_metrics_noalloc(const fzp_params* in, const void* d_fi
                                           fzp_metrics_t* out) {
   using namespace fzp;
   if (!in || !d_field || !out) return set_error(FZP_E_INVALID, "NULL argument");
-  if (!(in->D > 0) || !(in->f > 0) || !(in->lambda > 0) || !(in->pitch > 0) || !std::isfinite(in->D) ||
-      !std::isfinite(in->f) || !std::isfinite(in->lambda) || !std::isfinite(in->pitch) || in->dx < 0)
-    return set_error(FZP_E_INVALID, "D, f, lambda and pitch must be finite and positive");
-  if (in->M < 64 || in->M > kNoAllocMaxM || (in->M & (in->M - 1)) != 0)
+  // the plan's own host path: validation (Eq. 6, N, levels, centre
+  // configuration, ROI origin) and grids (Fig. 2 / Fig. 18 Stage 1-2), no
+  // CUDA call and no allocation
+  Plan P;
+  int64_t sR = 0, zmax = 0;
+  fzp_status st = plan_host(in, P, &sR, &zmax);
+  if (st != FZP_OK) return st;
+  if (P.M > kNoAllocMaxM)
     return set_error(FZP_E_INVALID, "M = %d outside the static scratch of fzp_metrics_noalloc "
-                     "(a power of two in [64, %d])", in->M, kNoAllocMaxM);
-  if (in->N < 0 || (in->N > 0 && (in->N % 2) == 0)) return set_error(FZP_E_INVALID, "N must be 0 or odd");
-  if (in->levels < 0 || in->levels > 64) return set_error(FZP_E_INVALID, "levels must be in [0, 64]");
-  if (in->centre_open != 0 && in->centre_open != 1) return set_error(FZP_E_INVALID, "centre_open must be 0 or 1");
-  // grids as fzp_plan derives them (Fig. 2 / Fig. 18 Stage 1-2): dx_in =
-  // lambda f / (2 D max(L, 2)); the aperture disc does not depend on the
-  // plate's levels or centre configuration
-  const double lf = in->lambda * in->f;
-  const double dx = in->dx > 0 ? in->dx : lf / (2.0 * (in->levels > 2 ? in->levels : 2) * in->D);
-  int64_t N = in->N;
-  if (N == 0) {
-    const double n = std::ceil(in->D / dx);
-    if (!(n < 1e9)) return set_error(FZP_E_INVALID, "grid too large");
-    N = (int64_t)n;
-    if ((N % 2) == 0) N += 1;
-  }
-  const int64_t c = (N - 1) / 2;
-  const double R = std::min(in->D / 2.0, lf / (2.0 * dx));
-  const double dx2 = dx * dx, R2 = R * R;
-  int64_t sR = (int64_t)std::floor(R2 / dx2);
-  if (sR < 0) sR = 0;
-  while (fl_mul(sR + 1, dx2) <= R2) ++sR;
-  while (sR > 0 && fl_mul(sR, dx2) > R2) --sR;
-
+                     "(a power of two in [64, %d])", P.M, kNoAllocMaxM);
+  if (P.msh != (double)(P.M / 2))
+    return set_error(FZP_E_UNSUPPORTED, "metrics read the focus at the ROI centre: the ROI is off axis");
   double* scr = nullptr;
-  fzp_status st = noalloc_scratch(&scr);
+  st = noalloc_scratch(&scr);
   if (st != FZP_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  const int M = in->M;
-  int logM = 0;
-  while ((1 << logM) < M) ++logM;
-  const double2* U = reinterpret_cast<const double2*>(d_field);
-  double2* F = reinterpret_cast<double2*>(scr + S_FFT + 6 * 1024);
-  const double rnull = AIRY_NULL * lf / (2.0 * R);
-  FZP_CUDA_TRY(cudaMemsetAsync(scr, 0, S_FFT * sizeof(double), s));  // sums, counts, bins start at zero
-  k_sums<<<256, 256, 0, s>>>(M, in->pitch, rnull * rnull, U, scr);
-  k_count<<<256, 256, 0, s>>>(N, c, sR, scr);
-  k_fft_rows<<<M, 256, M * sizeof(double2), s>>>(M, logM, U, F);
-  k_fft_cols<<<M, 256, M * sizeof(double2), s>>>(M, logM, F, scr);
-  k_fwhm<<<2, 32, 0, s>>>(M, in->pitch, U, scr + S_FFT, scr);
-  FZP_CUDA_TRY(cudaGetLastError());
+  const double lf = P.lambda * P.f;
   double h[S_FFT];
-  FZP_CUDA_TRY(cudaMemcpyAsync(h, scr, sizeof(h), cudaMemcpyDeviceToHost, s));
+  st = extract_enqueue(P.M, P.p, AIRY_NULL * lf / (2.0 * P.R), P.N, P.c, sR,
+                       reinterpret_cast<const double2*>(d_field), scr, h, s);
+  if (st != FZP_OK) return st;
   FZP_CUDA_TRY(cudaStreamSynchronize(s));
-  const double sum = h[S_SUM], lobe = h[S_LOBE];
-  int64_t count;
-  memcpy(&count, &h[S_COUNT], sizeof(count));
-  const double pin = (double)count * dx2;
-  out->aperture_count = count;
-  out->p_in = pin;
-  out->p_in_disc = 3.14159265358979323846 * R2;
-  out->de_lobe = lobe * in->pitch * in->pitch / pin;
-  out->de_roi = sum * in->pitch * in->pitch / pin;
-  out->fwhm_x = h[S_OUT];
-  out->fwhm_y = h[S_OUT + 1];
-  out->peak = h[S_OUT + 2];
-  const double ip = 3.14159265358979323846 * R2 / lf;
-  out->strehl = out->peak / (ip * ip);
-  double centre[NBINS], mean[NBINS];
-  int nb = 0;
-  const double nyq = 1.0 / (2.0 * in->pitch);
-  for (int b = 0; b < NBINS; ++b) {
-    int64_t cnt;
-    memcpy(&cnt, &h[S_BINCNT + b], sizeof(cnt));
-    if (cnt > 0) {
-      centre[nb] = (b + 0.5) * nyq / NBINS;
-      mean[nb] = h[S_BINS + b] / (double)cnt / sum;
-      ++nb;
-    }
-  }
-  auto interp = [&](double nu) -> double {
-    if (nb == 0) return (double)NAN;
-    if (nu <= centre[0]) return mean[0];
-    if (nu >= centre[nb - 1]) return mean[nb - 1];
-    int i = 0;
-    while (centre[i + 1] < nu) ++i;
-    const double t = (nu - centre[i]) / (centre[i + 1] - centre[i]);
-    return mean[i] + t * (mean[i + 1] - mean[i]);
-  };
-  const double nucut = 2.0 * R / lf;
-  out->mtf_half_cut = interp(0.5 * nucut);
-  for (int q = 0; q < 16; ++q) out->mtf16[q] = interp((q + 0.5) * nucut / 16.0);
+  extract_finish(h, P.p, P.R2, lf, P.dx2, out);
   return FZP_OK;
 }

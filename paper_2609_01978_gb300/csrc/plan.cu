@@ -116,6 +116,14 @@ fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
   if (in->centre_open != 0 && in->centre_open != 1) return set_error(FZP_E_INVALID, "centre_open must be 0 or 1");
   if (in->centre_open && in->levels >= 2)
     return set_error(FZP_E_INVALID, "centre_open applies to the binary amplitude plate (levels 0 or 1)");
+  if (in->roi_origin != 0 && in->roi_origin != 1) return set_error(FZP_E_INVALID, "roi_origin must be 0 or 1");
+  if (in->reserved != 0) return set_error(FZP_E_INVALID, "reserved must be 0");
+  if (in->roi_origin == 1) {
+    if (!std::isfinite(in->x0) || !std::isfinite(in->y0))
+      return set_error(FZP_E_INVALID, "x0 and y0 must be finite");
+    if (in->x0 != in->y0)
+      return set_error(FZP_E_UNSUPPORTED, "off-axis ROI with x0 != y0 (one kernel matrix serves both axes)");
+  }
   P.levels = in->levels >= 2 ? in->levels : 0;
   P.mg.centre_open = in->centre_open;
   const double lf = in->lambda * in->f;
@@ -137,7 +145,15 @@ fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
   if (P.N < 3) return set_error(FZP_E_INVALID, "N must be >= 3");
   P.c = (P.N - 1) / 2;
   P.R = std::min(in->D / 2.0, lf / (2.0 * P.dx));  // R_eff (Fig. 2 Stage 2)
-  P.x0 = -(double)(P.M / 2) * P.p;
+  // ROI grid x_m = x0 + m p = (m - msh) p on both axes (Eq. 10's A from x0):
+  // centred on the focus, msh = M/2 exactly
+  if (in->roi_origin == 1) {
+    P.x0 = in->x0;
+    P.msh = -in->x0 / P.p;
+  } else {
+    P.x0 = -(double)(P.M / 2) * P.p;
+    P.msh = (double)(P.M / 2);
+  }
   P.dx2 = P.dx * P.dx;
   P.R2 = P.R * P.R;
   P.kappa = P.dx2 / lf;
@@ -341,10 +357,12 @@ fzp_status fzp_plan(const fzp_params* params, fzp_plan_t* out) {
   return FZP_OK;
 }
 
+}  // extern "C"
+
 // Host part of a plan: validation, grids and the zone-rule limits, without
 // any CUDA call.  Returns the disc limit and the last zone step through *sR
 // and *zmax.
-static fzp_status plan_host(const fzp_params* params, Plan& P, int64_t* sR, int64_t* zmax) {
+fzp_status fzp::plan_host(const fzp_params* params, Plan& P, int64_t* sR, int64_t* zmax) {
   fzp_status st = validate_and_derive(params, P);
   if (st != FZP_OK) return st;
   *sR = disc_limit(P.dx2, P.R2);
@@ -356,6 +374,8 @@ static fzp_status plan_host(const fzp_params* params, Plan& P, int64_t* sR, int6
     return set_error(FZP_E_INVALID, "kappa >= 1: grid far too coarse");
   return FZP_OK;
 }
+
+extern "C" {
 
 fzp_status fzp_plan_query(const fzp_params* params, fzp_plan_info* out) {
   if (!params || !out) return set_error(FZP_E_INVALID, "NULL argument");
@@ -384,6 +404,7 @@ fzp_status fzp_plan_query(const fzp_params* params, fzp_plan_info* out) {
   out->levels = P.levels;
   out->passes = P.passes.empty() ? 1 : (int32_t)P.passes.size();
   out->centre_open = P.mg.centre_open;
+  out->s_R = sR;
   return FZP_OK;
 }
 
@@ -419,6 +440,7 @@ fzp_status fzp_plan_info_get(fzp_plan_t plan, fzp_plan_info* out) {
   out->levels = P.levels;
   out->passes = P.passes.empty() ? 1 : (int32_t)P.passes.size();
   out->centre_open = P.mg.centre_open;
+  out->s_R = P.mg.sR;
   out->device_bytes = P.device_bytes;
   return FZP_OK;
 }

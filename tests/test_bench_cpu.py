@@ -68,3 +68,21 @@ def test_reference_arm_under_torchrun_prints_on_rank0_only():
     assert len(outs[0]) == 1
     d = json.loads(outs[0][0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2
+
+
+def test_disc_sample_count_of_the_roofline(oracle_mod):
+    """The roofline's work count (samples inside the aperture disc over the
+    timed rows) from the library's host plan equals the oracle's aperture
+    count over all rows, and splits additively over row ranges."""
+    import paper_2609_01978_gb300 as fzp
+    import __graft_entry__
+    __graft_entry__.build()
+    for D, f in [(4e-3, 20e-3), (0.05, 0.25)]:
+        q = fzp.plan_query(D=D, f=f, lam=632.8e-9, M=64, pitch=0.4e-6)
+        g = oracle_mod.Geometry(D=D, f=f, lam=632.8e-9, M=64, p=0.4e-6)
+        N, c, sR = q["N"], q["c"], q["s_R"]
+        assert N == g.N
+        assert bench.disc_samples(N, c, sR, 0, N) == oracle_mod.count_aperture(g)
+        mid = N // 3
+        assert bench.disc_samples(N, c, sR, 0, mid) + bench.disc_samples(N, c, sR, mid, N) == \
+            bench.disc_samples(N, c, sR, 0, N)

@@ -69,6 +69,29 @@ def test_unsupported_combinations(fzp):
     assert ei.value.status == fzp.FZP_E_UNSUPPORTED
 
 
+def test_roi_origin_validation(fzp):
+    """Off-axis ROI (Eq. 10's A from the first ROI coordinate): x0 = y0 is
+    accepted and reported by the host plan; x0 != y0 needs a second kernel
+    matrix and is unsupported; a bad flag or a non-finite origin is invalid."""
+    import ctypes
+    L = fzp.lib()
+    base = dict(D=1e-3, f=5e-3, lam=632.8e-9, M=64, pitch=0.4e-6)
+    q = fzp.plan_query(x0=-3.3e-6, **base)
+    assert q["x0"] == -3.3e-6
+    assert fzp.plan_query(**base)["x0"] == -32 * 0.4e-6
+    inf = fzp.PlanInfo()
+    for kw, status in [(dict(roi_origin=1, x0=1e-6, y0=2e-6), fzp.FZP_E_UNSUPPORTED),
+                       (dict(roi_origin=2), fzp.FZP_E_INVALID),
+                       (dict(roi_origin=1, x0=float("inf"), y0=float("inf")), fzp.FZP_E_INVALID),
+                       (dict(reserved=1), fzp.FZP_E_INVALID)]:
+        p = fzp._params(**base)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        assert L.fzp_plan_query(ctypes.byref(p), ctypes.byref(inf)) == status, kw
+        h = ctypes.c_void_p()
+        assert L.fzp_plan(ctypes.byref(p), ctypes.byref(h)) == status and not h.value, kw
+
+
 def test_null_arguments(fzp):
     import ctypes
     L = fzp.lib()
