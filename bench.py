@@ -200,7 +200,7 @@ def run_membranes(args, fzp, torch, dev, ws, pg, rank, local):
     probs = [dict(D=m.D, f=fnum * m.D, lam=m.lam, M=M, pitch=m.lam * fnum / 8, precision=fzp.PREC_AUTO_1E4,
                   deform=fzp.make_deform(m.amp, m.period, m.theta, m.taper, m.ridges)) for m in mem]
     stream = torch.cuda.current_stream(dev)
-    b = fzp.Batch(probs)
+    b = fzp.Batch(probs)  # autotunes every instance (cached per process for the e2e leg)
     infos = [b.info(i) for i in range(len(probs))]
     samples = sum(inf["N"] ** 2 for inf in infos)
     fields = [torch.empty((M, M), dtype=torch.complex128, device=dev) for _ in probs]
@@ -235,12 +235,52 @@ def run_membranes(args, fzp, torch, dev, ws, pg, rank, local):
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         ms = float(t.item())
+    kernels = b.kernels
     b.close()
     forms = {}
+    dense_flops = 0.0
     for inf in infos:
         k = ("dense" if inf["form"] == fzp.FORM_DENSE else "bluestein") + "/" + \
             {0: "f64", 1: "f32", 2: "split-bf16", 3: "bf16"}[inf["precision"]]
         forms[k] = forms.get(k, 0) + 1
+        if inf["form"] == fzp.FORM_DENSE:
+            # membrane passes: 2 passes x 3 split products x 2 real rows x M x 2 flops
+            # = 24 M flops per aperture sample inside the disc
+            dense_flops += 24.0 * M * disc_samples(inf["N"], inf["c"], inf["s_R"], 0, inf["N"])
+    peaks, peak_kind = _peaks()
+    roof = None
+    if dense_flops > 0:
+        achieved = dense_flops * args.steps / (ms / 1e3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "whole step (graph of every instance's passes; dense membrane "
+                                           "passes dominate)", "peak_source": peak_kind + " bf16 sustained",
+                "work": "24 M flops per aperture sample inside the disc (dense instances only)"}
+    # end to end through the public API with host buffers: batch from host
+    # parameters (tuned choices cached in-process), propagate, fields to pinned
+    # host memory, every instance's metrics, destroy
+    e2e = None
+    n_e2e = min(args.e2e_steps, 1)  # one end-to-end batch: a step of the full batch takes minutes
+    if n_e2e > 0:
+        hosts = [torch.empty((M, M), dtype=torch.complex128, pin_memory=True) for _ in probs]
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        h2d = 0
+        for _ in range(n_e2e):
+            b2 = fzp.Batch(probs)
+            h2d = sum(8 * b2.info(i)["n_thresholds"] for i in range(len(probs)))
+            b2.propagate(fields, stream=stream)
+            for i in range(len(probs)):
+                hosts[i].copy_(fields[i], non_blocking=True)
+            for i in range(len(probs)):
+                b2.metrics(i, fields[i], stream=stream)
+            torch.cuda.synchronize(dev)
+            b2.close()
+        e2e_s = (time.perf_counter() - t0) / n_e2e
+        e2e = {"value": ws * samples / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": len(probs) * (M * M * 16 + 8 * 1024 + 4),
+               "note": "fzp_batch_plan (tuning cached) + graph capture and launch + fields to pinned host + "
+                       "fzp_batch_metrics per instance + fzp_batch_destroy"}
     return {"metric": METRIC, "value": ws * args.steps * samples / (ms / 1e3) / 1e9, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "mixed (autotuned per instance)",
@@ -248,7 +288,7 @@ def run_membranes(args, fzp, torch, dev, ws, pg, rank, local):
             "config": {"workload": "membranes", "instances": len(probs), "of": 256, "seed": 0, "roi": M,
                        "f_number": fnum, "samples_per_step": samples, "forms": forms,
                        "l2": "256 MiB buffer written between steps (flush)"},
-            "roofline": None, "e2e": None, "gpu_launches": None, "clocks": clocks,
+            "roofline": roof, "e2e": e2e, "gpu_launches": kernels * args.steps, "clocks": clocks,
             "per_instance_ms": ms / args.steps / len(probs),
             "de_lobe_range": [min(m["de_lobe"] for m in mets), max(m["de_lobe"] for m in mets)]}
 
@@ -369,7 +409,7 @@ def main():
                     help="rows of the plain form's timed sample (0: all; -1: all up to N = 316,057, else 16,384)")
     ap.add_argument("--replicas", action="store_true",
                     help="N > 1: every rank propagates the whole aperture (weak scaling) instead of its rows")
-    ap.add_argument("--instances", type=int, default=16, help="membranes workload: instances per batch")
+    ap.add_argument("--instances", type=int, default=256, help="membranes workload: instances per batch")
     ap.add_argument("--rows", type=int, default=0,
                     help="time only this many central aperture rows per step (a sample; 0: all N)")
     args = ap.parse_args()

@@ -319,6 +319,10 @@ FZP_API fzp_status fzp_batch_info(fzp_batch_t batch, int index, fzp_plan_info* o
 FZP_API fzp_status fzp_batch_metrics(fzp_batch_t batch, int index, const void* d_field, void* stream,
                                      fzp_metrics_t* out);
 
+/* Kernel launches of one replay: the kernel nodes of the captured graph
+ * (0 before the first fzp_batch_propagate).  Host only. */
+FZP_API fzp_status fzp_batch_kernels(fzp_batch_t batch, int64_t* kernels);
+
 /* Release the batch.  NULL is accepted.  Synchronises the device. */
 FZP_API fzp_status fzp_batch_destroy(fzp_batch_t batch);
 
@@ -378,7 +382,11 @@ FZP_API fzp_status fzp_surrogate_destroy(fzp_surrogate_t s);
  * loads libfzp holds until the process exits.  Limit: M <= 512 (power of two,
  * >= 64); larger M is rejected with FZP_E_INVALID.  The first call on a device
  * looks up the array's device address with that device current (once per
- * device); make that first call before any stream capture.  All calls share
+ * device) and keeps it for the life of the process; make that first call
+ * before any stream capture.  cudaDeviceReset discards the array's address
+ * with the context, so a process that resets a device must not call this
+ * entry point on that device afterwards.  The parameters are validated as
+ * fzp_plan validates them (no CUDA call for that).  All calls share
  * the array and it keeps the last call's contents (the call clears what must
  * start at zero); calls that overlap on the GPU, on any streams, race and give
  * wrong results, so serialise them.

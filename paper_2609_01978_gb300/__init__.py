@@ -111,6 +111,7 @@ def lib() -> ctypes.CDLL:
             "fzp_batch_info": [vp, i32, ctypes.POINTER(PlanInfo)],
             "fzp_batch_metrics": [vp, i32, vp, vp, ctypes.POINTER(Metrics)],
             "fzp_batch_destroy": [vp],
+            "fzp_batch_kernels": [vp, ctypes.POINTER(ctypes.c_int64)],
             "fzp_surrogate_create": [i32, i32, i32, i32, i32, ctypes.c_uint64, ctypes.POINTER(vp)],
             "fzp_surrogate_params": [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t, i32],
             "fzp_surrogate_infer": [vp, vp, i32, vp, vp],
@@ -278,6 +279,13 @@ class Batch:
     def propagate(self, fields, stream=None):
         ptrs = (ctypes.c_void_p * self.n)(*[_ptr(f) for f in fields])
         _check(lib().fzp_batch_propagate(self._h, ptrs, _stream(stream)))
+
+    @property
+    def kernels(self) -> int:
+        """Kernel launches of one replay of the captured graph."""
+        n = ctypes.c_int64()
+        _check(lib().fzp_batch_kernels(self._h, ctypes.byref(n)))
+        return n.value
 
     def metrics(self, i: int, field, stream=None) -> dict:
         m = Metrics()

@@ -4,9 +4,10 @@
 // <= 1e-4) it builds the candidate plans -- the split-BF16 dense form with two
 // accumulation-chunk lengths, and the FP32 Bluestein form -- times each on a
 // probe stripe of central aperture rows sized to fill the GPU twice with dense
-// work items, and keeps the fastest.  Deformed membranes have complex
-// transmission, which only the Bluestein form supports, and so have phase
-// plates of more than two levels.  Results are cached
+// work items, and keeps the fastest.  Deformed membranes (complex
+// transmission) are dense candidates as binary amplitude plates (two membrane
+// passes); odd-level phase plates and deformed phase plates have the
+// Bluestein form only.  Results are cached
 // per (N, M, deformed) for the process and, when FZP_TUNE_CACHE names a file,
 // in that file (one "key value..." line per problem).
 //
@@ -153,7 +154,9 @@ fzp_status autotune(const fzp_params* in, fzp_params* chosen, fzp_plan_t* keep) 
     return FZP_OK;
   }
   std::vector<Choice> cands;
-  if (!deformed && geo.levels % 2 == 0) {  // the dense form's mask values must be exact in BF16
+  // the dense form takes binary and even-level plates, and deformed binary
+  // amplitude plates (membrane passes with split mask values)
+  if ((!deformed && geo.levels % 2 == 0) || (deformed && geo.levels == 0)) {
     // cluster 0: the plan's own choice (4 CTAs for M = 512); 1: single-CTA kernel
     cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 128, 0, 0, 0});
     cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 256, 0, 0, 0});
@@ -347,6 +350,22 @@ fzp_status fzp_batch_metrics(fzp_batch_t b, int i, const void* d_field, void* st
   if (!b || !d_field || !out || i < 0 || i >= (int)b->inst.size())
     return set_error(FZP_E_INVALID, "bad batch index or NULL argument");
   return metrics(*b->inst[i], d_field, (cudaStream_t)stream, out);
+}
+
+fzp_status fzp_batch_kernels(fzp_batch_t b, int64_t* kernels) {
+  if (!b || !kernels) return set_error(FZP_E_INVALID, "NULL argument");
+  *kernels = 0;
+  if (!b->graph) return FZP_OK;
+  size_t n = 0;
+  FZP_CUDA_TRY(cudaGraphGetNodes(b->graph, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  FZP_CUDA_TRY(cudaGraphGetNodes(b->graph, nodes.data(), &n));
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    FZP_CUDA_TRY(cudaGraphNodeGetType(nd, &t));
+    if (t == cudaGraphNodeTypeKernel) ++*kernels;
+  }
+  return FZP_OK;
 }
 
 fzp_status fzp_batch_destroy(fzp_batch_t b) {

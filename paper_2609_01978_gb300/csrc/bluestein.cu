@@ -140,11 +140,7 @@ struct RowArgs {
   // the deformation phase in turns, 2 w / lambda, as FP32 coefficients:
   //   amp2 sin(2 pi (di kx + dj ky)) (1 - tq (di^2 + dj^2)) + sum_k h2_k exp(-q_k d_k^2),
   //   d_k = (di - pi_k) nx_k + (dj - pj_k) ny_k  (sample units; (pi_k, pj_k) on the crease)
-  struct DeformF {
-    float kxh, kxl, kyh, kyl, amp2, tq;  // wrinkle rates split hi + lo, hi a multiple of 2^-14
-    int n;
-    float nx[3], ny[3], pi_[3], pj[3], q[3], h2[3];
-  } df;
+  DeformCoef df;
   const void* pre;   // N
   const void* H;     // [L1][L2]
   void* Z;           // [rows][L1][L2]
@@ -548,6 +544,38 @@ static size_t f1_smem(const RowArgs& a) {
   return sizeof(typename Cplx<R>::T) * (size_t)((a.L1 + 1) * a.B + a.L1 / 2);
 }
 
+}  // namespace
+
+DeformCoef deform_coef(const Plan& P) {
+  DeformCoef c{};
+  const fzp_deform& d = P.deform;
+  const double k2 = 2.0 / P.lambda;  // metres -> turns of phase (phi / 2 pi = 2 w / lambda)
+  const double kx = std::cos(d.theta) * P.dx / d.period, ky = std::sin(d.theta) * P.dx / d.period;
+  c.kxh = (float)(std::rint(kx * 16384.0) / 16384.0);
+  c.kyh = (float)(std::rint(ky * 16384.0) / 16384.0);
+  c.kxl = (float)(kx - (double)c.kxh);
+  c.kyl = (float)(ky - (double)c.kyh);
+  c.amp2 = (float)(d.amp * k2);
+  c.tq = (float)(d.taper * P.dx * P.dx / (P.R * P.R));
+  c.zc = (float)std::cos(2.0 * M_PI * kx);
+  c.zs = (float)std::sin(2.0 * M_PI * kx);
+  c.n = d.n_ridges;
+  for (int k = 0; k < d.n_ridges && k < 3; ++k) {
+    const double nx = -std::sin(d.ridge_alpha[k]), ny = std::cos(d.ridge_alpha[k]);
+    const double sg = d.ridge_width[k] / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+    c.nx[k] = (float)nx;
+    c.ny[k] = (float)ny;
+    c.pi_[k] = (float)(d.ridge_px[k] / P.dx);
+    c.pj[k] = (float)(d.ridge_py[k] / P.dx);
+    c.q[k] = (float)(P.dx * P.dx / (2.0 * sg * sg));
+    c.h2[k] = (float)(d.ridge_h[k] * k2);
+    c.rho[k] = (float)std::exp(-2.0 * (P.dx * P.dx / (2.0 * sg * sg)) * nx * nx);
+  }
+  return c;
+}
+
+namespace {
+
 static RowArgs make_args(const Plan& P) {
   const Bluestein& b = P.bs;
   RowArgs a{};
@@ -564,28 +592,7 @@ static RowArgs make_args(const Plan& P) {
   a.has_deform = P.has_deform ? 1 : 0;
   a.def = P.deform;
   a.dx = P.dx; a.R = P.R; a.inv_lambda = 1.0 / P.lambda;
-  if (P.has_deform) {
-    const fzp_deform& d = P.deform;
-    const double k2 = 2.0 / P.lambda;  // metres -> turns of phase (phi / 2 pi = 2 w / lambda)
-    const double kx = std::cos(d.theta) * P.dx / d.period, ky = std::sin(d.theta) * P.dx / d.period;
-    a.df.kxh = (float)(std::rint(kx * 16384.0) / 16384.0);
-    a.df.kyh = (float)(std::rint(ky * 16384.0) / 16384.0);
-    a.df.kxl = (float)(kx - (double)a.df.kxh);
-    a.df.kyl = (float)(ky - (double)a.df.kyh);
-    a.df.amp2 = (float)(d.amp * k2);
-    a.df.tq = (float)(d.taper * P.dx * P.dx / (P.R * P.R));
-    a.df.n = d.n_ridges;
-    for (int k = 0; k < d.n_ridges && k < 3; ++k) {
-      const double nx = -std::sin(d.ridge_alpha[k]), ny = std::cos(d.ridge_alpha[k]);
-      const double sg = d.ridge_width[k] / (2.0 * std::sqrt(2.0 * std::log(2.0)));
-      a.df.nx[k] = (float)nx;
-      a.df.ny[k] = (float)ny;
-      a.df.pi_[k] = (float)(d.ridge_px[k] / P.dx);
-      a.df.pj[k] = (float)(d.ridge_py[k] / P.dx);
-      a.df.q[k] = (float)(P.dx * P.dx / (2.0 * sg * sg));
-      a.df.h2[k] = (float)(d.ridge_h[k] * k2);
-    }
-  }
+  if (P.has_deform) a.df = deform_coef(P);
   a.pre = b.d_pre; a.H = b.d_H; a.Z = b.d_Z; a.G = b.d_G; a.post = b.d_post; a.tw = b.d_tw;
   a.twN = (int)b.L2;
   a.twL = b.d_twL;

@@ -34,6 +34,11 @@
 //              aperture without promotion, 8e-6 with 4096-sample chunks).
 // Phase plates: L = 2 as a +-1 mask (disc and odd-zone bits); L >= 4 as L/2
 // passes of -1 / 0 / +1 masks on level sets (level mode of the generator).
+// Deformed membranes (complex transmission T e^{i phi}): two passes with the
+// real masks T cos(phi) and T sin(phi), whose fields enter the ROI sum with
+// weights 1 and i; each mask value is split as BF16 hi + lo (it is not exact
+// in BF16), so a K step takes K_hi B_hi + K_lo B_hi + K_hi B_lo (the dropped
+// K_lo B_lo is ~2^-17 of the product) in 3 stages of 64 KiB.
 // Every mbarrier wait is bounded in time; on expiry the kernel records an error
 // code, drains what it issued, frees tensor memory and returns.
 #include <cuda.h>
@@ -54,9 +59,10 @@ constexpr int TILES = 2;               // kernel tiles per item: 256 kernel rows
 constexpr int BN = 256;                // aperture rows per item (tcgen05 N)
 constexpr int BK = 32;                 // K per stage: one 64-byte swizzle row of BF16
 constexpr int STAGES = 4;
+constexpr int STAGES_CX = 3;           // membrane passes: A 32 KiB + B hi and lo planes 32 KiB
 constexpr int SUB = BM * BK * 2;       // 8 KiB: one (tile, hi|lo) operand image
 constexpr int A_BYTES = TILES * 2 * SUB;  // 32 KiB per stage: [t0 hi][t1 hi][t0 lo][t1 lo]
-constexpr int B_BYTES = BN * BK * 2;      // 16 KiB per stage
+constexpr int B_BYTES = BN * BK * 2;      // 16 KiB per stage (per plane)
 constexpr int EPI_WARPS = 8;           // warps 0-7: epilogue (tile = warp / 4)
 constexpr int LOAD_WARP = 8, MMA_WARP = 9, GEN_WARP0 = 10;
 constexpr int GEN_WARPS = 8;           // warps 10-17: mask generators
@@ -80,6 +86,8 @@ struct DenseArgs {
   uint64_t pos, neg;        // level sets of the pass (bit q)
   int promote;              // stages per accumulation chunk
   int hi_only;              // 1: BF16 kernel (hi) only
+  int cx_sin;               // membrane pass: 0 -> mask T cos(phi), 1 -> T sin(phi)
+  DeformCoef df;            // membrane pass: the deformation phase
   const uint8_t* A;         // pre-swizzled kernel tiles, [pair][kb][t0hi t1hi t0lo t1lo]
   float* C1;                // [rows][c1_stride], column = j - c1_j0
   int64_t c1_stride, c1_j0;
@@ -424,6 +432,95 @@ __device__ __forceinline__ void expand_signed(uint32_t disc, uint32_t odd, uint3
   for (int k = 0; k < 16; ++k) w[k] = mag[k] | ((sgn[k] << 8) & 0x80008000u);
 }
 
+// Membrane pass: one row's T cos(phi) (or T sin(phi)) on 8-column chunks of a
+// 32-column block given the block's open bits, as BF16 hi and lo planes (the
+// 16-byte chunks of the 64-byte-swizzled row).  phi / 2 pi = 2 w / lambda in
+// FP32, walked along the row from the first column: the wrinkle's phasor
+// e^{2 pi i t} (t = di kx + dj ky, integer turns dropped exactly) turns by
+// e^{2 pi i kx} per column, a ridge's g = exp(-q d^2) by its ratio r, which
+// itself scales by rho = exp(-2 q nx^2); the sum is reduced to [-1/2, 1/2]
+// turns before one hardware sine or cosine (absolute error below 4e-7; the
+// walk adds ~1e-6 relative over 32 columns).  A ridge below 1e-30 at the
+// first column stays below 1e-29 in the block (its width is hundreds of
+// columns) and is left out.
+struct CxRow {
+  float fjkh, fjkl, fj2, cr[3];  // row terms: dj kyh, dj kyl, dj^2, ridge offsets
+};
+
+__device__ __forceinline__ void cx_row_init(const DeformCoef& d, int64_t dj, CxRow& r) {
+  const float fj = (float)dj;
+  r.fjkh = fj * d.kyh;
+  r.fjkl = fj * d.kyl;
+  r.fj2 = fj * fj;
+#pragma unroll
+  for (int e = 0; e < 3; ++e) r.cr[e] = (fj - d.pj[e]) * d.ny[e] - d.pi_[e] * d.nx[e];
+}
+
+__device__ __forceinline__ uint32_t bf16_pair(float a, float b) {
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+         ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+}
+
+// Chunks [q0, q0 + nq) of the row (8 columns each); di0 = column of the block
+// start minus c.
+__device__ __forceinline__ void cx_store(const DeformCoef& d, const CxRow& r, int64_t di0, uint32_t bits, int sinpart,
+                                         uint8_t* hi_row, uint8_t* lo_row, int sw, int q0, int nq) {
+  constexpr float TWO_PI = 6.28318530717958648f;
+  float fi = (float)(di0 + 8 * q0);
+  // wrinkle phasor at the first column
+  const float th = fmaf(fi, d.kxh, r.fjkh);
+  float tt = (th - rintf(th)) + fmaf(fi, d.kxl, r.fjkl);
+  tt -= rintf(tt);
+  float ws, wc;
+  __sincosf(TWO_PI * tt, &ws, &wc);
+  // ridges at the first column, and their ratios to the next column
+  float g[3], rr[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    g[e] = 0.0f;
+    rr[e] = 1.0f;
+    if (e < d.n) {
+      const float d0 = fmaf(fi, d.nx[e], r.cr[e]);
+      const float ex = d.q[e] * d0 * d0;
+      if (ex < 69.0f) {
+        g[e] = __expf(-ex);
+        rr[e] = __expf(-d.q[e] * d.nx[e] * fmaf(2.0f, d0, d.nx[e]));
+      }
+    }
+  }
+#pragma unroll 1
+  for (int q = q0; q < q0 + nq; ++q) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+      float v[2];
+#pragma unroll
+      for (int z = 0; z < 2; ++z) {
+        float wz = d.amp2 * ws * fmaf(-d.tq, fmaf(fi, fi, r.fj2), 1.0f);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          wz = fmaf(d.h2[e], g[e], wz);  // h2 = 0 beyond the plate's ridges
+          g[e] *= rr[e];
+          rr[e] *= d.rho[e];
+        }
+        const float nws = fmaf(ws, d.zc, wc * d.zs);
+        wc = fmaf(wc, d.zc, -ws * d.zs);
+        ws = nws;
+        fi += 1.0f;
+        wz -= rintf(wz);
+        const float x = TWO_PI * wz;
+        const int col = 8 * q + k + z;
+        v[z] = ((bits >> col) & 1u) ? (sinpart ? __sinf(x) : __cosf(x)) : 0.0f;
+      }
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(v[0]), h1 = __float2bfloat16_rn(v[1]);
+      h[k / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+      l[k / 2] = bf16_pair(v[0] - __bfloat162float(h0), v[1] - __bfloat162float(h1));
+    }
+    *reinterpret_cast<uint4*>(hi_row + ((q ^ sw) << 4)) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(lo_row + ((q ^ sw) << 4)) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
 // ---------------------------------------------------------------- kernel
 // Work units: unit u = (tile-pair group pu = u / n_stripes, stripe s = u % n_stripes);
 // CTA rank rk of a cluster of CL takes pair pu * CL + rk, so the CL CTAs of a
@@ -433,18 +530,29 @@ __device__ __forceinline__ void expand_signed(uint32_t disc, uint32_t odd, uint3
 // generator warps form CL phases of 8 / CL warps; phase p generates the stages of
 // the CTA's global K blocks G with G % CL == p, so CL stages are in flight at once
 // and each warp has CL stage times for its rows.
-template <int CL>
+template <int CL, bool CX>
 __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, const __grid_constant__ CUtensorMap tmC1) {
+  // CX: membrane pass (B planes hi and lo per stage, 3 stages); else 4 stages of one B plane
+  constexpr int NST = CX ? STAGES_CX : STAGES;
+  constexpr int BST = CX ? 2 * B_BYTES : B_BYTES;
+  // Generator phases: CL (phase p produces the blocks G = p mod CL; with NST =
+  // CL = 4 it is the only producer of stage p).  A membrane pass has 3 stages,
+  // so its 8 generator warps form at most two phases: a stage's producer must
+  // not get two laps ahead of its consumer, which a parity wait cannot see.
+  constexpr int PH = CX ? (CL < 2 ? CL : 2) : CL;
+  // A phase's previous wait proves block G - PH - NST consumed; the parity wait
+  // for block G is exact only if block G - 2 NST is, i.e. if NST >= PH.
+  static_assert(PH <= NST, "a generator phase could run two laps ahead of the issuer");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* sA = base;                     // STAGES x 32 KiB
-  uint8_t* sB = base + STAGES * A_BYTES;  // STAGES x 16 KiB
-  uint8_t* sE = sB + STAGES * B_BYTES;     // EPI_BYTES: epilogue staging (1024-aligned)
+  uint8_t* sA = base;                  // NST x 32 KiB
+  uint8_t* sB = base + NST * A_BYTES;  // NST x BST
+  uint8_t* sE = sB + NST * BST;        // EPI_BYTES: epilogue staging (1024-aligned)
   uint64_t* bars = reinterpret_cast<uint64_t*>(sE + EPI_BYTES);
   uint64_t* fullA = bars;
-  uint64_t* fullB = bars + STAGES;
-  uint64_t* empty = bars + 2 * STAGES;
-  uint64_t* accFull = bars + 3 * STAGES;
+  uint64_t* fullB = bars + NST;
+  uint64_t* empty = bars + 2 * NST;
+  uint64_t* accFull = bars + 3 * NST;
   uint64_t* accEmpty = accFull + 1;
   uint64_t* drain = accEmpty + 1;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(drain + 1);
@@ -456,11 +564,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(&fullA[s], 1);
       // mask rows: the 8 / CL local warps of the stage's phase, plus (CL > 1) the
       // expect-tx arrival for the rows the peers' bulk copies deliver
-      mbar_init(&fullB[s], CL > 1 ? GEN_WARPS / CL + 1 : GEN_WARPS);
+      mbar_init(&fullB[s], CL > 1 ? GEN_WARPS / PH + 1 : GEN_WARPS);
       mbar_init(&empty[s], CL);  // MMA completion of every CTA that reads rows this CTA writes
     }
     mbar_init(accFull, 1);
@@ -507,13 +615,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
           mbar_arrive_tx(&fullA[stage], a_bytes);
           bulk_g2s(sA + stage * A_BYTES, Ap + kb * A_BYTES, a_bytes, &fullA[stage]);
           last[stage] = (int)phase;
-          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+          if (++stage == NST) { stage = 0; phase ^= 1; }
         }
       }
       if (*abort_flag) {
         // copies already issued must land before shared memory is released
 #pragma unroll
-        for (int s2 = 0; s2 < STAGES; ++s2) {
+        for (int s2 = 0; s2 < NST; ++s2) {
           if (last[s2] < 0) continue;
           const uint64_t t0 = gtimer();
           while (!mbar_try(&fullA[s2], (uint32_t)last[s2]) && gtimer() - t0 < WAIT_NS) {
@@ -544,24 +652,27 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
               break;
             }
             tc_fence_after();
-            const uint64_t bdesc = sdesc(sB + stage * B_BYTES);
+            const uint64_t bdesc = sdesc(sB + stage * BST);
             const uint64_t adesc = sdesc(sA + stage * A_BYTES);
 #pragma unroll
             for (int ks = 0; ks < BK / 16; ++ks) {
 #pragma unroll
               for (int q = 0; q < TILES; ++q) {
+                // products (A part h, B plane b): K_hi B_hi, K_lo B_hi and, for a
+                // membrane pass, K_hi B_lo
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                  if (h == 1 && a.hi_only) continue;
+                for (int pi = 0; pi < (CX ? 3 : 2); ++pi) {
+                  const int h = pi == 1 ? 1 : 0, b = pi == 2 ? 1 : 0;
+                  if (pi > 0 && a.hi_only) continue;
                   const uint64_t ad = adesc + (uint64_t)(((h * TILES + q) * SUB + ks * 32) >> 4);
-                  const uint64_t bd = bdesc + (uint64_t)((ks * 32) >> 4);
-                  mma_bf16(tmem + (uint32_t)(q * BN), ad, bd, (kb > kb0 || ks > 0 || h > 0) ? 1u : 0u);
+                  const uint64_t bd = bdesc + (uint64_t)((b * B_BYTES + ks * 32) >> 4);
+                  mma_bf16(tmem + (uint32_t)(q * BN), ad, bd, (kb > kb0 || ks > 0 || pi > 0) ? 1u : 0u);
                 }
               }
             }
             if (CL > 1) mma_commit_mc(&empty[stage], (uint16_t)((1u << CL) - 1u));
             else mma_commit(&empty[stage]);
-            if (++stage == STAGES) { stage = 0; phase ^= 1; }
+            if (++stage == NST) { stage = 0; phase ^= 1; }
           }
           if (!ok) break;
           mma_commit(accFull);
@@ -576,10 +687,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
     }
   } else if (warp >= GEN_WARP0) {
     // ---------------- mask generators
-    constexpr int RPC = BN / CL, WPS = GEN_WARPS / CL;
+    // RPC rows of the stripe per CTA in RG groups of 32 (a lane per row); a
+    // phase's WPS warps cover them, each group split into WPS / RG column parts
+    // (one part except for membrane passes)
+    constexpr int RPC = BN / CL, WPS = GEN_WARPS / PH, RG = RPC / 32, NCP = WPS / RG;
     const int gw = warp - GEN_WARP0;
     const int ph = gw / WPS, wr = gw % WPS;
-    const int row = (int)rk * RPC + wr * 32 + lane;  // row of the stripe, 0 .. BN - 1
+    const int cp = wr / RG;                                 // column part: 16-byte chunks [cp, cp + 1) * 4 / NCP
+    const int row = (int)rk * RPC + (wr % RG) * 32 + lane;  // row of the stripe, 0 .. BN - 1
     // 64-byte swizzle, K-major: row at (row/8)*512 + (row%8)*64, 16-byte chunk q at q ^ ((row%8)/2)
     uint8_t* rowbase0 = sB + (row >> 3) * 512 + (row & 7) * 64;
     const int sw = (row & 7) >> 1;
@@ -589,11 +704,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
 #pragma unroll
     for (int s2 = 0; s2 < STAGES; ++s2) last[s2] = -1;
     Walker w;
+    CxRow cxr{};
     uint32_t state = 0;  // CL = 1: open state of the sequential walk
     int64_t cur_unit = -1;
     // The CTA's K blocks in MMA order: unit ui (its stripe's span [klo, klo +
     // nlen)), block offset t within it; block G of the sequence (G = ph, ph +
-    // CL, ...) sits on stage G % STAGES like the loader's and the issuer's.
+    // PH, ...) sits on stage G % NST like the loader's and the issuer's.
     int64_t ui = 0, t = ph, klo = 0, nlen = 1;
     auto unit_span = [&](int64_t u) {
       int64_t hi;
@@ -611,26 +727,27 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
     const bool prefetch = CL > 1 || a.level_mode;
     BlockPrep pre{}, cur{};
     bool have_pre = false;
-    for (int64_t G = ph; ui < my_units; G += CL) {
+    for (int64_t G = ph; ui < my_units; G += PH) {
       const int64_t kb = klo + t;
-      const int stage = (int)(G & (STAGES - 1));
-      const uint32_t phase = (uint32_t)((G / STAGES) & 1);
+      const int stage = (int)(G % NST);
+      const uint32_t phase = (uint32_t)((G / NST) & 1);
       if (ui != cur_unit) {
         cur_unit = ui;
         const int64_t s = (u0 + ui * ustep) % a.n_stripes;
         walker_init(w, a.j_begin + s * BN + row, a.j_end, a.mg, a.level_mode != 0);
+        if constexpr (CX) cx_row_init(a.df, a.j_begin + s * BN + row - a.mg.c, cxr);
         state = 0;
         have_pre = false;
       }
       if (prefetch) {
         if (!have_pre) block_prep(w, kb * BK, a.mg, pre);
         cur = pre;
-        have_pre = t + CL < nlen;
-        if (have_pre) block_prep(w, (kb + CL) * BK, a.mg, pre);
+        have_pre = t + PH < nlen;
+        if (have_pre) block_prep(w, (kb + PH) * BK, a.mg, pre);
       }
       // One thread per phase waits for the stage; the phase's warps take its
       // decision at a named barrier (waiting there issues no instructions).
-      const int slot = 2 * ph + (int)(G / CL & 1);
+      const int slot = 2 * ph + (int)(G / PH & 1);
       if (leader)
         gen_ok[slot] = (CL > 1 ? mbar_wait_cl(&empty[stage], phase ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 5)
                                : mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 5))
@@ -638,9 +755,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
                             : 0;
       named_bar_sync(1 + ph, WPS * 32);
       if (!gen_ok[slot]) break;
-      uint8_t* rowp = rowbase0 + stage * B_BYTES;
+      uint8_t* rowp = rowbase0 + stage * BST;
       uint32_t wd[16];
-      if (a.level_mode) {
+      if constexpr (CX) {
+        // membrane pass: T cos(phi) or T sin(phi), hi and lo planes
+        uint32_t bits = CL == 1 ? walker_bits(w, kb * BK, state, a.mg.thr) : block_finish(w, kb * BK, a.mg, cur);
+        if (a.mg.centre_open) bits = disc_bits(w, kb * BK) & ~bits;
+        cx_store(a.df, cxr, kb * BK - a.mg.c, bits, a.cx_sin, rowp, rowp + B_BYTES, sw, cp * (4 / NCP), 4 / NCP);
+      } else if (a.level_mode) {
         // phase-plate pass: +1 / -1 on the pass's level sets
         uint32_t pb, nb;
         block_values(w, kb * BK, a.mg, cur, a.lmod, a.pos, a.neg, pb, nb);
@@ -652,9 +774,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
         if (a.signed_mask) expand_signed(disc_bits(w, kb * BK), bits, wd);
         else expand_bits(bits, wd);
       }
+      if constexpr (!CX) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        *reinterpret_cast<uint4*>(rowp + ((q ^ sw) << 4)) = make_uint4(wd[4 * q], wd[4 * q + 1], wd[4 * q + 2], wd[4 * q + 3]);
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<uint4*>(rowp + ((q ^ sw) << 4)) =
+              make_uint4(wd[4 * q], wd[4 * q + 1], wd[4 * q + 2], wd[4 * q + 3]);
+      }
       fence_proxy_async();
       if constexpr (CL == 1) {
         __syncwarp();
@@ -663,19 +788,22 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
         // all of this CTA's rows of the stage are written: one thread sends them
         named_bar_sync(1 + ph, WPS * 32);
         if (leader) {
-          const uint32_t off = (uint32_t)(stage * B_BYTES + rk * RPC * 64);
-          mbar_arrive_tx(&fullB[stage], (uint32_t)((CL - 1) * RPC * 64));  // the peers' rows land here
+          constexpr int NPL = CX ? 2 : 1;  // B planes per stage
+          const uint32_t off = (uint32_t)(stage * BST + rk * RPC * 64);
+          mbar_arrive_tx(&fullB[stage], (uint32_t)((CL - 1) * RPC * 64 * NPL));  // the peers' rows land here
 #pragma unroll
           for (int q = 1; q < CL; ++q) {
             const uint32_t peer = (rk + (uint32_t)q) % (uint32_t)CL;
-            bulk_s2peer(mapa(smem_u32(sB + off), peer), sB + off, (uint32_t)(RPC * 64),
-                        mapa(smem_u32(&fullB[stage]), peer));
+#pragma unroll
+            for (int pl = 0; pl < NPL; ++pl)
+              bulk_s2peer(mapa(smem_u32(sB + off + pl * B_BYTES), peer), sB + off + pl * B_BYTES,
+                          (uint32_t)(RPC * 64), mapa(smem_u32(&fullB[stage]), peer));
           }
           last[stage] = (int)phase;
         }
         if (lane == 0) mbar_arrive(&fullB[stage]);
       }
-      t += CL;
+      t += PH;
       while (ui < my_units && t >= nlen) {
         t -= nlen;
         if (++ui < my_units) unit_span(ui);
@@ -686,7 +814,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
         // after an abort the peers' copies already issued must land before this
         // CTA's shared memory is released (bounded: a peer may have stopped first)
 #pragma unroll
-        for (int s2 = 0; s2 < STAGES; ++s2) {
+        for (int s2 = 0; s2 < NST; ++s2) {
           if (last[s2] < 0) continue;
           const uint64_t t0 = gtimer();
           while (!mbar_try_cl(&fullB[s2], (uint32_t)last[s2]) && gtimer() - t0 < WAIT_NS) {
@@ -879,6 +1007,8 @@ __global__ void k_mask_blocks(MaskGeom mg, int64_t N, int64_t j0, int64_t rows, 
   }
 }
 
+// Both variants take the same shared memory: 4 x (32 + 16) KiB or 3 x (32 + 32) KiB.
+static_assert(STAGES * (A_BYTES + B_BYTES) == STAGES_CX * (A_BYTES + 2 * B_BYTES), "stage layouts");
 size_t dense_smem_bytes() { return 1024 + STAGES * (A_BYTES + B_BYTES) + EPI_BYTES + 256; }
 
 // 2-D FP32 tensor map of the row intermediate: x = C1 column (aperture row of
@@ -919,10 +1049,13 @@ fzp_status dense_layout(Plan& P, FormSizes* out) {
   FZP_CUDA_TRY(cudaGetDevice(&dev));
   FZP_CUDA_TRY(cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev));
   out->A = (size_t)d.npairs * (size_t)d.kblocks * A_BYTES;
-  static std::atomic<uint64_t> attr1{0}, attr2{0}, attr4{0};
-  FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<1>, (int)dense_smem_bytes(), attr1));
-  FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<2>, (int)dense_smem_bytes(), attr2));
-  FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<4>, (int)dense_smem_bytes(), attr4));
+  static std::atomic<uint64_t> attr1{0}, attr2{0}, attr4{0}, attr1c{0}, attr2c{0}, attr4c{0};
+  FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<1, false>, (int)dense_smem_bytes(), attr1));
+  FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<2, false>, (int)dense_smem_bytes(), attr2));
+  FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<4, false>, (int)dense_smem_bytes(), attr4));
+  FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<1, true>, (int)dense_smem_bytes(), attr1c));
+  FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<2, true>, (int)dense_smem_bytes(), attr2c));
+  FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<4, true>, (int)dense_smem_bytes(), attr4c));
   // The kernel is persistent: launch only CTAs that are resident at once.  A
   // cluster must fit in one GPC, so with clusters fewer than all SMs may hold one.
   d.max_ctas = d.num_sms;
@@ -939,8 +1072,8 @@ fzp_status dense_layout(Plan& P, FormSizes* out) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int nclusters = 0;
-    if (d.cluster == 2) FZP_CUDA_TRY(cudaOccupancyMaxActiveClusters(&nclusters, k_dense<2>, &cfg));
-    else FZP_CUDA_TRY(cudaOccupancyMaxActiveClusters(&nclusters, k_dense<4>, &cfg));
+    if (d.cluster == 2) FZP_CUDA_TRY(cudaOccupancyMaxActiveClusters(&nclusters, k_dense<2, false>, &cfg));
+    else FZP_CUDA_TRY(cudaOccupancyMaxActiveClusters(&nclusters, k_dense<4, false>, &cfg));
     if (nclusters < 1) return set_error(FZP_E_UNSUPPORTED, "no %d-CTA cluster of the dense kernel fits", d.cluster);
     d.max_ctas = std::min(nclusters * d.cluster, d.num_sms / d.cluster * d.cluster);
   }
@@ -997,11 +1130,16 @@ fzp_status dense_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
   a.npairs = d.npairs;
   a.M = P.M;
   a.signed_mask = P.levels == 2 ? 1 : 0;
-  a.level_mode = P.pass_index >= 0 ? 1 : 0;
+  const bool cx = P.pass_index >= 0 && P.passes[P.pass_index].cx >= 0;
+  a.level_mode = P.pass_index >= 0 && !cx ? 1 : 0;
   a.lmod = P.levels > 0 ? P.levels : 2;
-  if (P.pass_index >= 0) {
+  if (P.pass_index >= 0 && !cx) {
     a.pos = P.passes[P.pass_index].pos;
     a.neg = P.passes[P.pass_index].neg;
+  }
+  if (cx) {
+    a.cx_sin = P.passes[P.pass_index].cx;
+    a.df = deform_coef(P);
   }
   a.promote = d.promote_kblocks;
   a.hi_only = P.precision == FZP_PREC_BF16 ? 1 : 0;
@@ -1033,10 +1171,17 @@ fzp_status dense_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (CL == 2) FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<2>, a, tm));
-    else FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<4>, a, tm));
+    if (cx) {
+      if (CL == 2) FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<2, true>, a, tm));
+      else FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<4, true>, a, tm));
+    } else {
+      if (CL == 2) FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<2, false>, a, tm));
+      else FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<4, false>, a, tm));
+    }
+  } else if (cx) {
+    k_dense<1, true><<<grid, NUM_THREADS, dense_smem_bytes(), s>>>(a, tm);
   } else {
-    k_dense<1><<<grid, NUM_THREADS, dense_smem_bytes(), s>>>(a, tm);
+    k_dense<1, false><<<grid, NUM_THREADS, dense_smem_bytes(), s>>>(a, tm);
   }
   prof_end(P, s);
   P.launches += 1;

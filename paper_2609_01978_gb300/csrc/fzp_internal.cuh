@@ -90,6 +90,25 @@ __device__ __forceinline__ bool mask_open(int64_t dj, int64_t di, const MaskGeom
 }
 
 // --------------------------------------------------------------------------
+// Membrane deformation phase in turns, 2 w / lambda (phi / 2 pi, phi = (4 pi /
+// lambda) w), as FP32 coefficients in sample units (di = i - c, dj = j - c):
+//   amp2 sin(2 pi (di kx + dj ky)) (1 - tq (di^2 + dj^2)) + sum_k h2_k exp(-q_k d_k^2),
+//   d_k = (di - pi_k) nx_k + (dj - pj_k) ny_k  ((pi_k, pj_k) on the k-th crease).
+// kx, ky are split hi + lo with hi a multiple of 2^-14: for |di| < 2^20 and the
+// configured wrinkle periods (>= 1 mm at sub-micron pitch) di * kxh is exact in
+// FP32, so the integer turns drop exactly before the sine.
+// --------------------------------------------------------------------------
+struct DeformCoef {
+  float kxh, kxl, kyh, kyl, amp2, tq;
+  int n;
+  float nx[3], ny[3], pi_[3], pj[3], q[3], h2[3];
+  // steps along a row (di -> di + 1) for generators that walk columns:
+  // the wrinkle phasor turns by e^{2 pi i kx}; a ridge's ratio g(di+1)/g(di)
+  // is multiplied by rho_k = exp(-2 q_k nx_k^2)
+  float zc, zs, rho[3];
+};
+
+// --------------------------------------------------------------------------
 // Phase helpers.  Phases are carried in turns; the integer part is removed in
 // FP64 before the (co)sine is evaluated.
 // --------------------------------------------------------------------------
@@ -161,6 +180,7 @@ struct Bluestein {
 struct MaskPass {
   uint64_t pos = 0, neg = 0;
   double wr = 1.0, wi = 0.0;
+  int cx = -1;  // membrane deformation (complex T e^{i phi}): 0 -> mask T cos(phi), 1 -> T sin(phi)
 };
 
 struct Dense {
@@ -213,6 +233,9 @@ struct Plan {
   size_t prof_used = 0;
   const char* dominant = "";
 };
+
+// FP32 deformation coefficients of a plan with a deformation (host).
+DeformCoef deform_coef(const Plan& P);
 
 // Bracket one launch of the dominant kernel with events (no-op unless profiling).
 void prof_begin(Plan& P, cudaStream_t s);

@@ -204,10 +204,30 @@ fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
     P.passes.push_back(mp);
   }
   if (in->deform) {
-    if (P.form == FZP_FORM_DENSE)
-      return set_error(FZP_E_UNSUPPORTED, "deformation phase is supported by the Bluestein form only");
+    const fzp_deform& d = *in->deform;
+    bool ok = d.period > 0 && std::isfinite(d.period) && std::isfinite(d.amp) && std::isfinite(d.theta) &&
+              std::isfinite(d.taper);
+    for (int k = 0; k < d.n_ridges; ++k)
+      ok = ok && d.ridge_width[k] > 0 && std::isfinite(d.ridge_width[k]) && std::isfinite(d.ridge_h[k]) &&
+           std::isfinite(d.ridge_px[k]) && std::isfinite(d.ridge_py[k]) && std::isfinite(d.ridge_alpha[k]);
+    if (!ok) return set_error(FZP_E_INVALID, "deformation: period and ridge widths must be positive, all finite");
+    if (P.form == FZP_FORM_DENSE && P.levels >= 2)
+      return set_error(FZP_E_UNSUPPORTED, "dense form: a deformed membrane must be a binary amplitude plate");
     P.has_deform = true;
-    P.deform = *in->deform;
+    P.deform = d;
+    if (P.form == FZP_FORM_DENSE) {
+      // complex transmission T e^{i phi}: the real masks T cos(phi) and T sin(phi)
+      // in two passes, their fields weighted 1 and i (the centre configuration
+      // is applied by the membrane generator itself)
+      P.passes.clear();
+      MaskPass re, im;
+      re.cx = 0;
+      im.cx = 1;
+      im.wr = 0.0;
+      im.wi = 1.0;
+      P.passes.push_back(re);
+      P.passes.push_back(im);
+    }
   }
   P.stripe_rows = in->stripe_rows;
   P.promote_req = in->promote;

@@ -59,7 +59,8 @@ def test_batch_graph_matches_single_plans_and_oracle(env):
         Iref = np.abs(O.field_czt(g)) ** 2
         tol = 1e-6 if info["precision"] == fzp.PREC_FP64 else 1e-4
         assert rel_l2(np.abs(first[i]) ** 2, Iref) <= tol, (i, info["form"], info["precision"])
-    assert b.info(2)["form"] == fzp.FORM_BLUESTEIN  # deformed: only the Bluestein form applies
+    # deformed binary plate: both forms are candidates; the autotuner keeps the faster
+    assert b.info(2)["form"] in (fzp.FORM_BLUESTEIN, fzp.FORM_DENSE)
     m = b.metrics(0, fields[0])
     assert m["aperture_count"] > 0
     b.close()
