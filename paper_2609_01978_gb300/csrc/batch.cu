@@ -256,6 +256,7 @@ fzp_status fzp_batch_plan(const fzp_params* params, int n, fzp_batch_t* out) {
     if (st != FZP_OK) { batch_release(b); return st; }
     mx.pre = std::max(mx.pre, z.pre); mx.H = std::max(mx.H, z.H); mx.tab = std::max(mx.tab, z.tab);
     mx.Z = std::max(mx.Z, z.Z); mx.G = std::max(mx.G, z.G); mx.A = std::max(mx.A, z.A);
+    mx.sched = std::max(mx.sched, z.sched);
     const size_t rowsC1 = (size_t)((2 * (int64_t)P->M + 511) / 512 * 512) * (size_t)P->chunk_rows;
     if (P->precision == FZP_PREC_FP64) c1d = std::max(c1d, rowsC1 * 8);
     else c1 = std::max(c1, rowsC1 * 4);
@@ -271,9 +272,10 @@ fzp_status fzp_batch_plan(const fzp_params* params, int n, fzp_batch_t* out) {
     return q;
   };
   void *pre = alloc(mx.pre), *H = alloc(mx.H), *tab = alloc(mx.tab), *Z = alloc(mx.Z), *G = alloc(mx.G),
-       *A = alloc(mx.A), *C1 = alloc(c1), *C1d = alloc(c1d), *U = alloc(uacc), *M = alloc(metr),
+       *A = alloc(mx.A), *sched = alloc(mx.sched), *C1 = alloc(c1), *C1d = alloc(c1d), *U = alloc(uacc), *M = alloc(metr),
        *err = alloc(sizeof(int));
   if ((mx.pre && !pre) || (mx.H && !H) || (mx.tab && !tab) || (mx.Z && !Z) || (mx.G && !G) || (mx.A && !A) ||
+      (mx.sched && !sched) ||
       (c1 && !C1) || (c1d && !C1d) || !U || !M || !err) {
     cudaGetLastError();
     batch_release(b);
@@ -283,6 +285,7 @@ fzp_status fzp_batch_plan(const fzp_params* params, int n, fzp_batch_t* out) {
   for (fzp_plan_s* P : b->inst) {
     P->bs.d_pre = pre; P->bs.d_H = H; P->bs.d_tab = tab; P->bs.d_Z = Z; P->bs.d_G = G;
     P->dn.d_A = A;
+    P->dn.d_sched = reinterpret_cast<int*>(sched);
     P->d_C1 = reinterpret_cast<float*>(C1);
     P->d_C1d = reinterpret_cast<double*>(C1d);
     P->d_Uacc = reinterpret_cast<double2*>(U);

@@ -78,6 +78,8 @@ struct DenseArgs {
   int64_t kblocks;          // ceil(N / BK)
   int64_t j_begin, j_end;   // aperture rows of this launch [j_begin, j_end)
   int64_t n_stripes;        // ceil((j_end - j_begin) / BN)
+  const int* sched;         // work list (k_dense_sched): off[nchunks + 1], slo[nchunks], cnt[nchunks]
+  int nchunks;              // ceil(kblocks / promote): K chunks of the work list
   int npairs;               // kernel tile pairs (items per stripe; a multiple of the cluster size)
   int M;                    // ROI side: tiles t with 64 t >= M are zero padding, not stored
   int signed_mask;          // 1: binary phase plate, T = +1 / -1 on even / odd zones inside the disc
@@ -400,6 +402,92 @@ __device__ __forceinline__ void stripe_kspan(const DenseArgs& a, int64_t s, int6
   if (khi <= klo) khi = klo + 1;
 }
 
+// Work units in chunk-major order: unit (g, pair group pu, stripe s) covers the
+// K blocks of chunk g, [g P, (g + 1) P) with P = promote, that meet stripe s's
+// disc chord; units of one chunk are consecutive, so the clusters of a wave read
+// the same kernel-matrix blocks (one fetch from HBM, the rest from L2) while each
+// unit still ends with one promotion of its accumulators into C1 (reduce-add).
+// Per chunk g the stripes meeting it are a contiguous range [slo_g, slo_g +
+// cnt_g) (the chords are nested about the stripe nearest the axis); off_g counts
+// the units before chunk g.
+struct Unit {
+  int64_t s, pu, kb0, kb1;
+};
+
+__device__ __forceinline__ Unit unit_at(const DenseArgs& a, int64_t it, int npg) {
+  const int* off = a.sched;
+  const int* slo = a.sched + a.nchunks + 1;
+  const int* cnt = slo + a.nchunks;
+  int lo = 0, hi = a.nchunks - 1;  // largest g with off[g] <= it
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((int64_t)__ldg(off + mid) <= it) lo = mid;
+    else hi = mid - 1;
+  }
+  const int g = lo;
+  const int64_t r = it - __ldg(off + g), c = __ldg(cnt + g);
+  Unit u;
+  u.pu = r / c;
+  u.s = __ldg(slo + g) + r % c;
+  int64_t klo, khi;
+  stripe_kspan(a, u.s, klo, khi);
+  const int64_t c0 = (int64_t)g * a.promote, c1 = c0 + a.promote;
+  u.kb0 = klo > c0 ? klo : c0;
+  u.kb1 = khi < c1 ? khi : c1;
+  (void)npg;
+  return u;
+}
+
+// Builds the work list of one k_dense launch (one block).  For each chunk g the
+// stripes meeting it are found by bisection on either side of the stripe
+// nearest the axis, whose chord holds every other stripe's.
+__global__ void k_dense_sched(const DenseArgs a, int npg, int* sched) {
+  int* off = sched;
+  int* slo = sched + a.nchunks + 1;
+  int* cnt = slo + a.nchunks;
+  const int64_t ns = a.n_stripes;
+  int64_t sc = (a.mg.c - a.j_begin) / BN;
+  sc = a.mg.c < a.j_begin ? 0 : (sc >= ns ? ns - 1 : sc);
+  for (int g = threadIdx.x; g < a.nchunks; g += blockDim.x) {
+    const int64_t c0 = (int64_t)g * a.promote, c1 = c0 + a.promote;
+    auto meets = [&](int64_t st) {
+      int64_t klo, khi;
+      stripe_kspan(a, st, klo, khi);
+      return klo < c1 && khi > c0;
+    };
+    if (!meets(sc)) {
+      slo[g] = (int)sc;
+      cnt[g] = 0;
+      continue;
+    }
+    int64_t lo = 0, hi = sc;  // first stripe in [0, sc] that meets the chunk
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (meets(mid)) hi = mid;
+      else lo = mid + 1;
+    }
+    const int64_t first = lo;
+    lo = sc;
+    hi = ns - 1;  // last stripe in [sc, ns) that meets it
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if (meets(mid)) lo = mid;
+      else hi = mid - 1;
+    }
+    slo[g] = (int)first;
+    cnt[g] = (int)(lo - first + 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t acc = 0;
+    for (int g = 0; g < a.nchunks; ++g) {
+      off[g] = (int)acc;
+      acc += (int64_t)cnt[g] * npg;
+    }
+    off[a.nchunks] = (int)acc;
+  }
+}
+
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
   uint32_t d;
   asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
@@ -590,7 +678,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
   const uint32_t rk = CL > 1 ? cluster_rank() : 0u;
   if (CL > 1) cluster_sync();  // peers' barriers are initialised before any remote arrive
 
-  const int64_t n_items = a.n_stripes * (a.npairs / CL);  // units of this cluster
+  const int npg = a.npairs / CL;                           // pair groups per stripe
+  const int64_t n_items = __ldg(a.sched + a.nchunks);     // units of the work list
   const int64_t u0 = blockIdx.x / CL, ustep = gridDim.x / CL;
   const int64_t nkb = a.kblocks;
   const uint32_t a_bytes = a.hi_only ? A_BYTES / 2 : A_BYTES;
@@ -604,11 +693,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
 #pragma unroll
       for (int s2 = 0; s2 < STAGES; ++s2) last[s2] = -1;
       for (int64_t it = u0; it < n_items && !*abort_flag; it += ustep) {
-        const int64_t pr = (it / a.n_stripes) * CL + rk;
+        const Unit un = unit_at(a, it, npg);
+        const int64_t pr = un.pu * CL + rk;
         const uint8_t* Ap = a.A + pr * nkb * A_BYTES;
-        int64_t klo, khi;
-        stripe_kspan(a, it % a.n_stripes, klo, khi);
-        for (int64_t kb = klo; kb < khi; ++kb) {
+        for (int64_t kb = un.kb0; kb < un.kb1; ++kb) {
           if (!(CL > 1 ? mbar_wait_cl(&empty[stage], phase ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 1)
                        : mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 1)))
             break;
@@ -636,14 +724,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
       uint32_t phase = 0, accph = 0;
       bool ok = true;
       for (int64_t it = u0; it < n_items && ok; it += ustep) {
-        int64_t klo, khi;
-        stripe_kspan(a, it % a.n_stripes, klo, khi);
-        const int64_t nch = (khi - klo + a.promote - 1) / a.promote;
-        for (int64_t ch = 0; ch < nch && ok; ++ch) {
-          // the epilogue has drained both accumulators of the previous chunk
+        const Unit un = unit_at(a, it, npg);
+        {
+          // the epilogue has drained both accumulators of the previous unit
           if (!mbar_wait(accEmpty, accph ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 2)) { ok = false; break; }
           tc_fence_after();
-          const int64_t kb0 = klo + ch * a.promote, kb1 = kb0 + a.promote < khi ? kb0 + a.promote : khi;
+          const int64_t kb0 = un.kb0, kb1 = un.kb1;
           for (int64_t kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait(&fullA[stage], phase, abort_flag, a.err, ERR_TIMEOUT_BASE + 3) ||
                 !(CL > 1 ? mbar_wait_cl(&fullB[stage], phase, abort_flag, a.err, ERR_TIMEOUT_BASE + 4)
@@ -710,11 +796,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
     // The CTA's K blocks in MMA order: unit ui (its stripe's span [klo, klo +
     // nlen)), block offset t within it; block G of the sequence (G = ph, ph +
     // PH, ...) sits on stage G % NST like the loader's and the issuer's.
-    int64_t ui = 0, t = ph, klo = 0, nlen = 1;
+    int64_t ui = 0, t = ph, klo = 0, nlen = 1, ustripe = 0;
     auto unit_span = [&](int64_t u) {
-      int64_t hi;
-      stripe_kspan(a, (u0 + u * ustep) % a.n_stripes, klo, hi);
-      nlen = hi - klo;
+      const Unit un = unit_at(a, u0 + u * ustep, npg);
+      klo = un.kb0;
+      nlen = un.kb1 - un.kb0;
+      ustripe = un.s;
     };
     if (my_units > 0) unit_span(0);
     while (ui < my_units && t >= nlen) {
@@ -733,10 +820,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
       const uint32_t phase = (uint32_t)((G / NST) & 1);
       if (ui != cur_unit) {
         cur_unit = ui;
-        const int64_t s = (u0 + ui * ustep) % a.n_stripes;
+        const int64_t s = ustripe;
         walker_init(w, a.j_begin + s * BN + row, a.j_end, a.mg, a.level_mode != 0);
         if constexpr (CX) cx_row_init(a.df, a.j_begin + s * BN + row - a.mg.c, cxr);
         state = 0;
+        if constexpr (CL == 1) {
+          // the sequential walk starts at the unit's first block: skip the
+          // events before it; the open state there is their parity
+          if (w.ne > 0) {
+            const int32_t e = walker_count(w, klo * BK - 1, a.mg);
+            w.e = e;
+            w.next = walker_event(w, e, a.mg.thr);
+            state = (uint32_t)(e & 1);
+          }
+        }
         have_pre = false;
       }
       if (prefetch) {
@@ -831,23 +928,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
     uint32_t accph = 0;
     bool ok = true;
     for (int64_t it = u0; it < n_items && ok; it += ustep) {
-      const int64_t pr = (it / a.n_stripes) * CL + rk;
-      const int64_t s = it % a.n_stripes;
+      const Unit un = unit_at(a, it, npg);
+      const int64_t pr = un.pu * CL + rk;
+      const int64_t s = un.s;
       // zero-padding tiles (64 t >= M) have no rows in C1: nothing is stored
       const bool live = (pr * TILES + q) * 64 < (int64_t)a.M;
       const int x0 = (int)(a.j_begin + s * BN - a.c1_j0);       // C1 column of the stripe's first row
       const int y0 = (int)((pr * TILES + q) * BM + (warp & 3) * 32);  // C1 row of lane 0
-      int64_t klo, khi;
-      stripe_kspan(a, s, klo, khi);
-      const int64_t nch = (khi - klo + a.promote - 1) / a.promote;
-      for (int64_t ch = 0; ch < nch; ++ch) {
+      {
         // thread 0 waits for the accumulators; the 8 warps meet at a named barrier
         if (threadIdx.x == 0) epi_ok[accph] = mbar_wait(accFull, accph, abort_flag, a.err, ERR_TIMEOUT_BASE + 6) ? 1 : 0;
         named_bar_sync(1 + 4, EPI_WARPS * 32);
         if (!epi_ok[accph]) { ok = false; break; }
         tc_fence_after();
         const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(q * BN);
-        if (ch == 1 && lane == 0) bulk_wait0();  // the unit's stores have landed before the first add
 #pragma unroll 1
         for (int col = 0; col < (live ? BN : 0); col += EPI_BOX) {
           float v[32];
@@ -861,8 +955,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
           fence_proxy_async();
           __syncwarp();
           if (lane == 0) {
-            if (ch == 0) tma_store_2d(&tmC1, eb, x0 + col, y0);
-            else tma_reduce_add_2d(&tmC1, eb, x0 + col, y0);
+            tma_reduce_add_2d(&tmC1, eb, x0 + col, y0);  // C1 was zeroed before the launch
             bulk_commit();
           }
         }
@@ -1049,6 +1142,7 @@ fzp_status dense_layout(Plan& P, FormSizes* out) {
   FZP_CUDA_TRY(cudaGetDevice(&dev));
   FZP_CUDA_TRY(cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev));
   out->A = (size_t)d.npairs * (size_t)d.kblocks * A_BYTES;
+  out->sched = sizeof(int) * (size_t)(3 * ((d.kblocks + d.promote_kblocks - 1) / d.promote_kblocks) + 1);
   static std::atomic<uint64_t> attr1{0}, attr2{0}, attr4{0}, attr1c{0}, attr2c{0}, attr4c{0};
   FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<1, false>, (int)dense_smem_bytes(), attr1));
   FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<2, false>, (int)dense_smem_bytes(), attr2));
@@ -1094,7 +1188,8 @@ fzp_status dense_build_tables(Plan& P) {
   fzp_status st = dense_layout(P, &z);
   if (st != FZP_OK) return st;
   FZP_CUDA_TRY(cudaMalloc(&P.dn.d_A, z.A));
-  P.device_bytes += z.A;
+  FZP_CUDA_TRY(cudaMalloc(&P.dn.d_sched, z.sched));
+  P.device_bytes += z.A + z.sched;
   return dense_fill_tables(P, 0);
 }
 
@@ -1148,9 +1243,15 @@ fzp_status dense_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
   a.c1_stride = P.chunk_rows;
   a.c1_j0 = j0;
   a.err = P.d_err;
-  const int64_t units = a.n_stripes * (a.npairs / CL);
-  const int64_t max_ctas = d.max_ctas;
-  const int grid = (int)std::min<int64_t>(units * CL, max_ctas);
+  a.nchunks = (int)((d.kblocks + d.promote_kblocks - 1) / d.promote_kblocks);
+  a.sched = d.d_sched;
+  // every unit adds its promotion into C1 (units of one stripe run in any order)
+  FZP_CUDA_TRY(cudaMemsetAsync(P.d_C1, 0, (size_t)P.c1_rows * (size_t)P.chunk_rows * sizeof(float), s));
+  k_dense_sched<<<1, 1024, 0, s>>>(a, a.npairs / CL, d.d_sched);
+  P.launches += 1;
+  FZP_CUDA_TRY(cudaGetLastError());
+  // a grid of every resident cluster (the work list's length is known on the device only)
+  const int grid = d.max_ctas;
   CUtensorMap tm;
   {
     const fzp_status st = c1_tensor_map(P, &tm);

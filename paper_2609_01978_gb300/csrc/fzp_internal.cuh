@@ -192,6 +192,7 @@ struct Dense {
   int cluster = 1;         // CTAs per cluster sharing each mask tile
   int num_sms = 0;
   int max_ctas = 0;        // CTAs that can be resident at once (whole clusters)
+  int* d_sched = nullptr;  // work list of a row-pass launch (3 nchunks + 1 ints)
 };
 
 struct Plan {
@@ -245,7 +246,7 @@ void prof_end(Plan& P, cudaStream_t s);
 // Form layouts: sizes in bytes of the form's tables and transform workspace.
 struct FormSizes {
   size_t pre = 0, H = 0, tab = 0, Z = 0, G = 0;  // Bluestein
-  size_t A = 0;                                  // dense
+  size_t A = 0, sched = 0;                       // dense
 };
 fzp_status bluestein_layout(Plan& P, FormSizes* out);
 fzp_status bluestein_fill_tables(Plan& P, cudaStream_t s);  // buffers already assigned

@@ -83,7 +83,7 @@ void release_plan(Plan* P) {
   if (P->d_thr) cudaFree(P->d_thr);
   if (P->owns_buffers) {
     void* ptrs[] = {P->d_C1, P->d_C1d, P->d_Uacc, P->d_err, P->d_metrics,
-                    P->bs.d_pre, P->bs.d_H, P->bs.d_Z, P->bs.d_G, P->bs.d_tab, P->dn.d_A};
+                    P->bs.d_pre, P->bs.d_H, P->bs.d_Z, P->bs.d_G, P->bs.d_tab, P->dn.d_A, P->dn.d_sched};
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }
