@@ -83,8 +83,8 @@ KERNEL_SOURCES = {
     "bluestein": ["bluestein.cu", "fzp_internal.cuh"],
 }
 TRAFFIC = {
-    ("fzp-d0.25m", "dense"): (823.07e9 + 98.34e9,
-                              "d356299ae7132297e56c43436390ef7695f065076395d89b1ebccbbf82f3bfa3"),
+    ("fzp-d0.25m", "dense"): (82.608e9 + 79.682e9,
+                              "44a8a75ba5b1d7274c10bff31019ec239016b446b28da4aef503d52a8bc189e0"),
 }
 METRIC = "aperture Gsamples/s into 512² ROI, split-BF16 vs FP32 CZT at ≤1e-4 PSF error"
 UNIT = "Gsamples/s"

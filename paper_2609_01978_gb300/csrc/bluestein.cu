@@ -473,6 +473,158 @@ __global__ void __launch_bounds__(RT) k_f2_r16(RowArgs a, int mode) {
   }
 }
 
+// ---------------------------------------------------------------- FP32 pass F2, radix 8
+// L2 = 4096 = 8^4 points, 512 threads x 8 values in registers, Stockham
+// order (pass s, Ns = 8^s: x_r = in[j + 512 r] times W_{8 Ns}^{r k}, k = j mod
+// Ns, 8-point DFT, y_q -> out[(j / Ns) 8 Ns + q Ns + k]).  After the forward
+// passes thread j holds Y[j + 512 q], the layout the inverse's first pass
+// reads, so the product with H needs no exchange; the inverse's last pass
+// (Ns = 512) evaluates only the outputs q < ceil(M / 512) it keeps.  Shared
+// memory (padded one element per 8 against bank conflicts) carries the three
+// exchanges of each transform.  Twiddles: W^k, W^{2k}, W^{4k} from the table,
+// the other four by products.
+constexpr int R8T = 512;
+__device__ __forceinline__ int pidx8(int i) { return i + (i >> 3); }
+
+__device__ __forceinline__ void dft8(float2 (&v)[8], bool inv) {
+  // radix 2 x 4: two 4-point DFTs on the even and odd inputs, then W_8^q
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4(e0, e1, e2, e3, inv);
+  dft4(o0, o1, o2, o3, inv);
+  const float h = 0.70710678118654752f;
+  // o_q times W_8^{q} (forward e^{-2 pi i q / 8}; inverse conjugate)
+  const float sg = inv ? 1.0f : -1.0f;
+  float2 t1 = make_float2(h * (o1.x - sg * o1.y), h * (o1.y + sg * o1.x));  // W^1
+  float2 t2 = make_float2(-sg * o2.y, sg * o2.x);                           // W^2 = -+i
+  float2 t3 = make_float2(h * (-o3.x - sg * o3.y), h * (-o3.y + sg * o3.x)); // W^3
+  v[0] = make_float2(e0.x + o0.x, e0.y + o0.y);
+  v[4] = make_float2(e0.x - o0.x, e0.y - o0.y);
+  v[1] = make_float2(e1.x + t1.x, e1.y + t1.y);
+  v[5] = make_float2(e1.x - t1.x, e1.y - t1.y);
+  v[2] = make_float2(e2.x + t2.x, e2.y + t2.y);
+  v[6] = make_float2(e2.x - t2.x, e2.y - t2.y);
+  v[3] = make_float2(e3.x + t3.x, e3.y + t3.y);
+  v[7] = make_float2(e3.x - t3.x, e3.y - t3.y);
+}
+
+// v[r] *= W_{8 Ns}^{r k} (forward) or its conjugate; tw[t] = e^{-2 pi i t / 4096}.
+__device__ __forceinline__ void twiddle8(float2 (&v)[8], int k, int step, const float2* __restrict__ tw, bool inv) {
+  if (k == 0) return;
+  float2 w1 = __ldg(tw + k * step), w2 = __ldg(tw + 2 * k * step), w4 = __ldg(tw + 4 * k * step);
+  if (inv) { w1.y = -w1.y; w2.y = -w2.y; w4.y = -w4.y; }
+  const float2 w3 = cmul(w1, w2), w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
+  v[1] = cmul(v[1], w1); v[2] = cmul(v[2], w2); v[3] = cmul(v[3], w3); v[4] = cmul(v[4], w4);
+  v[5] = cmul(v[5], w5); v[6] = cmul(v[6], w6); v[7] = cmul(v[7], w7);
+}
+
+// One Stockham pass with the exchange that feeds the next: twiddle, DFT,
+// scatter to shared memory, gather the next pass's inputs.
+__device__ __forceinline__ void r8_pass(float2 (&v)[8], float2* sm, int Ns, const float2* __restrict__ tw, bool inv) {
+  const int j = threadIdx.x;
+  const int k = j & (Ns - 1);
+  twiddle8(v, k, 512 / Ns, tw, inv);
+  dft8(v, inv);
+  const int base = (j / Ns) * 8 * Ns + k;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) sm[pidx8(base + q * Ns)] = v[q];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = sm[pidx8(j + R8T * q)];
+  __syncthreads();
+}
+
+// mode 0: row transform; mode 1: forward FFT only, natural order -> Z row (table build).
+__global__ void __launch_bounds__(R8T, 2) k_f2_r8(RowArgs a, int mode) {
+  __shared__ float2 sm[RL + RL / 8];
+  const int j = threadIdx.x;
+  const int64_t k1 = blockIdx.x, r = blockIdx.y, row = a.j0 + r;
+  const float2* tw = reinterpret_cast<const float2*>(a.tw);
+  float2 v[8];
+  if (a.L1 == 1) {
+    const float2* pre = reinterpret_cast<const float2*>(a.pre);
+    const float2* vin = reinterpret_cast<const float2*>(a.vin);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int n = j + R8T * q;
+      if (mode == 0) {
+        float2 x = aperture<float>(a, row, n);
+        if (x.x != 0.f || x.y != 0.f) x = cmul(x, pre[n]);
+        v[q] = x;
+      } else {
+        v[q] = vin[n];
+      }
+    }
+  } else {
+    const float2* Z = reinterpret_cast<const float2*>(a.Z) + r * a.L + k1 * RL;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = Z[j + R8T * q];
+  }
+  // forward: passes Ns = 1, 8, 64 with exchanges, then Ns = 512 in registers
+  r8_pass(v, sm, 1, tw, false);
+  r8_pass(v, sm, 8, tw, false);
+  r8_pass(v, sm, 64, tw, false);
+  twiddle8(v, j, 1, tw, false);
+  dft8(v, false);  // thread j now holds Y[j + 512 q] in v[q]
+  if (mode == 1) {
+    float2* out = reinterpret_cast<float2*>(a.Z) + r * a.L + k1 * RL;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) out[q * R8T + j] = v[q];
+    return;
+  }
+  const float2* H = reinterpret_cast<const float2*>(a.H) + k1 * RL;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = cmul(v[q], __ldg(H + q * R8T + j));
+  // inverse: passes Ns = 1, 8, 64, then the kept outputs of Ns = 512
+  r8_pass(v, sm, 1, tw, true);
+  r8_pass(v, sm, 8, tw, true);
+  r8_pass(v, sm, 64, tw, true);
+  twiddle8(v, j, 1, tw, true);
+  // outputs m = q * 512 + j < M: y_q = sum_r v_r W_8^{-r q} (inverse sign)
+  const int nq = (a.M + R8T - 1) / R8T;
+  float2 y[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    y[q] = make_float2(0.f, 0.f);
+    if (q < nq) {
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) {
+        float sn, cs;
+        // W_8^{-r q} = e^{+2 pi i r q / 8}: exact for r q mod 8 in {0, 2, 4, 6}; 1/sqrt(2) otherwise
+        const int t = (rr * q) & 7;
+        const float h = 0.70710678118654752f;
+        const float ct[8] = {1.f, h, 0.f, -h, -1.f, -h, 0.f, h};
+        const float st[8] = {0.f, h, 1.f, h, 0.f, -h, -1.f, -h};
+        cs = ct[t];
+        sn = st[t];
+        y[q].x += v[rr].x * cs - v[rr].y * sn;
+        y[q].y += v[rr].x * sn + v[rr].y * cs;
+      }
+    }
+  }
+  if (a.L1 == 1) {
+    const float2* post = reinterpret_cast<const float2*>(a.post);
+    float* C1 = reinterpret_cast<float*>(a.C1);
+    const int64_t jl = row - a.c1_j0;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int m = q * R8T + j;
+      if (q < nq && m < a.M) {
+        const float2 z = cmul(y[q], post[m]);
+        C1[(int64_t)c1_row_re(m) * a.c1_stride + jl] = z.x;
+        C1[(int64_t)c1_row_im(m) * a.c1_stride + jl] = z.y;
+      }
+    }
+    return;
+  }
+  float2* G = reinterpret_cast<float2*>(a.G) + (r * a.L1 + k1) * a.M;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int m = q * R8T + j;
+    if (q < nq && m < a.M) G[m] = cmul(y[q], twiddle_L<float>(a, (k1 * m) & (a.L - 1), true));
+  }
+}
+
 // Sum over k1; tile of 32 rows x 32 m; writes C1 coalesced along rows.
 template <typename R>
 __global__ void __launch_bounds__(256) k_f3(RowArgs a) {
@@ -648,7 +800,7 @@ fzp_status fill_tables_t(Plan& P, cudaStream_t s) {
   a.j0 = 0;
   a.rows = 1;
   if (b.L1 > 1) k_f1<R><<<dim3((unsigned)(b.L2 / a.B), 1), 256, f1_smem<R>(a), s>>>(a, 1);
-  if (sizeof(R) == 4 && b.L2 == RL) k_f2_r16<<<dim3((unsigned)b.L1, 1), RT, 0, s>>>(a, 1);
+  if (sizeof(R) == 4 && b.L2 == RL) k_f2_r8<<<dim3((unsigned)b.L1, 1), R8T, 0, s>>>(a, 1);
   else k_f2<R><<<dim3((unsigned)b.L1, 1), 512, sizeof(C) * b.L2, s>>>(a, 1);
   FZP_CUDA_TRY(cudaGetLastError());
   FZP_CUDA_TRY(cudaMemcpyAsync(b.d_H, b.d_Z, sizeof(C) * b.L, cudaMemcpyDeviceToDevice, s));
@@ -684,14 +836,14 @@ fzp_status rows_t(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
     if (b.L1 > 1) {
       k_f1<R><<<dim3((unsigned)(b.L2 / a.B), (unsigned)rb), 256, f1_smem<R>(a), s>>>(a, 0);
       prof_begin(P, s);
-      if (sizeof(R) == 4 && b.L2 == RL) k_f2_r16<<<dim3((unsigned)b.L1, (unsigned)rb), RT, 0, s>>>(a, 0);
+      if (sizeof(R) == 4 && b.L2 == RL) k_f2_r8<<<dim3((unsigned)b.L1, (unsigned)rb), R8T, 0, s>>>(a, 0);
       else k_f2<R><<<dim3((unsigned)b.L1, (unsigned)rb), 512, sizeof(C) * b.L2, s>>>(a, 0);
       prof_end(P, s);
       k_f3<R><<<dim3((unsigned)(P.M / 32), (unsigned)((rb + 31) / 32)), 256, 0, s>>>(a);
       P.launches += 3;
     } else {
       prof_begin(P, s);
-      if (sizeof(R) == 4 && b.L2 == RL) k_f2_r16<<<dim3(1, (unsigned)rb), RT, 0, s>>>(a, 0);
+      if (sizeof(R) == 4 && b.L2 == RL) k_f2_r8<<<dim3(1, (unsigned)rb), R8T, 0, s>>>(a, 0);
       else k_f2<R><<<dim3(1, (unsigned)rb), 512, sizeof(C) * b.L2, s>>>(a, 0);
       prof_end(P, s);
       P.launches += 1;
