@@ -85,6 +85,8 @@ KERNEL_SOURCES = {
 TRAFFIC = {
     ("fzp-d0.25m", "dense"): (82.608e9 + 79.682e9,
                               "44a8a75ba5b1d7274c10bff31019ec239016b446b28da4aef503d52a8bc189e0"),
+    ("fzp-d1m", "dense"): (1818.244e9 + 1258.300e9,
+                           "44a8a75ba5b1d7274c10bff31019ec239016b446b28da4aef503d52a8bc189e0"),
 }
 METRIC = "aperture Gsamples/s into 512² ROI, split-BF16 vs FP32 CZT at ≤1e-4 PSF error"
 UNIT = "Gsamples/s"

@@ -319,6 +319,11 @@ FZP_API fzp_status fzp_batch_info(fzp_batch_t batch, int index, fzp_plan_info* o
 FZP_API fzp_status fzp_batch_metrics(fzp_batch_t batch, int index, const void* d_field, void* stream,
                                      fzp_metrics_t* out);
 
+/* I = |U|^2 of instance `index` (as fzp_intensity): d_field device complex128
+ * M_i*M_i (input), d_intensity device double M_i*M_i (output).  Asynchronous. */
+FZP_API fzp_status fzp_batch_intensity(fzp_batch_t batch, int index, const void* d_field, void* d_intensity,
+                                       void* stream);
+
 /* Kernel launches of one replay: the kernel nodes of the captured graph
  * (0 before the first fzp_batch_propagate).  Host only. */
 FZP_API fzp_status fzp_batch_kernels(fzp_batch_t batch, int64_t* kernels);

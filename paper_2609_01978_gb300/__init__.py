@@ -112,6 +112,7 @@ def lib() -> ctypes.CDLL:
             "fzp_batch_metrics": [vp, i32, vp, vp, ctypes.POINTER(Metrics)],
             "fzp_batch_destroy": [vp],
             "fzp_batch_kernels": [vp, ctypes.POINTER(ctypes.c_int64)],
+            "fzp_batch_intensity": [vp, i32, vp, vp, vp],
             "fzp_surrogate_create": [i32, i32, i32, i32, i32, ctypes.c_uint64, ctypes.POINTER(vp)],
             "fzp_surrogate_params": [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t, i32],
             "fzp_surrogate_infer": [vp, vp, i32, vp, vp],
@@ -279,6 +280,10 @@ class Batch:
     def propagate(self, fields, stream=None):
         ptrs = (ctypes.c_void_p * self.n)(*[_ptr(f) for f in fields])
         _check(lib().fzp_batch_propagate(self._h, ptrs, _stream(stream)))
+
+    def intensity(self, i: int, field, out, stream=None):
+        """fzp_batch_intensity: I = |U|^2 of instance i into `out` (float64 M x M)."""
+        _check(lib().fzp_batch_intensity(self._h, i, _ptr(field), _ptr(out), _stream(stream)))
 
     @property
     def kernels(self) -> int:

@@ -156,11 +156,16 @@ fzp_status autotune(const fzp_params* in, fzp_params* chosen, fzp_plan_t* keep) 
   std::vector<Choice> cands;
   // the dense form takes binary and even-level plates, and deformed binary
   // amplitude plates (membrane passes with split mask values)
-  if ((!deformed && geo.levels % 2 == 0) || (deformed && geo.levels == 0)) {
+  if (!deformed && geo.levels % 2 == 0) {
     // cluster 0: the plan's own choice (4 CTAs for M = 512); 1: single-CTA kernel
     cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 128, 0, 0, 0});
     cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 256, 0, 0, 0});
     cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 128, 0, 1, 0});
+  } else if (deformed && geo.levels == 0) {
+    // membrane passes are limited by their generators, whose share per CTA
+    // shrinks with the cluster: 2- and 4-CTA clusters (small ROIs padded)
+    cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 128, 0, 2, 0});
+    cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 128, 0, 4, 0});
   }
   cands.push_back({FZP_FORM_BLUESTEIN, FZP_PREC_FP32, 0, 0, 0, 0});
   fzp_plan_t best = nullptr;
@@ -353,6 +358,12 @@ fzp_status fzp_batch_metrics(fzp_batch_t b, int i, const void* d_field, void* st
   if (!b || !d_field || !out || i < 0 || i >= (int)b->inst.size())
     return set_error(FZP_E_INVALID, "bad batch index or NULL argument");
   return metrics(*b->inst[i], d_field, (cudaStream_t)stream, out);
+}
+
+fzp_status fzp_batch_intensity(fzp_batch_t b, int i, const void* d_field, void* d_intensity, void* stream) {
+  if (!b || !d_field || !d_intensity || i < 0 || i >= (int)b->inst.size())
+    return set_error(FZP_E_INVALID, "bad batch index or NULL argument");
+  return intensity(*b->inst[i], d_field, d_intensity, (cudaStream_t)stream);
 }
 
 fzp_status fzp_batch_kernels(fzp_batch_t b, int64_t* kernels) {

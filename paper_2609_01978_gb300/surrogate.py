@@ -1,8 +1,11 @@
 """Learned surrogate of the propagation: data, training and evaluation.
 
 Training data are PSFs that this library's propagation computes for deformed
-membranes (``Batch`` of Bluestein FP32 plans, one CUDA graph per chunk), with
-the metric extractor's FWHM, diffraction efficiency and 16 MTF samples.  The
+membranes (a ``Batch`` per chunk, one CUDA graph: by default the dense
+tensor-core form's membrane passes; the plain FP32 Bluestein CZT judges the
+held-out set), with the metric extractor's FWHM, diffraction efficiency and
+16 MTF samples.  The intensity and the Strehl denominator come from the
+library (fzp_batch_intensity; peak / Strehl).  The
 network (``SurrogateNet``: hand-written BF16 tensor-core training kernels) maps
 the 8-vector (A/lambda, log10 period, theta, taper, three ridge heights /
 lambda, lambda) to 4114 outputs: log10(I / I_ideal + 1e-6) on the central 64^2
@@ -17,45 +20,54 @@ import math
 
 import numpy as np
 
-from . import FORM_BLUESTEIN, PREC_FP32, Batch, SurrogateNet, make_deform
+from . import FORM_BLUESTEIN, FORM_DENSE, PREC_FP32, PREC_SPLIT_BF16, Batch, SurrogateNet, make_deform
 
 ROI = 128
 CROP = 64
 EPS = 1e-6
 
 
-def _problem(m, fnum: float):
+def _problem(m, fnum: float, form: int, precision: int, cluster: int):
     f = fnum * m.D
-    return dict(D=m.D, f=f, lam=m.lam, M=ROI, pitch=m.lam * fnum / 8, form=FORM_BLUESTEIN, precision=PREC_FP32,
-                deform=make_deform(m.amp, m.period, m.theta, m.taper, m.ridges))
+    return dict(D=m.D, f=f, lam=m.lam, M=ROI, pitch=m.lam * fnum / 8, form=form, precision=precision,
+                cluster=cluster, deform=make_deform(m.amp, m.period, m.theta, m.taper, m.ridges))
 
 
-def generate(membranes, fnum: float = 5.0, chunk: int = 128, torch=None):
-    """Propagate every membrane; returns (Y[n, 4114] raw targets, psf[n, 64, 64])."""
+PLAIN = dict(form=FORM_BLUESTEIN, precision=PREC_FP32, cluster=0)  # the plain CZT: judge of the error
+DENSE = dict(form=FORM_DENSE, precision=PREC_SPLIT_BF16, cluster=4)
+
+
+def generate(membranes, fnum: float = 5.0, chunk: int = 128, torch=None, form: dict = DENSE):
+    """Propagate every membrane; returns (Y[n, 4114] raw targets, psf[n, 64, 64],
+    ideal[n]: each instance's Strehl denominator)."""
     import torch as _t
     torch = torch or _t
     dev = torch.device("cuda")
     Y = np.zeros((len(membranes), CROP * CROP + 18), dtype=np.float64)
     psf = np.zeros((len(membranes), CROP, CROP))
+    ideals = np.zeros(len(membranes))
     lo = (ROI - CROP) // 2
     for s in range(0, len(membranes), chunk):
         ms = membranes[s:s + chunk]
-        b = Batch([_problem(m, fnum) for m in ms])
+        b = Batch([_problem(m, fnum, **form) for m in ms])
         fields = [torch.empty((ROI, ROI), dtype=torch.complex128, device=dev) for _ in ms]
+        inten = torch.empty((ROI, ROI), dtype=torch.float64, device=dev)
         b.propagate(fields)
         torch.cuda.synchronize()
         for k, (m, U) in enumerate(zip(ms, fields)):
             met = b.metrics(k, U)
-            I = (U.abs() ** 2)[lo:lo + CROP, lo:lo + CROP].cpu().numpy()
-            R, f = m.D / 2, fnum * m.D
-            ideal = (math.pi * R * R / (m.lam * f)) ** 2
+            b.intensity(k, U, inten)
+            torch.cuda.synchronize()
+            I = inten[lo:lo + CROP, lo:lo + CROP].cpu().numpy()
+            ideal = met["peak"] / met["strehl"]  # (pi R^2 / (lambda f))^2, the Strehl denominator
             psf[s + k] = I
             Y[s + k, :CROP * CROP] = np.log10(I / ideal + EPS).ravel()
             Y[s + k, CROP * CROP] = met["fwhm_x"] / (m.lam * fnum)  # in units of lambda f/#
             Y[s + k, CROP * CROP + 1] = met["de_lobe"]
             Y[s + k, CROP * CROP + 2:] = met["mtf16"]
+            ideals[s + k] = ideal
         b.close()
-    return Y, psf
+    return Y, psf, ideals
 
 
 def encode(X: np.ndarray, D: float) -> np.ndarray:
@@ -115,10 +127,10 @@ def train(X: np.ndarray, Y: np.ndarray, D: float, steps: int = 2000, batch: int 
     return Trained(net, mean, std, D)
 
 
-def psf_from_targets(Y: np.ndarray, membranes, fnum: float = 5.0) -> np.ndarray:
+def psf_from_targets(Y: np.ndarray, ideal: np.ndarray) -> np.ndarray:
+    """PSFs from predicted targets; ideal[k] is instance k's Strehl denominator
+    (the ``ideal`` returned by ``generate``)."""
     out = np.zeros((Y.shape[0], CROP, CROP))
-    for k, m in enumerate(membranes):
-        R, f = m.D / 2, fnum * m.D
-        ideal = (math.pi * R * R / (m.lam * f)) ** 2
-        out[k] = (10.0 ** Y[k, :CROP * CROP].reshape(CROP, CROP) - EPS) * ideal
+    for k in range(Y.shape[0]):
+        out[k] = (10.0 ** Y[k, :CROP * CROP].reshape(CROP, CROP) - EPS) * ideal[k]
     return out

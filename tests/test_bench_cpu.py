@@ -48,9 +48,10 @@ def test_config_is_shared_and_names_the_sample():
 def test_bluestein_flop_model_and_traffic_keying():
     info = {"fft_length": 1 << 19, "fft_inner": 4096}
     assert bench.bluestein_f2_flops(info, 256) == 256 * 128 * (10.0 * 4096 * 12 + 6.0 * 4096)
-    assert bench._traffic("fzp-d1m", "dense") is None  # nothing captured for this workload
-    t = bench._traffic("fzp-d0.25m", "dense")
-    assert t is None or t > 1e9  # reported only while the sources hash to the capture
+    assert bench._traffic("fzp-d2m", "dense") is None  # nothing captured for this workload
+    for wl in ("fzp-d0.25m", "fzp-d1m"):
+        t = bench._traffic(wl, "dense")
+        assert t is None or t > 1e9  # reported only while the sources hash to the capture
 
 
 def test_reference_arm_under_torchrun_prints_on_rank0_only():

@@ -57,29 +57,36 @@ def test_gradients_match_oracle(env, sizes, B):
 
 
 def test_trained_surrogate_judged_by_czt(env):
-    """Train on 1536 membranes propagated by the library (D = 2 mm, f/# = 5,
-    lambda 450-650 nm, 128^2 ROI), evaluate 128 held-out membranes against the
-    plain CZT, and compare with the method without a learned part: the
-    undeformed zone plate's PSF at the same wavelength, and the mean training PSF."""
+    """Train on 1536 membranes propagated by the library's dense membrane passes
+    (D = 2 mm, f/# = 5, lambda 450-650 nm, 128^2 ROI), evaluate 128 held-out
+    membranes against the plain CZT (FP32 Bluestein form, the judge), and
+    compare with the method without a learned part: the undeformed zone
+    plate's PSF at the same wavelength, and the mean training PSF.  The dense
+    targets of the held-out set equal the plain CZT's (PSF rel L2 <= 1e-4)."""
     fzp, torch, S = env
     import fzp_inputs
     from paper_2609_01978_gb300 import surrogate as SG
     D = 2e-3
-    mem, X = fzp_inputs.surrogate_draws(1536 + 128, seed=11, D=D)
+    ntr = 1536
+    mem, X = fzp_inputs.surrogate_draws(ntr + 128, seed=11, D=D)
     t0 = time.perf_counter()
-    Y, psf = SG.generate(mem)
+    Y, psf, _ = SG.generate(mem[:ntr])
     t_gen = time.perf_counter() - t0
-    Xtr, Ytr, Xte, Yte = X[:1536], Y[:1536], X[1536:], Y[1536:]
+    t0 = time.perf_counter()
+    Yte, T, ideal = SG.generate(mem[ntr:], form=SG.PLAIN)
+    t_plain = (time.perf_counter() - t0) / 128
+    _, Tdense, _ = SG.generate(mem[ntr:])
+    dense_vs_plain = np.array([np.linalg.norm(Tdense[k] - T[k]) / np.linalg.norm(T[k]) for k in range(len(T))])
+    Xtr, Ytr, Xte = X[:ntr], Y, X[ntr:]
     model = SG.train(Xtr, Ytr, D, steps=1500, log=[])
     pred = model.predict(Xte)
-    P = SG.psf_from_targets(pred, mem[1536:])
-    T = psf[1536:]
+    P = SG.psf_from_targets(pred, ideal)
     err = np.array([np.linalg.norm(P[k] - T[k]) / np.linalg.norm(T[k]) for k in range(len(T))])
     flat_mem = [fzp_inputs.Membrane(0.0, m.period, m.theta, 0.0, [(a, b, c, 0.0, w) for a, b, c, _, w in m.ridges],
-                                    m.lam, m.D) for m in mem[1536:]]
-    _, flat = SG.generate(flat_mem)
+                                    m.lam, m.D) for m in mem[ntr:]]
+    _, flat, _ = SG.generate(flat_mem, form=SG.PLAIN)
     err_flat = np.array([np.linalg.norm(flat[k] - T[k]) / np.linalg.norm(T[k]) for k in range(len(T))])
-    mean_psf = psf[:1536].mean(0)
+    mean_psf = psf.mean(0)
     err_mean = np.array([np.linalg.norm(mean_psf - T[k]) / np.linalg.norm(T[k]) for k in range(len(T))])
     de_err = np.abs(pred[:, 4097] - Yte[:, 4097])
     # throughput: surrogate inference vs the propagation it replaces
@@ -93,11 +100,13 @@ def test_trained_surrogate_judged_by_czt(env):
         model.net.infer(xb, yb)
     torch.cuda.synchronize()
     per_inst_sur = (time.perf_counter() - t1) / (10 * xb.shape[0])
-    per_inst_czt = t_gen / len(mem)
-    print(f"held-out PSF rel L2: surrogate median {np.median(err):.3f} mean {err.mean():.3f}; "
+    per_inst_dense = t_gen / ntr
+    print(f"held-out PSF rel L2 (judge: plain CZT): surrogate median {np.median(err):.3f} mean {err.mean():.3f}; "
           f"flat-FZP baseline {np.median(err_flat):.3f}; mean-PSF baseline {np.median(err_mean):.3f}; "
-          f"DE abs err median {np.median(de_err):.2e}; per instance: surrogate {per_inst_sur * 1e6:.1f} us, "
-          f"CZT {per_inst_czt * 1e3:.2f} ms (gain {per_inst_czt / per_inst_sur:.0f}x)")
+          f"DE abs err median {np.median(de_err):.2e}; dense vs plain targets max {dense_vs_plain.max():.2e}; "
+          f"per instance: surrogate {per_inst_sur * 1e6:.1f} us, dense {per_inst_dense * 1e3:.2f} ms, "
+          f"plain CZT {t_plain * 1e3:.2f} ms")
+    assert dense_vs_plain.max() <= 1e-4
     assert np.median(err) < 0.5 * np.median(err_flat)
     assert np.median(err) < 0.5 * np.median(err_mean)
-    assert per_inst_czt / per_inst_sur > 10
+    assert per_inst_dense / per_inst_sur > 10
