@@ -74,6 +74,10 @@ WORKLOADS = {
     # batched deformed membranes (D ~ U[0.05, 0.30] m, 450/550/650 nm, ROI 256^2,
     # seed 0): the first --instances of the 256 draws, one CUDA graph per step
     "membranes": dict(D=0.0, lam=0.0, fnum=5.0, M=256),
+    # learned surrogate on D = 0.2 m membranes (λ 450-650 nm, ROI 128², seed 11):
+    # --train PSFs from the dense membrane passes, --test held out and judged by
+    # the plain FP32 CZT
+    "surrogate": dict(D=0.2, lam=0.0, fnum=5.0, M=128),
 }
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the dominant kernel, from a one-pass ncu capture of this workload; reported
@@ -295,6 +299,72 @@ def run_membranes(args, fzp, torch, dev, ws, pg, rank, local):
             "de_lobe_range": [min(m["de_lobe"] for m in mets), max(m["de_lobe"] for m in mets)]}
 
 
+def run_surrogate(args, fzp, torch, dev):
+    """Config 5 at D = 0.2 m: training PSFs generated by the dense membrane
+    passes (timed: the value is their aperture Gsamples/s), a held-out set
+    judged by the plain FP32 CZT, the trained network's error on it against
+    two baselines without a learned part, and the time per instance of the
+    surrogate and of both propagation forms."""
+    import numpy as np
+    import fzp_inputs
+    from paper_2609_01978_gb300 import surrogate as SG
+    D = WORKLOADS["surrogate"]["D"]
+    ntr, nte = args.train, args.test
+    mem, X = fzp_inputs.surrogate_draws(ntr + nte, seed=11, D=D)
+    samples = sum(fzp.plan_query(D=m.D, f=5.0 * m.D, lam=m.lam, M=128, pitch=m.lam * 5.0 / 8)["N"] ** 2
+                  for m in mem[:ntr])
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    Y, psf, _ = SG.generate(mem[:ntr])
+    torch.cuda.synchronize(dev)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Yte, T, ideal = SG.generate(mem[ntr:], form=SG.PLAIN)
+    t_plain = (time.perf_counter() - t0) / nte
+    _, Tdense, _ = SG.generate(mem[ntr:])
+    dense_vs_plain = [float(np.linalg.norm(Tdense[k] - T[k]) / np.linalg.norm(T[k])) for k in range(nte)]
+    t0 = time.perf_counter()
+    model = SG.train(X[:ntr], Y, D, steps=args.train_steps)
+    t_train = time.perf_counter() - t0
+    pred = model.predict(X[ntr:])
+    P = SG.psf_from_targets(pred, ideal)
+    err = np.array([np.linalg.norm(P[k] - T[k]) / np.linalg.norm(T[k]) for k in range(nte)])
+    nflat = min(nte, args.flat)
+    flat_mem = [fzp_inputs.Membrane(0.0, m.period, m.theta, 0.0, [(a, b, c, 0.0, w) for a, b, c, _, w in m.ridges],
+                                    m.lam, m.D) for m in mem[ntr:ntr + nflat]]
+    _, flat, _ = SG.generate(flat_mem, form=SG.PLAIN)
+    err_flat = np.array([np.linalg.norm(flat[k] - T[k]) / np.linalg.norm(T[k]) for k in range(nflat)])
+    mean_psf = psf.mean(0)
+    err_mean = np.array([np.linalg.norm(mean_psf - T[k]) / np.linalg.norm(T[k]) for k in range(nte)])
+    de_err = np.abs(pred[:, 4097] - Yte[:, 4097])
+    fwhm_err = np.abs(pred[:, 4096] / Yte[:, 4096] - 1)
+    xb = torch.from_numpy(SG.encode(np.tile(X[ntr:], (max(1, 256 // nte), 1))[:256], D).astype(np.float32)).to(dev)
+    yb = torch.empty((xb.shape[0], Y.shape[1]), dtype=torch.float32, device=dev)
+    model.net.infer(xb, yb)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(20):
+        model.net.infer(xb, yb)
+    torch.cuda.synchronize(dev)
+    t_inf = (time.perf_counter() - t0) / (20 * xb.shape[0])
+    return {"metric": METRIC, "value": samples / t_gen / 1e9, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": 1e3 * t_gen, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x2 (dense membrane passes)", "data": "synthetic (seeded deformed membranes)",
+            "config": {"workload": "surrogate", "D_m": D, "roi": 128, "crop": 64, "f_number": 5.0, "seed": 11,
+                       "train": ntr, "test": nte, "train_steps": args.train_steps,
+                       "samples_per_step": samples, "note": "value: aperture Gsamples/s of the training-set "
+                                                             "generation (dense membrane passes, one batch graph "
+                                                             "per 128 instances, metrics and intensity included)"},
+            "roofline": None, "e2e": None, "gpu_launches": None,
+            "surrogate": {"heldout_psf_rel_l2_median": float(np.median(err)), "heldout_psf_rel_l2_mean": float(err.mean()),
+                          "baseline_flat_fzp_median": float(np.median(err_flat)), "baseline_flat_n": nflat,
+                          "baseline_mean_psf_median": float(np.median(err_mean)),
+                          "de_abs_err_median": float(np.median(de_err)), "fwhm_rel_err_median": float(np.median(fwhm_err)),
+                          "judge": "plain FP32 Bluestein CZT", "dense_vs_plain_targets_max": max(dense_vs_plain),
+                          "s_per_instance_dense": t_gen / ntr, "s_per_instance_plain": t_plain,
+                          "s_per_instance_surrogate": t_inf, "train_s": t_train}}
+
+
 def _config(args, wl, N):
     """The workload description shared by both arms' JSON lines."""
     rows = N if args.rows <= 0 else min(N, args.rows)
@@ -412,6 +482,10 @@ def main():
     ap.add_argument("--replicas", action="store_true",
                     help="N > 1: every rank propagates the whole aperture (weak scaling) instead of its rows")
     ap.add_argument("--instances", type=int, default=256, help="membranes workload: instances per batch")
+    ap.add_argument("--train", type=int, default=768, help="surrogate workload: training PSFs")
+    ap.add_argument("--test", type=int, default=64, help="surrogate workload: held-out PSFs (judged by the plain CZT)")
+    ap.add_argument("--flat", type=int, default=32, help="surrogate workload: held-out PSFs of the flat baseline")
+    ap.add_argument("--train-steps", type=int, default=3000, help="surrogate workload: AdamW steps")
     ap.add_argument("--rows", type=int, default=0,
                     help="time only this many central aperture rows per step (a sample; 0: all N)")
     args = ap.parse_args()
@@ -439,6 +513,12 @@ def main():
         if rank != 0:
             __graft_entry__.build()  # already built by rank 0; loads the library
         dist.barrier()
+    if args.workload == "surrogate":
+        if rank == 0:
+            _print(run_surrogate(args, fzp, torch, dev))
+        if pg:
+            pg.destroy_process_group()
+        return
     if args.workload == "membranes":
         out = run_membranes(args, fzp, torch, dev, ws, pg, rank, local)
         if rank == 0:

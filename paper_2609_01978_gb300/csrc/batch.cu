@@ -162,8 +162,10 @@ fzp_status autotune(const fzp_params* in, fzp_params* chosen, fzp_plan_t* keep) 
     cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 256, 0, 0, 0});
     cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 128, 0, 1, 0});
   } else if (deformed && geo.levels == 0) {
-    // membrane passes are limited by their generators, whose share per CTA
-    // shrinks with the cluster: 2- and 4-CTA clusters (small ROIs padded)
+    // membrane passes are limited by their generators: single CTAs and 2- and
+    // 4-CTA clusters (small ROIs padded) trade generator share per CTA against
+    // peer copies and padded tiles; measured, the single CTA wins at M = 128
+    cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 128, 0, 1, 0});
     cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 128, 0, 2, 0});
     cands.push_back({FZP_FORM_DENSE, FZP_PREC_SPLIT_BF16, 128, 0, 4, 0});
   }
