@@ -63,7 +63,11 @@ typedef enum {
 typedef enum {
   FZP_FORM_AUTO = 0,      /* dense for split-BF16/BF16 precision, Bluestein otherwise  */
   FZP_FORM_BLUESTEIN = 1, /* (a) separable Bluestein CZT with hand-written FFTs (Sec. 2.6) */
-  FZP_FORM_DENSE = 2      /* (b) tensor-core contraction U = K diag T K^T (separability of Eq. 2) */
+  FZP_FORM_DENSE = 2,     /* (b) tensor-core contraction U = K diag T K^T (separability of Eq. 2) */
+  FZP_FORM_SACZT = 3      /* semi-analytical CZT (Sec. 3.6, Fig. 5): angular-spectrum propagation
+                             without the paraxial approximation on a padded grid, then a Fresnel
+                             chirp and a CZT zoom onto the ROI; FP32; with exact_radii = 1 the
+                             zone radii of Eq. 3 */
 } fzp_form;
 
 /* Arithmetic of the row transform.  Phase arguments are always reduced in
@@ -144,6 +148,12 @@ typedef struct fzp_params {
                           are invalid                                          */
   int32_t reserved;    /* must be 0                                            */
   double x0, y0;       /* first ROI coordinates [m] when roi_origin = 1 (finite) */
+  int32_t exact_radii; /* 0: paraxial zone radii r_m^2 = m lambda f (Eq. 4), every
+                          form; 1: exact radii of Eq. 3, r_m^2 = m lambda f +
+                          (m lambda / 2)^2, the binary amplitude plate under
+                          FZP_FORM_SACZT only (the paraxial forms' kernel would
+                          aberrate it; FZP_E_UNSUPPORTED elsewhere)          */
+  int32_t reserved2;   /* must be 0                                            */
 } fzp_params;
 
 /* Opaque plan: geometry, zone-threshold table, chirp / kernel tables and the
@@ -210,7 +220,9 @@ typedef struct fzp_metrics_t {
  * Size limits (FZP_E_UNSUPPORTED beyond them): the exact zone rule needs the
  * squared disc radius in samples s_R < 2^46 (N up to about 1.67e7 for a
  * full-aperture plate) and fewer than 2^24 zone steps; the Bluestein form
- * needs N + M - 1 <= 2^24 (its FFT length, a power of two).  Errors:
+ * needs N + M - 1 <= 2^24 (its FFT length, a power of two); the SA-CZT form
+ * a padded grid P <= 16384 (P the power of two >= 1.5 N, N <= 10922; the
+ * plan holds two P x P complex64 grids, 4 GiB at the limit).  Errors:
  * FZP_E_INVALID (bad parameters, Eq. 6 violated, M out of range), FZP_E_OOM,
  * FZP_E_CUDA, FZP_E_UNSUPPORTED (e.g. dense form with FP64 precision). */
 FZP_API fzp_status fzp_plan(const fzp_params* params, fzp_plan_t* out);

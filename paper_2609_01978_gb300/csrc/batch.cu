@@ -246,6 +246,10 @@ fzp_status fzp_batch_plan(const fzp_params* params, int n, fzp_batch_t* out) {
       if (st != FZP_OK) { batch_release(b); return st; }
       p = chosen;
     }
+    if (p.form == FZP_FORM_SACZT) {
+      batch_release(b);
+      return set_error(FZP_E_UNSUPPORTED, "instance %d: the SA-CZT form does not run in batches", i);
+    }
     fzp_plan_s* P = new (std::nothrow) fzp_plan_s();
     if (!P) { batch_release(b); return set_error(FZP_E_OOM, "host allocation failed"); }
     P->owns_buffers = false;

@@ -180,6 +180,16 @@ fzp_status epilogue(Plan& P, void* d_field, int accumulate, cudaStream_t s) {
   return FZP_OK;
 }
 
+fzp_status epilogue_z(Plan& P, void* d_field, int accumulate, double z, cudaStream_t s) {
+  const double lz = P.lambda * z;
+  const int count = P.M * P.M;
+  k_epilogue<<<(count + 255) / 256, 256, 0, s>>>(P.M, P.msh, P.p, lz, P.f / P.lambda, P.dx2 / lz, P.d_Uacc,
+                                                 reinterpret_cast<double2*>(d_field), accumulate);
+  P.launches += 1;
+  FZP_CUDA_TRY(cudaGetLastError());
+  return FZP_OK;
+}
+
 fzp_status intensity(Plan& P, const void* d_field, void* d_I, cudaStream_t s) {
   const int64_t count = (int64_t)P.M * P.M;
   k_intensity<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(count, reinterpret_cast<const double2*>(d_field),

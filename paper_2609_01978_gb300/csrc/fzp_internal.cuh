@@ -195,6 +195,20 @@ struct Dense {
   int* d_sched = nullptr;  // work list of a row-pass launch (3 nchunks + 1 ints)
 };
 
+// SA-CZT (Sec. 3.6, Fig. 5): padded grid and its buffers.
+struct SaCzt {
+  int64_t P = 0;           // padded grid side, a power of two >= 1.5 N
+  int logP = 0;
+  int exact = 0;           // 1: exact zone radii of Eq. 3; 0: paraxial radii
+  double zF = 0;           // distance of the Fresnel part
+  double kmax = 0, d = 0;  // quadratic fit of k_z: c k_max + d K^2 / k_max, c = k0 / k_max
+  void* d_G = nullptr;     // P x P complex64
+  void* d_T = nullptr;     // P x P complex64 (transposed layout)
+  void* d_tw = nullptr;    // P / 2 twiddles e^{-2 pi i t / P}, complex64
+  void* d_K = nullptr;     // M x P complex64: Fresnel chirp and zoom kernel
+  void* d_RT = nullptr;    // M x P complex64: row pass, transposed
+};
+
 struct Plan {
   // problem
   double D, f, lambda, dx, R, p, x0;
@@ -225,6 +239,7 @@ struct Plan {
   double* d_metrics = nullptr; // device scratch for the metric extractor
   size_t device_bytes = 0;
   Bluestein bs;
+  SaCzt sa;
   Dense dn;
   // tracing: kernel launches issued, and CUDA events around the dominant
   // kernel (recorded on the launching stream when profiling is enabled)
@@ -263,6 +278,13 @@ bool column_pass_tc_applies(const Plan& P);
 fzp_status chunk_passes(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream);
 fzp_status column_pass_tc(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream);
 fzp_status epilogue(Plan& P, void* d_field, int accumulate, cudaStream_t stream);
+// The epilogue with the Fresnel part's distance z in the output chirp and the
+// amplitude dx^2 / (lambda z) (the phase e^{ikf} keeps the focal length).
+fzp_status epilogue_z(Plan& P, void* d_field, int accumulate, double z, cudaStream_t stream);
+fzp_status saczt_layout(Plan& P);                      // P, fit, z_F (host)
+fzp_status saczt_build(Plan& P);                       // allocate and fill its tables
+fzp_status saczt_propagate(Plan& P, int64_t j0, int64_t j1, cudaStream_t stream);  // into d_Uacc
+fzp_status saczt_mask(Plan& P, int64_t j0, int64_t rows, uint8_t* out, cudaStream_t stream);
 fzp_status intensity(Plan& P, const void* d_field, void* d_I, cudaStream_t stream);
 fzp_status metrics(Plan& P, const void* d_field, cudaStream_t stream, fzp_metrics_t* out);
 fzp_status bluestein_mask(Plan& P, int64_t j0, int64_t rows, uint8_t* out, cudaStream_t stream);

@@ -83,7 +83,8 @@ void release_plan(Plan* P) {
   if (P->d_thr) cudaFree(P->d_thr);
   if (P->owns_buffers) {
     void* ptrs[] = {P->d_C1, P->d_C1d, P->d_Uacc, P->d_err, P->d_metrics,
-                    P->bs.d_pre, P->bs.d_H, P->bs.d_Z, P->bs.d_G, P->bs.d_tab, P->dn.d_A, P->dn.d_sched};
+                    P->bs.d_pre, P->bs.d_H, P->bs.d_Z, P->bs.d_G, P->bs.d_tab, P->dn.d_A, P->dn.d_sched,
+                    P->sa.d_G, P->sa.d_T, P->sa.d_tw, P->sa.d_K, P->sa.d_RT};
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }
@@ -107,7 +108,9 @@ fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
   if (in->stripe_rows < 0 || (in->stripe_rows % 256) != 0)
     return set_error(FZP_E_INVALID, "stripe_rows must be 0 or a positive multiple of 256");
   if (in->promote < 0 || in->row_batch < 0) return set_error(FZP_E_INVALID, "promote and row_batch must be >= 0");
-  if (in->form < FZP_FORM_AUTO || in->form > FZP_FORM_DENSE) return set_error(FZP_E_INVALID, "unknown form");
+  if (in->form < FZP_FORM_AUTO || in->form > FZP_FORM_SACZT) return set_error(FZP_E_INVALID, "unknown form");
+  if (in->exact_radii != 0 && in->exact_radii != 1) return set_error(FZP_E_INVALID, "exact_radii must be 0 or 1");
+  if (in->reserved2 != 0) return set_error(FZP_E_INVALID, "reserved2 must be 0");
   if (in->precision < FZP_PREC_FP64 || in->precision > FZP_PREC_AUTO_1E4)
     return set_error(FZP_E_INVALID, "unknown precision");
   if (in->deform && (in->deform->n_ridges < 0 || in->deform->n_ridges > 3))
@@ -173,6 +176,16 @@ fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
     return set_error(FZP_E_UNSUPPORTED, "dense form runs in split-BF16 or BF16 precision only");
   if (P.form == FZP_FORM_BLUESTEIN && dense_prec)
     return set_error(FZP_E_UNSUPPORTED, "Bluestein form runs in FP32 or FP64 precision only");
+  if (P.form == FZP_FORM_SACZT) {
+    if (P.precision != FZP_PREC_FP32) return set_error(FZP_E_UNSUPPORTED, "SA-CZT form runs in FP32 precision only");
+    if (P.levels >= 2) return set_error(FZP_E_UNSUPPORTED, "SA-CZT form: binary amplitude plates only");
+    if (in->deform) return set_error(FZP_E_UNSUPPORTED, "SA-CZT form: flat membranes only");
+    if (in->stripe_rows || in->promote || in->row_batch || in->cluster)
+      return set_error(FZP_E_INVALID, "SA-CZT form takes no stripe, promotion, row-batch or cluster knobs");
+  }
+  if (in->exact_radii && P.form != FZP_FORM_SACZT)
+    return set_error(FZP_E_UNSUPPORTED, "exact zone radii (Eq. 3) are taken by the SA-CZT form only");
+  P.sa.exact = in->exact_radii;
   if (P.form == FZP_FORM_DENSE && P.levels > 2) {
     // T = e^{-2 pi i q/L} = sum over passes of w (pos - neg): Re T by magnitude
     // classes cos(2 pi k/L) > 0, Im T by sin(2 pi k/L) > 0; each pass's mask
@@ -363,7 +376,10 @@ fzp_status fzp_plan(const fzp_params* params, fzp_plan_t* out) {
       cudaGetLastError();
     }
   }
-  if (st == FZP_OK) st = (P->form == FZP_FORM_DENSE) ? dense_build_tables(*P) : bluestein_build_tables(*P);
+  if (st == FZP_OK)
+    st = P->form == FZP_FORM_DENSE ? dense_build_tables(*P)
+         : P->form == FZP_FORM_SACZT ? saczt_build(*P)
+                                     : bluestein_build_tables(*P);
   if (st == FZP_OK) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) st = set_error(FZP_E_CUDA, "plan build: %s", cudaGetErrorString(e));
@@ -419,6 +435,11 @@ fzp_status fzp_plan_query(const fzp_params* params, fzp_plan_info* out) {
     if (L > (1ll << 24)) return set_error(FZP_E_UNSUPPORTED, "FFT length %lld above %lld", (long long)L, 1ll << 24);
     out->fft_length = L;
   }
+  if (!tuned && P.form == FZP_FORM_SACZT) {
+    const fzp_status sst = saczt_layout(P);  // host only
+    if (sst != FZP_OK) return sst;
+    out->fft_length = P.sa.P;
+  }
   out->promote = !tuned && P.form == FZP_FORM_DENSE ? (P.promote_req > 0 ? P.promote_req : 128) : 0;
   out->cluster = !tuned && P.form == FZP_FORM_DENSE ? P.cluster_req : 0;
   out->levels = P.levels;
@@ -450,7 +471,7 @@ fzp_status fzp_plan_info_get(fzp_plan_t plan, fzp_plan_info* out) {
   out->dx = P.dx; out->R = P.R; out->kappa = P.kappa; out->x0 = P.x0;
   out->M = P.M; out->form = P.form; out->precision = P.precision;
   out->stripe_rows = P.stripe_rows;
-  out->fft_length = P.bs.L;
+  out->fft_length = P.form == FZP_FORM_SACZT ? P.sa.P : P.bs.L;
   out->promote = P.form == FZP_FORM_DENSE ? P.dn.promote_kblocks : 0;
   out->row_batch = P.form == FZP_FORM_BLUESTEIN ? (int32_t)P.bs.rows : 0;
   out->chunk_rows = P.chunk_rows;
@@ -484,6 +505,14 @@ fzp_status fzp_propagate_roi(fzp_plan_t plan, int64_t row_begin, int64_t row_end
   int64_t jlo, jhi;
   disc_rows(P, jlo, jhi);
   const int64_t a = std::max(row_begin, jlo), b = std::min(row_end, jhi);
+  if (P.form == FZP_FORM_SACZT) {
+    // the whole padded plane at once (rows outside the range masked to zero)
+    if (a < b) {
+      const fzp_status st = saczt_propagate(P, a, b, s);
+      if (st != FZP_OK) return st;
+    }
+    return epilogue_z(P, d_field, accumulate, P.sa.zF, s);
+  }
   for (int64_t j0 = a; j0 < b; j0 += P.chunk_rows) {
     const fzp_status st = chunk_passes(P, j0, std::min(P.chunk_rows, b - j0), s);
     if (st != FZP_OK) return st;
@@ -501,9 +530,9 @@ fzp_status fzp_aperture_mask(fzp_plan_t plan, int64_t row_begin, int64_t row_end
   uint8_t* out = reinterpret_cast<uint8_t*>(d_mask);
   // each form exports through the generator its row pass runs (the dense
   // form: walker, block-wise generator or level mode, as the plan launches it)
-  return P.form == FZP_FORM_DENSE
-             ? dense_mask(P, row_begin, row_end - row_begin, out, (cudaStream_t)stream)
-             : bluestein_mask(P, row_begin, row_end - row_begin, out, (cudaStream_t)stream);
+  return P.form == FZP_FORM_DENSE   ? dense_mask(P, row_begin, row_end - row_begin, out, (cudaStream_t)stream)
+         : P.form == FZP_FORM_SACZT ? saczt_mask(P, row_begin, row_end - row_begin, out, (cudaStream_t)stream)
+                                    : bluestein_mask(P, row_begin, row_end - row_begin, out, (cudaStream_t)stream);
 }
 
 fzp_status fzp_profile_enable(fzp_plan_t plan, int enable) {

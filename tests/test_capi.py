@@ -157,3 +157,23 @@ def test_other_entry_points_validate_before_the_device(fzp):
         assert e.value.status == fzp.FZP_E_INVALID
     assert L.fzp_batch_destroy(None) == fzp.FZP_OK
     assert L.fzp_surrogate_destroy(None) == fzp.FZP_OK
+
+
+def test_saczt_host_plan(fzp):
+    """The SA-CZT form's host checks: FP32 only, binary flat plates only, exact
+    radii in this form only, the padded grid (a power of two >= 1.5 N) reported
+    and limited to 16384."""
+    import ctypes
+    L = fzp.lib()
+    base = dict(D=4e-3, f=20e-3, lam=632.8e-9, M=256, pitch=0.2e-6, form=fzp.FORM_SACZT, precision=fzp.PREC_FP32)
+    q = fzp.plan_query(exact_radii=1, **base)
+    assert q["N"] == 5057 and q["fft_length"] == 8192
+    inf = fzp.PlanInfo()
+    for kw, status in [(dict(precision=fzp.PREC_FP64), fzp.FZP_E_UNSUPPORTED),
+                       (dict(levels=4), fzp.FZP_E_UNSUPPORTED),
+                       (dict(form=fzp.FORM_BLUESTEIN, exact_radii=1), fzp.FZP_E_UNSUPPORTED),
+                       (dict(D=0.02, f=0.1), fzp.FZP_E_UNSUPPORTED),   # N = 25,285: P = 65536 > 16384
+                       (dict(exact_radii=2), fzp.FZP_E_INVALID),
+                       (dict(cluster=2), fzp.FZP_E_INVALID)]:
+        p = fzp._params(**dict(base, **kw))
+        assert L.fzp_plan_query(ctypes.byref(p), ctypes.byref(inf)) == status, kw
