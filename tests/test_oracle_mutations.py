@@ -14,12 +14,24 @@ import sys
 import pytest
 
 import test_oracle_pins as pins
+import test_oracle_saczt
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle")
 
+def _sa_paraxial_limit(mod):
+    test_oracle_saczt.test_paraxial_limit_is_the_fresnel_sum(mod, mod.saczt)
+    test_oracle_saczt.test_paraxial_limit_asymmetric_aperture(mod, mod.saczt)
+
+
+def _sa_exact_focus(mod):
+    test_oracle_saczt.test_exact_radii_focus_under_the_exact_propagator(
+        mod, test_oracle_saczt.f5_fields_of(mod, mod.saczt))
+
+
 # (file, name, exact source text, replacement, pins that must catch it): "c" is
-# fzp_oracle.c, "py" the extractor and closed forms in __init__.py
+# fzp_oracle.c, "py" the extractor and closed forms in __init__.py, "sa" the
+# SA-CZT oracle saczt.py
 MUTATIONS = [
     ("c", "negative plate opens even zones",
      "    return ((int64_t)zone & 1) ? 1 : 0;\n  }\n  if (P->kind == ORC_FZP_POSITIVE)",
@@ -82,6 +94,22 @@ MUTATIONS = [
      "if ((double)(dj * dj + mid * mid) * dx2 <= R2) lo = mid;",
      "if ((double)(dj * dj + mid * mid) * dx2 < R2) lo = mid;",
      [(pins.test_count_aperture_is_the_disc_lattice_count, (2000 * 2.0 ** -20, 20e-3, 2.0 ** -20))]),
+    ("sa", "SA-CZT residual phase of the wrong sign",
+     "A * np.exp(1j * h * g.f)",
+     "A * np.exp(-1j * h * g.f)",
+     [(_sa_exact_focus, ())]),
+    ("sa", "SA-CZT Fresnel part over f instead of z_F",
+     "return -2.0 * k0 * d * g.f / kmax",
+     "return g.f",
+     [(_sa_exact_focus, ())]),
+    ("sa", "SA-CZT zoom kernel of the wrong sign",
+     "np.exp(-1j * k0 * np.outer(x, u) / zF)",
+     "np.exp(1j * k0 * np.outer(x, u) / zF)",
+     [(_sa_paraxial_limit, ())]),
+    ("sa", "SA-CZT mask not centred on the padded grid",
+     "o = P // 2 - g.c",
+     "o = 0",
+     [(_sa_paraxial_limit, ())]),
     ("py", "FWHM peak taken as the on-axis sample (no parabola)",
      "peak = y0 - 0.125 * (yp - ym) ** 2 / den if den != 0 else y0",
      "peak = y0",
@@ -120,7 +148,7 @@ MUTATIONS = [
 def _copy(tmp_path, tag, which=None, old=None, new=None):
     d = tmp_path / f"oracle_{tag}"
     d.mkdir()
-    for fn, key in (("__init__.py", "py"), ("fzp_oracle.c", "c")):
+    for fn, key in (("__init__.py", "py"), ("fzp_oracle.c", "c"), ("saczt.py", "sa")):
         src = open(os.path.join(SRC, fn)).read()
         if which == key:
             assert src.count(old) == 1, f"mutation target not unique: {old!r}"
@@ -132,6 +160,7 @@ def _copy(tmp_path, tag, which=None, old=None, new=None):
     sys.modules[spec.name] = mod  # dataclasses look their module up here
     spec.loader.exec_module(mod)
     mod.build(force=True)
+    mod.saczt = importlib.import_module(f"oracle_{tag}.saczt")
     return mod
 
 

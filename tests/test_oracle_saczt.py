@@ -33,6 +33,26 @@ def test_paraxial_limit_is_the_fresnel_sum(oracle_mod, sa):
     assert rel(sa.field_saczt(g2, paraxial=True), O.field_czt(g2)) < 1e-10
 
 
+def test_paraxial_limit_asymmetric_aperture(oracle_mod, sa):
+    """The same limit on a seeded random aperture (no symmetry, so a mirrored
+    or transposed zoom fails), against Eq. 2 summed directly here."""
+    O = oracle_mod
+    g = O.Geometry(D=41 * 1e-6, f=2e-3, lam=632.8e-9, M=9, p=3e-6, dx=1e-6, N=41, x0=-7e-6)
+    T = (np.random.default_rng(5).uniform(size=(g.N, g.N)) < 0.4).astype(np.float64)
+    U = sa.field_saczt(g, paraxial=True, mask=T)
+    lf, k = g.lam * g.f, 2 * math.pi / g.lam
+    u = (np.arange(g.N) - g.c) * g.dx
+    x = g.x0 + np.arange(g.M) * g.p
+    ref = np.zeros((g.M, g.M), complex)
+    for n in range(g.M):
+        for m in range(g.M):
+            ph = np.exp(1j * math.pi * (u[None, :] ** 2 + u[:, None] ** 2) / lf
+                        - 2j * math.pi * (x[m] * u[None, :] + x[n] * u[:, None]) / lf)
+            ref[n, m] = np.sum(T * ph)
+    ref *= np.exp(1j * k * g.f) * np.exp(1j * math.pi * (x[None, :] ** 2 + x[:, None] ** 2) / lf) * g.dx ** 2 / (1j * lf)
+    assert rel(U, ref) < 1e-10
+
+
 def test_angular_step_conserves_energy(oracle_mod, sa):
     """exp(i h f) has unit modulus and no component is evanescent at dx > lambda / 2,
     so the residual step keeps sum |U1|^2 = sum |T|^2 (Parseval)."""
@@ -49,15 +69,18 @@ def test_angular_step_conserves_energy(oracle_mod, sa):
     assert abs(math.sqrt(k0 ** 2 - kmax ** 2) - (c * kmax + d * kmax)) < 1e-9 * k0
 
 
-@pytest.fixture(scope="module")
-def f5_fields(oracle_mod, sa):
+def f5_fields_of(O, sa):
     """A 2 mm plate at f/5 (N = 2529, 158 zones, NA 0.1) under the exact
     propagator, with exact and with paraxial radii."""
-    O = oracle_mod
     kw = dict(D=2e-3, f=10e-3, lam=632.8e-9, M=128, p=632.8e-9 * 5 / 8)
     ge = O.Geometry(kind=O.FZP_EXACT, **kw)
     gp = O.Geometry(kind=O.FZP_PARAXIAL, **kw)
     return ge, sa.field_saczt(ge), gp, sa.field_saczt(gp)
+
+
+@pytest.fixture(scope="module")
+def f5_fields(oracle_mod, sa):
+    return f5_fields_of(oracle_mod, sa)
 
 
 def test_exact_radii_focus_under_the_exact_propagator(oracle_mod, f5_fields):
