@@ -11,8 +11,8 @@ columns; Eq. 9-10, Sec. 2.6) over all N rows, in FP64.  It is stored as
 complex64 (relative rounding 6e-8, far below the 1e-4 tolerance the GPU forms
 are held to); the oracle's own FP64 metrics of the FP64 field go beside it.
 
-This script calls only ``oracle`` (no GPU code).  On 8 x86 cores it takes
-about 50 minutes.  Run from the repository root:
+This script calls only ``oracle`` (no GPU code).  On 8 x86 cores it took
+about two hours (the stored JSON records the time and thread count).  Run from the repository root:
 
     python tests/golden/make_config2_oracle.py
 """
