@@ -22,7 +22,10 @@ focus.
 Workloads: fzp-d0.05m (small case for profiler captures), fzp-d0.25m,
 fzp-d1m ... fzp-d5m (the D sweep at f/# = 5), fzp-t1 ... fzp-t5 (the phase
 plates of Tables 1-5 on their own grids), membranes (a batch of the seeded
-deformed membranes, autotuned per instance, one CUDA graph per step).
+deformed membranes, autotuned per instance, one CUDA graph per step),
+surrogate (training-set generation and the trained network's held-out
+error), saczt-d8mm (the SA-CZT form on an exact-radii plate; its roofline is
+the zoom product's, and its oracle sample a 2 mm plate of the same method).
 --rows R times R central aperture rows per step (a sample, named in the
 config); --plain-rows R does the same for the plain FP32 form (its cost per
 row does not depend on the row; default: all rows up to D = 0.25 m, 16,384
@@ -78,7 +81,14 @@ WORKLOADS = {
     # --train PSFs from the dense membrane passes, --test held out and judged by
     # the plain FP32 CZT
     "surrogate": dict(D=0.2, lam=0.0, fnum=5.0, M=128),
+    # the SA-CZT form (Sec. 3.6, Fig. 5): exact-radii plate (Eq. 3), D = 8 mm at
+    # f/# = 5 (N = 10,115, padded grid 16,384^2), exact angular-spectrum residual,
+    # Fresnel chirp and zoom onto the 512^2 ROI
+    "saczt-d8mm": dict(D=8e-3, lam=632.8e-9, fnum=5.0, M=512, saczt=True),
 }
+# the oracle's bounded sample for the SA-CZT workloads: the same method on a
+# D = 2 mm plate (N = 2,529, padded grid 4096^2), whole, repeated
+SACZT_SAMPLE_D = 2e-3
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the dominant kernel, from a one-pass ncu capture of this workload; reported
 # only while the kernel's sources hash to what was captured (null otherwise).
@@ -394,6 +404,8 @@ def run_reference(args, wl):
     """The oracle (CPU FP64 Bluestein CZT, fzp_oracle.c) timed on the host cores on
     a bounded sample of aperture rows of the same workload."""
     import oracle as O
+    if wl.get("saczt"):
+        return run_reference_saczt(args, wl)
     g = _oracle_geometry(O, wl)
     rows = args.ref_rows
     j0 = g.c - rows // 2
@@ -413,6 +425,61 @@ def run_reference(args, wl):
             "config": dict(_config(args, wl, g.N), rows_per_step=rows),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def _saczt_sample_geometry(O, wl):
+    D = SACZT_SAMPLE_D
+    return O.Geometry(D=D, f=D * wl["fnum"], lam=wl["lam"], M=wl["M"], p=wl["lam"] * wl["fnum"] / 8,
+                      kind=O.FZP_EXACT)
+
+
+def run_reference_saczt(args, wl):
+    """The oracle's SA-CZT (FP64, numpy transforms and products) on the 2 mm
+    sample plate, whole, once per step."""
+    import oracle as O
+    from oracle import saczt as SA
+    g = _saczt_sample_geometry(O, wl)
+    for _ in range(args.warmup):
+        SA.field_saczt(g)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        SA.field_saczt(g)
+    dt = time.perf_counter() - t0
+    value = args.steps * g.N * g.N / dt / 1e9
+    sample = (f"SA-CZT of a D = {g.D:g} m exact-radii plate (N = {g.N}, padded grid {SA.pad_size(g.N)}^2), "
+              f"whole, x {args.steps} steps, FP64; numpy FFTs on one thread, BLAS products on the host cores")
+    cfg = {"workload": args.workload, "form": "saczt", "D_m": wl["D"], "lambda_m": wl["lam"],
+           "f_number": wl["fnum"], "roi": wl["M"], "sample_D_m": g.D, "sample_N": g.N}
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (procedural zone plate, exact radii)", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def cpu_baseline_saczt(wl, budget_s: float = 15.0) -> dict:
+    """The oracle's SA-CZT on the 2 mm sample plate, repeated until half the
+    budget has passed; returns its field for the parity check (private keys)."""
+    import numpy as np
+    import oracle as O
+    from oracle import saczt as SA
+    g = _saczt_sample_geometry(O, wl)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        U = SA.field_saczt(g)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * budget_s:
+            break
+    return {"value": reps * g.N * g.N / dt / 1e9, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+            "sample": f"SA-CZT (FP64, numpy) of a D = {g.D:g} m exact-radii plate, N = {g.N}, padded grid "
+                      f"{SA.pad_size(g.N)}^2, whole, {reps} x, {dt:.1f} s; numpy FFTs on one thread, BLAS "
+                      f"products on the host cores",
+            "seconds": dt, "_geometry": g, "_I": np.abs(U) ** 2,
+            "_airy_fwhm": O.airy_fwhm_factor() * g.lam * g.f / (2 * g.R),
+            "_lobe_de": O.airy_encircled(O.AIRY_NULL) * O.binary_fzp_efficiency()}
 
 
 def cpu_baseline(wl, budget_s: float = 15.0) -> dict:
@@ -472,7 +539,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fzp-d1m", choices=sorted(WORKLOADS))
-    ap.add_argument("--form", default="dense", choices=["dense", "bluestein"])
+    ap.add_argument("--form", default="dense", choices=["dense", "bluestein", "saczt"])
     ap.add_argument("--ref-rows", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -527,11 +594,22 @@ def main():
             pg.destroy_process_group()
         return
     D, lam, fnum, M = wl["D"], wl["lam"], wl["fnum"], wl["M"]
-    if args.form == "dense":
+    if wl.get("saczt"):
+        args.form, args.no_plain = "saczt", True
+    if args.form == "saczt":
+        if not wl.get("saczt"):
+            raise SystemExit("--form saczt needs an SA-CZT workload (saczt-d8mm)")
+        form, prec = fzp.FORM_SACZT, fzp.PREC_FP32
+        dtype = "f32 transforms + bf16x2 zoom" if M % 128 == 0 else "f32"
+    elif args.form == "dense":
         form, prec, dtype = fzp.FORM_DENSE, fzp.PREC_SPLIT_BF16, "bf16x2"
     else:
         form, prec, dtype = fzp.FORM_BLUESTEIN, fzp.PREC_FP32, "f32"
     params = dict(D=D, f=D * fnum, lam=lam, M=M, pitch=lam * fnum / 8, form=form, precision=prec)
+    if args.form == "saczt":
+        params.update(exact_radii=1)
+        if ws > 1 and not args.replicas:
+            raise SystemExit("the SA-CZT form transforms the whole padded grid: run it with --replicas")
     if wl.get("levels"):
         params.update(levels=wl["levels"], dx=_dx(wl))
     plan = fzp.Plan(**params)
@@ -605,6 +683,16 @@ def main():
                 "peak_source": peak_kind + " bf16 sustained",
                 "work": "8 M flops per aperture sample inside the disc and mask pass",
                 "disc_samples_per_launch": inside * args.steps / launches}
+    elif args.form == "saczt":
+        # k_sa_rows<1>: one pass of the padded grid through HBM (P^2 complex64
+        # read and written) with two transforms and the residual phase between
+        Pg = info["fft_length"]
+        bytes_launch = 2.0 * 8.0 * Pg * Pg
+        achieved = bytes_launch / (avg_ms / 1e3) / 1e9
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": prof["dominant_name"], "peak_source": peak_kind + " HBM copy",
+                "work": "16 P^2 bytes per launch (P = padded grid side)"}
     else:
         launches = max(1, prof["dominant_launches"])
         rows_per_launch = rows * args.steps / launches
@@ -649,7 +737,24 @@ def main():
     # the oracle on the host cores (cpu_baseline), and parity: the oracle's
     # FP64 field of its timed rows against this form's field of the same rows
     cb, parity = None, None
-    if ws == 1 and not args.no_cpu_baseline:
+    if ws == 1 and not args.no_cpu_baseline and args.form == "saczt":
+        cb = cpu_baseline_saczt(wl)
+        gs = cb.pop("_geometry")
+        Iref = cb.pop("_I")
+        with fzp.Plan(D=gs.D, f=gs.f, lam=gs.lam, M=gs.M, pitch=gs.p, form=form, precision=prec,
+                      exact_radii=1) as ps:
+            Is = _rows_intensity(fzp, torch, ps, M, 0, ps.info["N"], stream, dev)
+        parity = {"oracle": "oracle SA-CZT (FP64) of the cpu_baseline sample plate, whole", "tolerance": 1e-4,
+                  "sample_D_m": gs.D, "rel_l2_I_saczt": _rel_l2(Is, Iref)}
+        cb.pop("_airy_fwhm")
+        lobe = cb.pop("_lobe_de")
+        import oracle as O
+        gw = O.Geometry(D=D, f=D * fnum, lam=lam, M=M, p=lam * fnum / 8, kind=O.FZP_EXACT)
+        airy = O.airy_fwhm_factor() * gw.lam * gw.f / (2 * gw.R)
+        parity["full_aperture_vs_closed_forms"] = {
+            "fwhm_x_over_airy_minus_1": m["fwhm_x"] / airy - 1,
+            "de_lobe_over_ee_efficiency_minus_1": m["de_lobe"] / lobe - 1}
+    elif ws == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(wl)
         pa, pb_ = cb.pop("_rows")
         Iref = cb.pop("_I")
@@ -700,6 +805,8 @@ def main():
            "config": _config(args, wl, N),
            "roofline": roof, "e2e": e2e, "gpu_launches": prof["kernel_launches"], "clocks": clocks,
            "metrics_last_step": {k: m[k] for k in ("fwhm_x", "de_lobe", "mtf_half_cut")}}
+    if args.form == "saczt":
+        out["config"].update(exact_radii=True, padded_grid=info["fft_length"])
     if sharded:
         out["config"]["parallelism"] = f"rows split over {ws} ranks by open-sample count, one all_reduce per step"
     if plain:

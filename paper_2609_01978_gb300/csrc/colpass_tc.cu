@@ -39,7 +39,11 @@ constexpr int TA_BYTES = 4 * TSUB;       // [Cr hi][Cr lo][Ci hi][Ci lo]
 constexpr int TB_BYTES = 4 * TSUB;       // [t0 hi][t1 hi][t0 lo][t1 lo] (as stored)
 constexpr int T_EPI_WARPS = 4, T_PROD_WARP0 = 4, T_LOAD_WARP = 8, T_MMA_WARP = 9;
 constexpr int T_THREADS = 10 * 32;
-constexpr int T_PROMOTE = 128;           // K blocks per tensor-memory chunk
+// K blocks per tensor-memory chunk: the FP32 accumulator's error grows with
+// the chunk's length (a whole 0.25 m aperture: 4.2e-5 relative L2 of I with
+// 4096-row chunks), and the column pass is a small part of a step, so its
+// chunks are short
+constexpr int T_PROMOTE = 32;
 constexpr int T_TMEM_COLS = 512;         // D1 at columns 0-255, D2 at 256-511
 constexpr int T_ERR_BASE = 200;
 
@@ -343,6 +347,11 @@ bool column_pass_tc_applies(const Plan& P) {
 }
 
 fzp_status column_pass_tc(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
+  return column_pass_tc_w(P, j0, rows, P.pass_index >= 0 ? P.passes[P.pass_index].wr : 1.0,
+                          P.pass_index >= 0 ? P.passes[P.pass_index].wi : 0.0, s);
+}
+
+fzp_status column_pass_tc_w(Plan& P, int64_t j0, int64_t rows, double wr, double wi, cudaStream_t s) {
   static std::atomic<uint64_t> attr{0};
   FZP_CUDA_TRY(smem_attr_once((const void*)k_colpass_tc, (int)colpass_tc_smem(), attr));
   ColTcArgs a{};
@@ -362,8 +371,8 @@ fzp_status column_pass_tc(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
   slices = std::max<int64_t>(1, std::min<int64_t>(slices, a.nkb / 16));
   a.slices = (int)slices;
   a.Uacc = reinterpret_cast<double2*>(P.d_Uacc);
-  a.wr = P.pass_index >= 0 ? P.passes[P.pass_index].wr : 1.0;
-  a.wi = P.pass_index >= 0 ? P.passes[P.pass_index].wi : 0.0;
+  a.wr = wr;
+  a.wi = wi;
   a.err = P.d_err;
   const int64_t units = tiles2 * slices;
   const int grid = (int)std::min<int64_t>(units, P.dn.num_sms);

@@ -27,8 +27,8 @@
 //              into two FP32 accumulators (one per tile), completion multicast
 //              to the cluster's empty barriers
 //   warps 0-7: epilogue; every `promote` stages both accumulators are read with
-//              tcgen05.ld into shared memory and written to C1 by TMA (store
-//              for the first chunk, reduce-add afterwards).  The tensor core's
+//              tcgen05.ld into shared memory and added into C1 by TMA
+//              reduce-add (C1 zeroed before the launch).  The tensor core's
 //              FP32 accumulation loses precision in proportion to the chunk
 //              length (measured: 8e-4 relative error of I over a 0.25 m
 //              aperture without promotion, 8e-6 with 4096-sample chunks).
@@ -79,7 +79,8 @@ struct DenseArgs {
   int64_t j_begin, j_end;   // aperture rows of this launch [j_begin, j_end)
   int64_t n_stripes;        // ceil((j_end - j_begin) / BN)
   const int* sched;         // work list (k_dense_sched): off[nchunks + 1], slo[nchunks], cnt[nchunks]
-  int nchunks;              // ceil(kblocks / promote): K chunks of the work list
+  int nchunks;              // ceil(kblocks / group): K chunks of the work list
+  int group;                // K blocks per work-list chunk (a multiple of promote)
   int npairs;               // kernel tile pairs (items per stripe; a multiple of the cluster size)
   int M;                    // ROI side: tiles t with 64 t >= M are zero padding, not stored
   int signed_mask;          // 1: binary phase plate, T = +1 / -1 on even / odd zones inside the disc
@@ -90,6 +91,8 @@ struct DenseArgs {
   int hi_only;              // 1: BF16 kernel (hi) only
   int cx_sin;               // membrane pass: 0 -> mask T cos(phi), 1 -> T sin(phi)
   DeformCoef df;            // membrane pass: the deformation phase
+  const float* ld_src;      // non-null (membrane-pass kernels): B loaded from this real matrix,
+  int64_t ld_stride;        //   row j at ld_src + j * ld_stride, every K block of every stripe
   const uint8_t* A;         // pre-swizzled kernel tiles, [pair][kb][t0hi t1hi t0lo t1lo]
   float* C1;                // [rows][c1_stride], column = j - c1_j0
   int64_t c1_stride, c1_j0;
@@ -386,6 +389,11 @@ __device__ __forceinline__ uint32_t disc_bits(const Walker& w, int64_t i0) {
 // least one block (a stripe with no row on the disc still writes its zero
 // rows of C1).  Every role of the kernel derives the same range.
 __device__ __forceinline__ void stripe_kspan(const DenseArgs& a, int64_t s, int64_t& klo, int64_t& khi) {
+  if (a.ld_src) {  // a loaded operand is dense: no chord bound
+    klo = 0;
+    khi = a.kblocks;
+    return;
+  }
   const int64_t jb = a.j_begin + s * BN;
   const int64_t je = jb + BN < a.j_end ? jb + BN : a.j_end;
   const int64_t c = a.mg.c;
@@ -403,10 +411,12 @@ __device__ __forceinline__ void stripe_kspan(const DenseArgs& a, int64_t s, int6
 }
 
 // Work units in chunk-major order: unit (g, pair group pu, stripe s) covers the
-// K blocks of chunk g, [g P, (g + 1) P) with P = promote, that meet stripe s's
-// disc chord; units of one chunk are consecutive, so the clusters of a wave read
-// the same kernel-matrix blocks (one fetch from HBM, the rest from L2) while each
-// unit still ends with one promotion of its accumulators into C1 (reduce-add).
+// K blocks of chunk g, [g Q, (g + 1) Q) with Q = group (a few promotion
+// lengths), that meet stripe s's disc chord; units of one chunk are
+// consecutive, so the clusters of a wave read the same kernel-matrix blocks
+// (one fetch from HBM, the rest from L2).  A unit promotes its accumulators
+// into C1 (reduce-add) after every `promote` blocks; its C1 tile stays in L2
+// between those promotions.
 // Per chunk g the stripes meeting it are a contiguous range [slo_g, slo_g +
 // cnt_g) (the chords are nested about the stripe nearest the axis); off_g counts
 // the units before chunk g.
@@ -431,7 +441,7 @@ __device__ __forceinline__ Unit unit_at(const DenseArgs& a, int64_t it, int npg)
   u.s = __ldg(slo + g) + r % c;
   int64_t klo, khi;
   stripe_kspan(a, u.s, klo, khi);
-  const int64_t c0 = (int64_t)g * a.promote, c1 = c0 + a.promote;
+  const int64_t c0 = (int64_t)g * a.group, c1 = c0 + a.group;
   u.kb0 = klo > c0 ? klo : c0;
   u.kb1 = khi < c1 ? khi : c1;
   (void)npg;
@@ -449,7 +459,7 @@ __global__ void k_dense_sched(const DenseArgs a, int npg, int* sched) {
   int64_t sc = (a.mg.c - a.j_begin) / BN;
   sc = a.mg.c < a.j_begin ? 0 : (sc >= ns ? ns - 1 : sc);
   for (int g = threadIdx.x; g < a.nchunks; g += blockDim.x) {
-    const int64_t c0 = (int64_t)g * a.promote, c1 = c0 + a.promote;
+    const int64_t c0 = (int64_t)g * a.group, c1 = c0 + a.group;
     auto meets = [&](int64_t st) {
       int64_t klo, khi;
       stripe_kspan(a, st, klo, khi);
@@ -549,10 +559,20 @@ __device__ __forceinline__ uint32_t bf16_pair(float a, float b) {
          ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
 }
 
+// Two FP32 values -> packed BF16 hi (RN) and lo (RN of the remainder), lower
+// half from a: one cvt.rn.bf16x2 per plane (a goes to the upper half of the
+// instruction's result when given first, so b is given first).
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(b), "f"(a));
+  const float ah = __uint_as_float(hi << 16), bh = __uint_as_float(hi & 0xffff0000u);
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(b - bh), "f"(a - ah));
+}
+
 // Chunks [q0, q0 + nq) of the row (8 columns each); di0 = column of the block
-// start minus c.
-__device__ __forceinline__ void cx_store(const DeformCoef& d, const CxRow& r, int64_t di0, uint32_t bits, int sinpart,
-                                         uint8_t* hi_row, uint8_t* lo_row, int sw, int q0, int nq) {
+// start minus c; NR ridges.
+template <int NR>
+__device__ __forceinline__ void cx_store_n(const DeformCoef& d, const CxRow& r, int64_t di0, uint32_t bits,
+                                           int sinpart, uint8_t* hi_row, uint8_t* lo_row, int sw, int q0, int nq) {
   constexpr float TWO_PI = 6.28318530717958648f;
   float fi = (float)(di0 + 8 * q0);
   // wrinkle phasor at the first column
@@ -562,18 +582,16 @@ __device__ __forceinline__ void cx_store(const DeformCoef& d, const CxRow& r, in
   float ws, wc;
   __sincosf(TWO_PI * tt, &ws, &wc);
   // ridges at the first column, and their ratios to the next column
-  float g[3], rr[3];
+  float g[NR > 0 ? NR : 1], rr[NR > 0 ? NR : 1];
 #pragma unroll
-  for (int e = 0; e < 3; ++e) {
+  for (int e = 0; e < NR; ++e) {
     g[e] = 0.0f;
     rr[e] = 1.0f;
-    if (e < d.n) {
-      const float d0 = fmaf(fi, d.nx[e], r.cr[e]);
-      const float ex = d.q[e] * d0 * d0;
-      if (ex < 69.0f) {
-        g[e] = __expf(-ex);
-        rr[e] = __expf(-d.q[e] * d.nx[e] * fmaf(2.0f, d0, d.nx[e]));
-      }
+    const float d0 = fmaf(fi, d.nx[e], r.cr[e]);
+    const float ex = d.q[e] * d0 * d0;
+    if (ex < 69.0f) {
+      g[e] = __expf(-ex);
+      rr[e] = __expf(-d.q[e] * d.nx[e] * fmaf(2.0f, d0, d.nx[e]));
     }
   }
 #pragma unroll 1
@@ -586,8 +604,8 @@ __device__ __forceinline__ void cx_store(const DeformCoef& d, const CxRow& r, in
       for (int z = 0; z < 2; ++z) {
         float wz = d.amp2 * ws * fmaf(-d.tq, fmaf(fi, fi, r.fj2), 1.0f);
 #pragma unroll
-        for (int e = 0; e < 3; ++e) {
-          wz = fmaf(d.h2[e], g[e], wz);  // h2 = 0 beyond the plate's ridges
+        for (int e = 0; e < NR; ++e) {
+          wz = fmaf(d.h2[e], g[e], wz);
           g[e] *= rr[e];
           rr[e] *= d.rho[e];
         }
@@ -600,10 +618,41 @@ __device__ __forceinline__ void cx_store(const DeformCoef& d, const CxRow& r, in
         const int col = 8 * q + k + z;
         v[z] = ((bits >> col) & 1u) ? (sinpart ? __sinf(x) : __cosf(x)) : 0.0f;
       }
-      const __nv_bfloat16 h0 = __float2bfloat16_rn(v[0]), h1 = __float2bfloat16_rn(v[1]);
-      h[k / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-      l[k / 2] = bf16_pair(v[0] - __bfloat162float(h0), v[1] - __bfloat162float(h1));
+      split2(v[0], v[1], h[k / 2], l[k / 2]);
     }
+    *reinterpret_cast<uint4*>(hi_row + ((q ^ sw) << 4)) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(lo_row + ((q ^ sw) << 4)) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+// The membrane values of a block's row parts, specialised on the ridge count
+// (0 to 3, uniform over the launch).
+__device__ __forceinline__ void cx_store(const DeformCoef& d, const CxRow& r, int64_t di0, uint32_t bits, int sinpart,
+                                         uint8_t* hi_row, uint8_t* lo_row, int sw, int q0, int nq) {
+  switch (d.n) {
+    case 0: cx_store_n<0>(d, r, di0, bits, sinpart, hi_row, lo_row, sw, q0, nq); break;
+    case 1: cx_store_n<1>(d, r, di0, bits, sinpart, hi_row, lo_row, sw, q0, nq); break;
+    case 2: cx_store_n<2>(d, r, di0, bits, sinpart, hi_row, lo_row, sw, q0, nq); break;
+    default: cx_store_n<3>(d, r, di0, bits, sinpart, hi_row, lo_row, sw, q0, nq); break;
+  }
+}
+
+// A loaded B row (the SA-CZT zoom): 8-column parts q0 .. q0 + nq - 1 of one
+// K block of an FP32 row (src = its first column, or null for a row past the
+// matrix), split into BF16 hi and lo planes like the membrane values.
+__device__ __forceinline__ void ld_store(const float* src, uint8_t* hi_row, uint8_t* lo_row, int sw, int q0, int nq) {
+#pragma unroll 1
+  for (int q = q0; q < q0 + nq; ++q) {
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f), y = x;
+    if (src) {
+      x = __ldg(reinterpret_cast<const float4*>(src + 8 * q));
+      y = __ldg(reinterpret_cast<const float4*>(src + 8 * q + 4));
+    }
+    uint32_t h[4], l[4];
+    split2(x.x, x.y, h[0], l[0]);
+    split2(x.z, x.w, h[1], l[1]);
+    split2(y.x, y.y, h[2], l[2]);
+    split2(y.z, y.w, h[3], l[3]);
     *reinterpret_cast<uint4*>(hi_row + ((q ^ sw) << 4)) = make_uint4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<uint4*>(lo_row + ((q ^ sw) << 4)) = make_uint4(l[0], l[1], l[2], l[3]);
   }
@@ -618,9 +667,10 @@ __device__ __forceinline__ void cx_store(const DeformCoef& d, const CxRow& r, in
 // generator warps form CL phases of 8 / CL warps; phase p generates the stages of
 // the CTA's global K blocks G with G % CL == p, so CL stages are in flight at once
 // and each warp has CL stage times for its rows.
-template <int CL, bool CX>
+template <int CL, bool CX, bool LD = false>
 __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, const __grid_constant__ CUtensorMap tmC1) {
-  // CX: membrane pass (B planes hi and lo per stage, 3 stages); else 4 stages of one B plane
+  // CX: membrane pass (B planes hi and lo per stage, 3 stages); else 4 stages of one B plane.
+  // LD (with CX): the B planes come from a loaded FP32 matrix (a.ld_src) instead of the generator.
   constexpr int NST = CX ? STAGES_CX : STAGES;
   constexpr int BST = CX ? 2 * B_BYTES : B_BYTES;
   // Generator phases: CL (phase p produces the blocks G = p mod CL; with NST =
@@ -631,6 +681,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
   // A phase's previous wait proves block G - PH - NST consumed; the parity wait
   // for block G is exact only if block G - 2 NST is, i.e. if NST >= PH.
   static_assert(PH <= NST, "a generator phase could run two laps ahead of the issuer");
+  static_assert(CX || !LD, "a loaded operand takes the two-plane (membrane) stage layout");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = base;                  // NST x 32 KiB
@@ -725,11 +776,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
       bool ok = true;
       for (int64_t it = u0; it < n_items && ok; it += ustep) {
         const Unit un = unit_at(a, it, npg);
-        {
-          // the epilogue has drained both accumulators of the previous unit
+        const int64_t nch = (un.kb1 - un.kb0 + a.promote - 1) / a.promote;
+        for (int64_t ch = 0; ch < nch && ok; ++ch) {
+          // the epilogue has drained both accumulators of the previous chunk
           if (!mbar_wait(accEmpty, accph ^ 1, abort_flag, a.err, ERR_TIMEOUT_BASE + 2)) { ok = false; break; }
           tc_fence_after();
-          const int64_t kb0 = un.kb0, kb1 = un.kb1;
+          const int64_t kb0 = un.kb0 + ch * a.promote, kb1 = kb0 + a.promote < un.kb1 ? kb0 + a.promote : un.kb1;
           for (int64_t kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait(&fullA[stage], phase, abort_flag, a.err, ERR_TIMEOUT_BASE + 3) ||
                 !(CL > 1 ? mbar_wait_cl(&fullB[stage], phase, abort_flag, a.err, ERR_TIMEOUT_BASE + 4)
@@ -811,7 +863,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
     // block-wise generation (clusters, and every phase-plate pass): the next
     // own block's events and thresholds are prepared (its load issued) before
     // the current block is finished
-    const bool prefetch = CL > 1 || a.level_mode;
+    const bool prefetch = (CL > 1 || a.level_mode) && !LD;
     BlockPrep pre{}, cur{};
     bool have_pre = false;
     for (int64_t G = ph; ui < my_units; G += PH) {
@@ -821,10 +873,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
       if (ui != cur_unit) {
         cur_unit = ui;
         const int64_t s = ustripe;
-        walker_init(w, a.j_begin + s * BN + row, a.j_end, a.mg, a.level_mode != 0);
-        if constexpr (CX) cx_row_init(a.df, a.j_begin + s * BN + row - a.mg.c, cxr);
         state = 0;
-        if constexpr (CL == 1) {
+        if constexpr (!LD) walker_init(w, a.j_begin + s * BN + row, a.j_end, a.mg, a.level_mode != 0);
+        if constexpr (CX && !LD) cx_row_init(a.df, a.j_begin + s * BN + row - a.mg.c, cxr);
+        if constexpr (CL == 1 && !LD) {
           // the sequential walk starts at the unit's first block: skip the
           // events before it; the open state there is their parity
           if (w.ne > 0) {
@@ -854,7 +906,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
       if (!gen_ok[slot]) break;
       uint8_t* rowp = rowbase0 + stage * BST;
       uint32_t wd[16];
-      if constexpr (CX) {
+      if constexpr (LD) {
+        // loaded operand: row j of the source, this block's columns
+        const int64_t j = a.j_begin + ustripe * BN + row;
+        ld_store(j < a.j_end ? a.ld_src + j * a.ld_stride + kb * BK : nullptr, rowp, rowp + B_BYTES, sw,
+                 cp * (4 / NCP), 4 / NCP);
+      } else if constexpr (CX) {
         // membrane pass: T cos(phi) or T sin(phi), hi and lo planes
         uint32_t bits = CL == 1 ? walker_bits(w, kb * BK, state, a.mg.thr) : block_finish(w, kb * BK, a.mg, cur);
         if (a.mg.centre_open) bits = disc_bits(w, kb * BK) & ~bits;
@@ -922,7 +979,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
   } else {
     // ---------------- epilogue: warp w drains tile w/4, TMEM lanes 32(w%4)..+31.
     // Each 32 x 32 piece goes registers -> shared memory (128-byte swizzle) ->
-    // one TMA store (first chunk of a unit) or TMA reduce-add in L2 (later chunks).
+    // one TMA reduce-add into C1 (in L2), once per promotion of the unit.
     const int q = warp >> 2;
     uint8_t* eb = sE + warp * (EPI_BOX * EPI_BOX * 4);
     uint32_t accph = 0;
@@ -931,11 +988,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_dense(const DenseArgs a, con
       const Unit un = unit_at(a, it, npg);
       const int64_t pr = un.pu * CL + rk;
       const int64_t s = un.s;
+      const int64_t nch = (un.kb1 - un.kb0 + a.promote - 1) / a.promote;
       // zero-padding tiles (64 t >= M) have no rows in C1: nothing is stored
       const bool live = (pr * TILES + q) * 64 < (int64_t)a.M;
       const int x0 = (int)(a.j_begin + s * BN - a.c1_j0);       // C1 column of the stripe's first row
       const int y0 = (int)((pr * TILES + q) * BM + (warp & 3) * 32);  // C1 row of lane 0
-      {
+      for (int64_t ch = 0; ch < nch && ok; ++ch) {
         // thread 0 waits for the accumulators; the 8 warps meet at a named barrier
         if (threadIdx.x == 0) epi_ok[accph] = mbar_wait(accFull, accph, abort_flag, a.err, ERR_TIMEOUT_BASE + 6) ? 1 : 0;
         named_bar_sync(1 + 4, EPI_WARPS * 32);
@@ -1128,9 +1186,12 @@ fzp_status c1_tensor_map(const Plan& P, CUtensorMap* tm) {
 
 }  // namespace
 
-fzp_status dense_layout(Plan& P, FormSizes* out) {
+namespace {
+
+// Layout of the dense form's tables for a kernel matrix of `ncols` columns.
+fzp_status layout_cols(Plan& P, int64_t ncols, FormSizes* out) {
   Dense& d = P.dn;
-  d.kblocks = (P.N + BK - 1) / BK;
+  d.kblocks = (ncols + BK - 1) / BK;
   d.ntiles = 2 * P.M / BM;
   const int used = (d.ntiles + TILES - 1) / TILES;  // tile pairs holding ROI rows
   // cluster: CTAs sharing each stripe's mask (default: the largest of 4, 2, 1
@@ -1138,18 +1199,26 @@ fzp_status dense_layout(Plan& P, FormSizes* out) {
   d.cluster = P.cluster_req > 0 ? P.cluster_req : (used % 4 == 0 ? 4 : used % 2 == 0 ? 2 : 1);
   d.npairs = (used + d.cluster - 1) / d.cluster * d.cluster;
   d.promote_kblocks = P.promote_req > 0 ? P.promote_req : 128;  // 4096 samples per TMEM chunk
+  // one promotion per unit: units of several promotions of one stripe
+  // (measured with 4) kept C1's DRAM writes the same and, the clusters of a
+  // wave drifting apart along K, read the kernel matrix 2.7 times as often
+  d.group_kblocks = d.promote_kblocks;
   int dev = 0;
   FZP_CUDA_TRY(cudaGetDevice(&dev));
   FZP_CUDA_TRY(cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev));
   out->A = (size_t)d.npairs * (size_t)d.kblocks * A_BYTES;
-  out->sched = sizeof(int) * (size_t)(3 * ((d.kblocks + d.promote_kblocks - 1) / d.promote_kblocks) + 1);
-  static std::atomic<uint64_t> attr1{0}, attr2{0}, attr4{0}, attr1c{0}, attr2c{0}, attr4c{0};
+  out->sched = sizeof(int) * (size_t)(3 * ((d.kblocks + d.group_kblocks - 1) / d.group_kblocks) + 1);
+  static std::atomic<uint64_t> attr1{0}, attr2{0}, attr4{0}, attr1c{0}, attr2c{0}, attr4c{0}, attr1l{0},
+      attr2l{0}, attr4l{0};
   FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<1, false>, (int)dense_smem_bytes(), attr1));
   FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<2, false>, (int)dense_smem_bytes(), attr2));
   FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<4, false>, (int)dense_smem_bytes(), attr4));
   FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<1, true>, (int)dense_smem_bytes(), attr1c));
   FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<2, true>, (int)dense_smem_bytes(), attr2c));
   FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<4, true>, (int)dense_smem_bytes(), attr4c));
+  FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<1, true, true>, (int)dense_smem_bytes(), attr1l));
+  FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<2, true, true>, (int)dense_smem_bytes(), attr2l));
+  FZP_CUDA_TRY(smem_attr_once((const void*)k_dense<4, true, true>, (int)dense_smem_bytes(), attr4l));
   // The kernel is persistent: launch only CTAs that are resident at once.  A
   // cluster must fit in one GPC, so with clusters fewer than all SMs may hold one.
   d.max_ctas = d.num_sms;
@@ -1174,6 +1243,81 @@ fzp_status dense_layout(Plan& P, FormSizes* out) {
   return FZP_OK;
 }
 
+// Memsets C1, builds the work list and launches k_dense over `a` (its rows and
+// operand source set): mode 0 generated binary or signed mask, 1 membrane
+// pass, 2 loaded operand.  A non-null `name` brackets the launch as the
+// plan's dominant kernel.
+fzp_status run_dense(Plan& P, DenseArgs& a, int mode, const char* name, cudaStream_t s) {
+  const Dense& d = P.dn;
+  const int CL = d.cluster;
+  a.npairs = d.npairs;
+  a.M = P.M;
+  a.kblocks = d.kblocks;
+  a.promote = d.promote_kblocks;
+  a.group = d.group_kblocks;
+  a.A = reinterpret_cast<const uint8_t*>(d.d_A);
+  a.C1 = P.d_C1;
+  a.c1_stride = P.chunk_rows;
+  a.c1_j0 = a.j_begin;
+  a.err = P.d_err;
+  a.nchunks = (int)((d.kblocks + d.group_kblocks - 1) / d.group_kblocks);
+  a.sched = d.d_sched;
+  // every unit adds its promotion into C1 (units of one stripe run in any order)
+  FZP_CUDA_TRY(cudaMemsetAsync(P.d_C1, 0, (size_t)P.c1_rows * (size_t)P.chunk_rows * sizeof(float), s));
+  k_dense_sched<<<1, 1024, 0, s>>>(a, a.npairs / CL, d.d_sched);
+  P.launches += 1;
+  FZP_CUDA_TRY(cudaGetLastError());
+  // a grid of every resident cluster (the work list's length is known on the device only)
+  const int grid = d.max_ctas;
+  CUtensorMap tm;
+  {
+    const fzp_status st = c1_tensor_map(P, &tm);
+    if (st != FZP_OK) return st;
+  }
+  if (name) {
+    P.dominant = name;
+    prof_begin(P, s);
+  }
+  if (CL > 1) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)NUM_THREADS);
+    cfg.dynamicSmemBytes = dense_smem_bytes();
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (mode == 2) {
+      if (CL == 2) FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<2, true, true>, a, tm));
+      else FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<4, true, true>, a, tm));
+    } else if (mode == 1) {
+      if (CL == 2) FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<2, true>, a, tm));
+      else FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<4, true>, a, tm));
+    } else {
+      if (CL == 2) FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<2, false>, a, tm));
+      else FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<4, false>, a, tm));
+    }
+  } else if (mode == 2) {
+    k_dense<1, true, true><<<grid, NUM_THREADS, dense_smem_bytes(), s>>>(a, tm);
+  } else if (mode == 1) {
+    k_dense<1, true><<<grid, NUM_THREADS, dense_smem_bytes(), s>>>(a, tm);
+  } else {
+    k_dense<1, false><<<grid, NUM_THREADS, dense_smem_bytes(), s>>>(a, tm);
+  }
+  if (name) prof_end(P, s);
+  P.launches += 1;
+  FZP_CUDA_TRY(cudaGetLastError());
+  return FZP_OK;
+}
+
+}  // namespace
+
+fzp_status dense_layout(Plan& P, FormSizes* out) { return layout_cols(P, P.N, out); }
+
 fzp_status dense_fill_tables(Plan& P, cudaStream_t s) {
   Dense& d = P.dn;
   k_build_A<<<8 * d.num_sms, 256, 0, s>>>(P.M, P.msh, P.N, d.kblocks, d.npairs, P.c, P.kappa, P.delta,
@@ -1181,6 +1325,33 @@ fzp_status dense_fill_tables(Plan& P, cudaStream_t s) {
   P.launches += 1;
   FZP_CUDA_TRY(cudaGetLastError());
   return FZP_OK;
+}
+
+fzp_status dense_zoom_build(Plan& P, int64_t ncols, int64_t c, double kappa, double delta) {
+  FormSizes z;
+  fzp_status st = layout_cols(P, ncols, &z);
+  if (st != FZP_OK) return st;
+  Dense& d = P.dn;
+  FZP_CUDA_TRY(cudaMalloc(&d.d_A, z.A));
+  FZP_CUDA_TRY(cudaMalloc(&d.d_sched, z.sched));
+  P.device_bytes += z.A + z.sched;
+  k_build_A<<<8 * d.num_sms, 256>>>(P.M, P.msh, ncols, d.kblocks, d.npairs, c, kappa, delta,
+                                    reinterpret_cast<uint8_t*>(d.d_A));
+  P.launches += 1;
+  FZP_CUDA_TRY(cudaGetLastError());
+  return FZP_OK;
+}
+
+fzp_status dense_zoom_rows(Plan& P, const float* src, int64_t rows, int64_t stride, cudaStream_t s) {
+  DenseArgs a{};
+  a.mg = P.mg;
+  a.N = P.dn.kblocks * BK;
+  a.j_begin = 0;
+  a.j_end = rows;
+  a.n_stripes = (rows + BN - 1) / BN;
+  a.ld_src = src;
+  a.ld_stride = stride;
+  return run_dense(P, a, 2, nullptr, s);
 }
 
 fzp_status dense_build_tables(Plan& P) {
@@ -1221,9 +1392,6 @@ fzp_status dense_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
   a.j_begin = j0;
   a.j_end = j0 + rows;
   a.n_stripes = (rows + BN - 1) / BN;
-  const int CL = d.cluster;
-  a.npairs = d.npairs;
-  a.M = P.M;
   a.signed_mask = P.levels == 2 ? 1 : 0;
   const bool cx = P.pass_index >= 0 && P.passes[P.pass_index].cx >= 0;
   a.level_mode = P.pass_index >= 0 && !cx ? 1 : 0;
@@ -1236,58 +1404,8 @@ fzp_status dense_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
     a.cx_sin = P.passes[P.pass_index].cx;
     a.df = deform_coef(P);
   }
-  a.promote = d.promote_kblocks;
   a.hi_only = P.precision == FZP_PREC_BF16 ? 1 : 0;
-  a.A = reinterpret_cast<const uint8_t*>(d.d_A);
-  a.C1 = P.d_C1;
-  a.c1_stride = P.chunk_rows;
-  a.c1_j0 = j0;
-  a.err = P.d_err;
-  a.nchunks = (int)((d.kblocks + d.promote_kblocks - 1) / d.promote_kblocks);
-  a.sched = d.d_sched;
-  // every unit adds its promotion into C1 (units of one stripe run in any order)
-  FZP_CUDA_TRY(cudaMemsetAsync(P.d_C1, 0, (size_t)P.c1_rows * (size_t)P.chunk_rows * sizeof(float), s));
-  k_dense_sched<<<1, 1024, 0, s>>>(a, a.npairs / CL, d.d_sched);
-  P.launches += 1;
-  FZP_CUDA_TRY(cudaGetLastError());
-  // a grid of every resident cluster (the work list's length is known on the device only)
-  const int grid = d.max_ctas;
-  CUtensorMap tm;
-  {
-    const fzp_status st = c1_tensor_map(P, &tm);
-    if (st != FZP_OK) return st;
-  }
-  P.dominant = "dense_tcgen05";
-  prof_begin(P, s);
-  if (CL > 1) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)NUM_THREADS);
-    cfg.dynamicSmemBytes = dense_smem_bytes();
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (cx) {
-      if (CL == 2) FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<2, true>, a, tm));
-      else FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<4, true>, a, tm));
-    } else {
-      if (CL == 2) FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<2, false>, a, tm));
-      else FZP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_dense<4, false>, a, tm));
-    }
-  } else if (cx) {
-    k_dense<1, true><<<grid, NUM_THREADS, dense_smem_bytes(), s>>>(a, tm);
-  } else {
-    k_dense<1, false><<<grid, NUM_THREADS, dense_smem_bytes(), s>>>(a, tm);
-  }
-  prof_end(P, s);
-  P.launches += 1;
-  FZP_CUDA_TRY(cudaGetLastError());
-  return FZP_OK;
+  return run_dense(P, a, cx ? 1 : 0, "dense_tcgen05", s);
 }
 
 }  // namespace fzp

@@ -188,6 +188,7 @@ struct Dense {
   int64_t kblocks = 0;     // ceil(N / 32)
   int ntiles = 0;          // 2M / 128 row tiles of the kernel matrix
   int promote_kblocks = 0; // K blocks per TMEM accumulation chunk
+  int group_kblocks = 0;   // K blocks per work-list chunk (promotions of one unit)
   int npairs = 0;          // kernel tile pairs, padded to a multiple of the cluster size
   int cluster = 1;         // CTAs per cluster sharing each mask tile
   int num_sms = 0;
@@ -207,6 +208,8 @@ struct SaCzt {
   void* d_tw = nullptr;    // P / 2 twiddles e^{-2 pi i t / P}, complex64
   void* d_K = nullptr;     // M x P complex64: Fresnel chirp and zoom kernel
   void* d_RT = nullptr;    // M x P complex64: row pass, transposed
+  int64_t* d_xthr = nullptr;  // exact radii: first s of every zone m = 1 .. nx
+  int64_t nx = 0;
 };
 
 struct Plan {
@@ -271,12 +274,19 @@ fzp_status dense_layout(Plan& P, FormSizes* out);
 fzp_status dense_fill_tables(Plan& P, cudaStream_t s);
 fzp_status dense_build_tables(Plan& P);
 fzp_status dense_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream);
+// The SA-CZT zoom on the tensor cores: kernel images of `ncols` columns with
+// the chirp-kernel phase di^2 kappa / 2 - (m - msh) di delta turns (di = i - c),
+// then row passes over a real FP32 matrix [rows][stride] loaded as the B operand.
+fzp_status dense_zoom_build(Plan& P, int64_t ncols, int64_t c, double kappa, double delta);
+fzp_status dense_zoom_rows(Plan& P, const float* src, int64_t rows, int64_t stride, cudaStream_t stream);
 fzp_status column_pass(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream);
 bool column_pass_tc_applies(const Plan& P);
 // Row pass and column pass of rows [j0, j0 + rows) (every mask pass of a dense
 // phase plate), accumulated into the ROI accumulator.
 fzp_status chunk_passes(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream);
 fzp_status column_pass_tc(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream);
+// The same with the pass's field weighted by (wr + i wi).
+fzp_status column_pass_tc_w(Plan& P, int64_t j0, int64_t rows, double wr, double wi, cudaStream_t stream);
 fzp_status epilogue(Plan& P, void* d_field, int accumulate, cudaStream_t stream);
 // The epilogue with the Fresnel part's distance z in the output chirp and the
 // amplitude dx^2 / (lambda z) (the phase e^{ikf} keeps the focal length).

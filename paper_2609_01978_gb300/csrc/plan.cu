@@ -84,7 +84,7 @@ void release_plan(Plan* P) {
   if (P->owns_buffers) {
     void* ptrs[] = {P->d_C1, P->d_C1d, P->d_Uacc, P->d_err, P->d_metrics,
                     P->bs.d_pre, P->bs.d_H, P->bs.d_Z, P->bs.d_G, P->bs.d_tab, P->dn.d_A, P->dn.d_sched,
-                    P->sa.d_G, P->sa.d_T, P->sa.d_tw, P->sa.d_K, P->sa.d_RT};
+                    P->sa.d_G, P->sa.d_T, P->sa.d_tw, P->sa.d_K, P->sa.d_RT, P->sa.d_xthr};
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }
@@ -297,7 +297,14 @@ cudaError_t workspace_malloc(void** p, size_t bytes) {
 
 // Rows per row-pass chunk: requested (multiple of 256), else as many as an
 // 8 GiB row intermediate holds; never more than the grid (rounded to 256).
+// SA-CZT plans: the padded grid's side (rounded to 256).
 int64_t chunk_rows_for(const Plan& P) {
+  if (P.form == FZP_FORM_SACZT) {
+    // the zoom's row pass covers the padded grid's P rows in one chunk
+    int64_t n = 64;
+    while ((double)n < 1.5 * (double)P.N) n <<= 1;
+    return (n + 255) / 256 * 256;
+  }
   const int64_t M2 = (2 * (int64_t)P.M + 511) / 512 * 512;
   const int64_t budget_rows = (int64_t)((8ull << 30) / (uint64_t)(M2 * (P.precision == FZP_PREC_FP64 ? 8 : 4)));
   int64_t rows = P.stripe_rows > 0 ? (int64_t)P.stripe_rows : budget_rows;

@@ -17,52 +17,62 @@
 //      K[m, u] = e^{i k0 u^2 / (2 z_F) - i k0 x_m u / z_F}: rows, then columns.
 //
 // GB300 mapping: the 2-D transforms are one block per row (the row in shared
-// memory, up to 16384 points = 128 KiB, radix-2 passes) with tiled transposes
-// between the two directions; the phase step and the transposes are HBM
-// passes over the padded grid; the zoom is two FP32 complex products on the
-// CUDA cores (M P^2 and M^2 P complex multiply-adds), accumulated into the
-// FP64 ROI field.  Phases are reduced in FP64 before the FP32 (co)sines.
+// memory, up to 16384 points = 132 KiB with padding), radix-2 stages fused
+// four at a time in registers, forward transforms left in bit-reversed order
+// for the inverse ones to read back; three row kernels (mask + forward;
+// forward + residual phase + inverse; inverse) and two tiled transposes, so
+// the padded grid crosses HBM five times each way.  The zoom (M P^2 and M^2 P complex
+// multiply-adds) is a dense contraction with the structure of the dense
+// form's: K U1 K^T with the kernel K[m][u] above.  For M a multiple of 128 it
+// runs on the tensor cores through the dense form's kernels: the last inverse
+// transform writes U1 as two real planes, each plane is the loaded B operand
+// of one k_dense row pass (split BF16 hi + lo, three products, FP32 tensor
+// memory, C1 by reduce-add) against split-BF16 images of K, and the tensor
+// column pass adds K C1^T into the FP64 ROI field with weight 1 (real plane)
+// or i (imaginary plane).  Other M take two FP32 complex products on the CUDA
+// cores.  The zoom kernel's phases are reduced in FP64 before the FP32
+// (co)sines; the residual phase of step 2, once per grid sample, without FP64.
 #include <cmath>
+#include <vector>
 
 #include "fzp_internal.cuh"
 
 namespace fzp {
 namespace {
 
-constexpr int FFT_THREADS = 1024;
 constexpr int64_t SA_PMAX = 16384;  // rows of the transforms live in shared memory
 
 struct SaMaskArgs {
   MaskGeom mg;  // disc limit, centre, paraxial zone rule, centre configuration
   int64_t N, P, j0, j1;
   int exact;
-  double dx2, f, lambda;
+  const int64_t* xthr;  // exact radii: xthr[m - 1] = smallest s in zone >= m, m = 1 .. nx
+  int64_t nx;
+  float dx2f, ff, lamf;  // FP32 estimate of the exact zone index
 };
 
-// Open state of sample (j, i) (dj = j - c, di = i - c) inside the disc: exact
-// radii (Eq. 3) take the zone index n(r) = 2 (sqrt(f^2 + r^2) - f) / lambda,
-// written as 2 r^2 / (lambda (sqrt(f^2 + r^2) + f)) to avoid the cancellation;
-// paraxial radii the library's exact integer rule.
+// Zone of sample s = dj^2 + di^2 for the exact radii (Eq. 3): the zone index
+// is floor(n(r)), n(r) = 2 (sqrt(f^2 + r^2) - f) / lambda, r^2 = s dx^2.  The
+// host tabulates, by bisection on the same expression in FP64 written without
+// the cancellation (2 r^2 / (lambda (sqrt(f^2 + r^2) + f))), the first s of
+// every zone; here an FP32 estimate of n picks the entry and the table
+// decides.
+__device__ __forceinline__ int64_t zone_exact(const SaMaskArgs& a, int64_t s) {
+  const float r2 = (float)s * a.dx2f;
+  int64_t m = (int64_t)(2.0f * r2 / (a.lamf * (sqrtf(fmaf(a.ff, a.ff, r2)) + a.ff)));
+  m = m < 0 ? 0 : (m > a.nx ? a.nx : m);
+  while (m > 0 && __ldg(a.xthr + m - 1) > s) --m;
+  while (m < a.nx && __ldg(a.xthr + m) <= s) ++m;
+  return m;
+}
+
+// Open state of sample (j, i) (dj = j - c, di = i - c) inside the disc: the
+// exact radii's zone rule above, or the paraxial radii's exact integer rule.
 __device__ __forceinline__ bool sa_open(const SaMaskArgs& a, int64_t dj, int64_t di) {
   const int64_t s = dj * dj + di * di;
   if (s > a.mg.sR) return false;
-  if (!a.exact) return ((zone_of(s, a.mg) ^ a.mg.centre_open) & 1) != 0;
-  const double r2 = (double)s * a.dx2;
-  const double n = 2.0 * r2 / (a.lambda * (sqrt(a.f * a.f + r2) + a.f));
-  return ((((int64_t)floor(n)) ^ (int64_t)a.mg.centre_open) & 1) != 0;
-}
-
-// The mask on the padded grid (rows outside [j0, j1) zero): G[p][q] for
-// aperture sample (j, i) = (p, q) - P/2 + c.
-__global__ void k_sa_mask(SaMaskArgs a, float2* __restrict__ G) {
-  const int64_t total = a.P * a.P, o = a.P / 2 - a.mg.c;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = t / a.P, q = t % a.P;
-    const int64_t j = p - o, i = q - o;
-    float v = 0.0f;
-    if (j >= a.j0 && j < a.j1 && i >= 0 && i < a.N && sa_open(a, j - a.mg.c, i - a.mg.c)) v = 1.0f;
-    G[t] = make_float2(v, 0.0f);
-  }
+  const int64_t z = a.exact ? zone_exact(a, s) : zone_of(s, a.mg);
+  return ((z ^ a.mg.centre_open) & 1) != 0;
 }
 
 // Export of rows [j0, j0 + rows) of the mask (1 open, 0 closed), N per row.
@@ -83,32 +93,106 @@ __global__ void k_sa_twiddles(int64_t P, float2* __restrict__ tw) {
   }
 }
 
-__device__ __forceinline__ int sa_brev(int64_t v, int bits) { return (int)(__brev((unsigned)v) >> (32 - bits)); }
+__device__ __forceinline__ int sa_brev(int v, int bits) { return (int)(__brev((unsigned)v) >> (32 - bits)); }
 
-// In-place P-point FFT of every row (one block per row): bit-reversed load
-// into shared memory, log2 P radix-2 passes, store.  Forward e^{-2 pi i k n / P};
-// inverse the conjugate (no 1/P).
-__global__ void __launch_bounds__(FFT_THREADS) k_sa_fft_rows(float2* __restrict__ data, int64_t P, int logP,
-                                                             const float2* __restrict__ tw, int inverse) {
-  extern __shared__ float2 srow[];
-  float2* row = data + (int64_t)blockIdx.x * P;
-  for (int64_t t = threadIdx.x; t < P; t += blockDim.x) srow[sa_brev(t, logP)] = row[t];
-  __syncthreads();
-  for (int st = 1; st <= logP; ++st) {
-    const int64_t half = 1ll << (st - 1);
-    const int64_t step = P >> st;
-    for (int64_t b = threadIdx.x; b < P / 2; b += blockDim.x) {
-      const int64_t k = b & (half - 1);
-      const int64_t i0 = ((b >> (st - 1)) << st) + k, i1 = i0 + half;
-      float2 w = __ldg(tw + k * step);
-      if (inverse) w.y = -w.y;
-      const float2 u = srow[i0], v = cmul(srow[i1], w);
-      srow[i0] = cadd(u, v);
-      srow[i1] = csub(u, v);
+// Shared-memory slot of element i of a row: one padding slot per 32 keeps
+// the strided group accesses of the late passes within two-way bank
+// conflicts.
+__device__ __forceinline__ int spad(int i) { return i + (i >> 5); }
+
+// One pass of R radix-2 stages of the decimation-in-frequency transform
+// (natural order in, bit-reversed out; twiddles e^{-2 pi i t / P}):
+// halves H, H/2, ..., H / 2^(R-1); each thread takes groups of 2^R elements
+// at stride sig = H / 2^(R-1) and runs the R stages in registers.
+template <int R>
+__device__ __forceinline__ void dif_pass(float2* x, int P, int logP, int H, int lgH, const float2* __restrict__ tw) {
+  constexpr int NE = 1 << R;
+  const int lsig = lgH - (R - 1), sig = 1 << lsig;
+  for (int g = threadIdx.x; g < (P >> R); g += blockDim.x) {
+    const int k0 = g & (sig - 1);
+    const int base = ((g >> lsig) << (lgH + 1)) + k0;
+    float2 v[NE];
+#pragma unroll
+    for (int j = 0; j < NE; ++j) v[j] = x[spad(base + j * sig)];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const int span = 1 << (R - 1 - t);             // pair distance in j; half = sig * span
+      const int tsh = logP - 1 - (lsig + R - 1 - t);  // twiddle step P / (2 half) = 2^tsh
+#pragma unroll
+      for (int j = 0; j < NE; ++j) {
+        if (j & span) continue;
+        const float2 u = v[j], w = v[j + span];
+        const float2 w2 = __ldg(tw + ((k0 + (j & (span - 1)) * sig) << tsh));
+        v[j] = cadd(u, w);
+        v[j + span] = cmul(csub(u, w), w2);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NE; ++j) x[spad(base + j * sig)] = v[j];
+  }
+}
+
+// One pass of R radix-2 stages of the inverse decimation-in-time transform
+// (bit-reversed order in, natural out; twiddles e^{+2 pi i t / P}, no 1/P):
+// halves sig, 2 sig, ..., sig 2^(R-1).
+template <int R>
+__device__ __forceinline__ void dit_inv_pass(float2* x, int P, int logP, int lsig, const float2* __restrict__ tw) {
+  constexpr int NE = 1 << R;
+  const int sig = 1 << lsig;
+  for (int g = threadIdx.x; g < (P >> R); g += blockDim.x) {
+    const int k0 = g & (sig - 1);
+    const int base = ((g >> lsig) << (lsig + R)) + k0;
+    float2 v[NE];
+#pragma unroll
+    for (int j = 0; j < NE; ++j) v[j] = x[spad(base + j * sig)];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const int span = 1 << t;               // half = sig * span
+      const int tsh = logP - 1 - (lsig + t);  // twiddle step P / (2 half)
+#pragma unroll
+      for (int j = 0; j < NE; ++j) {
+        if (j & span) continue;
+        float2 w2 = __ldg(tw + ((k0 + (j & (span - 1)) * sig) << tsh));
+        w2.y = -w2.y;
+        const float2 u = v[j], b = cmul(v[j + span], w2);
+        v[j] = cadd(u, b);
+        v[j + span] = csub(u, b);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NE; ++j) x[spad(base + j * sig)] = v[j];
+  }
+}
+
+// The row in shared memory, forward (bit-reversed result) or inverse (from
+// bit-reversed order), in passes of four stages and one shorter pass.
+__device__ void row_fft_fwd(float2* x, int P, int logP, const float2* __restrict__ tw) {
+  for (int done = 0; done < logP;) {
+    const int r = logP - done < 4 ? logP - done : 4;
+    const int lgH = logP - 1 - done;
+    switch (r) {
+      case 4: dif_pass<4>(x, P, logP, 1 << lgH, lgH, tw); break;
+      case 3: dif_pass<3>(x, P, logP, 1 << lgH, lgH, tw); break;
+      case 2: dif_pass<2>(x, P, logP, 1 << lgH, lgH, tw); break;
+      default: dif_pass<1>(x, P, logP, 1 << lgH, lgH, tw); break;
     }
     __syncthreads();
+    done += r;
   }
-  for (int64_t t = threadIdx.x; t < P; t += blockDim.x) row[t] = srow[t];
+}
+
+__device__ void row_fft_inv(float2* x, int P, int logP, const float2* __restrict__ tw) {
+  for (int done = 0; done < logP;) {
+    const int r = logP - done < 4 ? logP - done : 4;
+    switch (r) {
+      case 4: dit_inv_pass<4>(x, P, logP, done, tw); break;
+      case 3: dit_inv_pass<3>(x, P, logP, done, tw); break;
+      case 2: dit_inv_pass<2>(x, P, logP, done, tw); break;
+      default: dit_inv_pass<1>(x, P, logP, done, tw); break;
+    }
+    __syncthreads();
+    done += r;
+  }
 }
 
 // out[x][y] = in[y][x] for a P x P complex64 matrix (32 x 32 tiles, block 32 x 8).
@@ -120,26 +204,182 @@ __global__ void k_sa_transpose(const float2* __restrict__ in, float2* __restrict
   for (int r = threadIdx.y; r < 32; r += 8) out[(x0 + r) * P + y0 + threadIdx.x] = tile[threadIdx.x][r];
 }
 
-// Step 2 with the 1 / P^2 of the inverse transform: element (a, b) of the
-// spectrum has K = 2 pi (fa, fb) / (P dx), fa the signed frequency index of a.
-// h = k_z - k0 - d K^2 / k_max with k_z - k0 = -K^2 / (k0 + k_z) (c k_max = k0).
-__global__ void k_sa_phase(float2* __restrict__ A, int64_t P, double dx, double k0, double f, double kmax, double d,
-                           float scale) {
-  const int64_t total = P * P;
-  const double dk = 2.0 * 3.14159265358979323846 / ((double)P * dx);
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t a = t / P, b = t % P;
-    const double ka = (double)(a < P / 2 ? a : a - P) * dk, kb = (double)(b < P / 2 ? b : b - P) * dk;
-    const double K2 = ka * ka + kb * kb;
-    float2 v = make_float2(0.0f, 0.0f);
-    if (K2 < k0 * k0) {
-      const double kz = sqrt(k0 * k0 - K2);
-      const double h = -K2 / (k0 + kz) - d * K2 / kmax;
-      const float2 w = cis_turns_f(h * f / (2.0 * 3.14159265358979323846));
-      const float2 x = A[t];
-      v = make_float2(scale * (x.x * w.x - x.y * w.y), scale * (x.x * w.y + x.y * w.x));
+// Step 2's phase in turns, h f / (2 pi), for spectrum sample (a, b) with
+// signed frequency indices (fa, fb) and s = fa^2 + fb^2 (an exact integer):
+// q = K^2 / k0^2 = eps s, eps = (lambda / (P dx))^2, and with z = 1 - sqrt(1 - q)
+// (= K^2 / (k0 (k0 + k_z)), no cancellation) and A = f / lambda,
+//   h f / (2 pi) = -A z - C s,   C = A (d k0 / k_max) eps.
+// It is evaluated without FP64 (FP64 runs at a small fraction of the FP32
+// rate here): z as a float-float pair (Dekker's two-sum and two-product with
+// a fused multiply-add, one correction of the FP32 square root), A z reduced
+// mod 1 in the same pairs, C s mod 1 in 64-bit fixed point.  Absolute error
+// about 1e-7 turns where A z is 1e4 turns (checked against FP64 on the host
+// in the same single-precision steps).
+struct SaPhase {
+  float eh, el;    // eps as a float-float pair
+  float ah, al;    // A as a float-float pair
+  uint64_t cfix;   // |C| 2^64 (|C| < 1)
+  int cneg;        // C < 0
+  int64_t s_ev;    // smallest s with eps s >= 1: evanescent from there
+  float scale;     // 1 / P^2 of the inverse transform
+};
+
+// The error-free transforms use the _rn intrinsics, which the compiler never
+// contracts into fused multiply-adds.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ float sa_turns(const SaPhase& c, int64_t s) {
+  // x = eps s; s < 2^28 splits exactly into two floats, each product exact
+  // as a pair (two-product)
+  const float sh = (float)(s & ~(int64_t)0xFFF), sl = (float)(s & 0xFFF);
+  const float p1 = __fmul_rn(c.eh, sh), p2 = __fmul_rn(c.eh, sl);
+  const float e1 = fmaf(c.eh, sh, -p1), e2 = fmaf(c.eh, sl, -p2);
+  float xh, xl;
+  two_sum(p1, p2, xh, xl);
+  xl = fmaf(c.el, __fadd_rn(sh, sl), __fadd_rn(xl, __fadd_rn(e1, e2)));
+  fast_two_sum(xh, xl, xh, xl);
+  // w = 1 - x, y = sqrt(w) (correctly rounded root, one correction)
+  float wh, wl;
+  two_sum(1.0f, -xh, wh, wl);
+  wl = __fsub_rn(wl, xl);
+  fast_two_sum(wh, wl, wh, wl);  // near the evanescent edge xl is not small against wh
+  const float y0 = __fsqrt_rn(wh);
+  const float y1 = (fmaf(-y0, y0, wh) + wl) * __frcp_rn(y0 + y0);
+  // z = 1 - y
+  float zh, ze;
+  two_sum(1.0f, -y0, zh, ze);
+  float zl = __fsub_rn(ze, y1);
+  fast_two_sum(zh, zl, zh, zl);
+  // A z mod 1
+  const float ph = __fmul_rn(c.ah, zh);
+  const float pl = fmaf(c.ah, zh, -ph) + fmaf(c.ah, zl, c.al * zh);
+  const float t1 = __fsub_rn(ph, rintf(ph)) + pl;
+  // |C| s mod 1
+  const uint64_t prod = c.cfix * (uint64_t)s;
+  const float t2 = (float)(uint32_t)(prod >> 40) * 0x1p-24f;
+  const float t = c.cneg ? t2 - t1 : -t2 - t1;
+  return t - rintf(t);
+}
+
+// The three row kernels of the 2-D transforms, one block per row of the P x P
+// grid, the row in shared memory:
+//   MODE 0: the mask row (step 1's input, generated here: aperture row
+//           j = p - P/2 + c, zero outside [j0, j1)), forward transform;
+//   MODE 1: a row of the transposed spectrum: forward transform along it,
+//           the residual phase of step 2 with the 1 / P^2 of the inverse
+//           transform (evanescent components zeroed), inverse transform;
+//   MODE 2: inverse transform, the result as two real planes (real parts at
+//           planar, imaginary parts at planar + P^2) for the zoom's loaded
+//           operand, or complex rows in place when planar is null.
+// Forward results stay in bit-reversed order along the row, which the
+// phase step and the inverse transforms read as such: no reordering pass.
+struct SaRowArgs {
+  int64_t P;
+  int logP;
+  const float2* tw;  // P / 2 twiddles e^{-2 pi i t / P}
+  SaMaskArgs m;      // MODE 0
+  SaPhase ph;        // MODE 1
+  const float2* in;  // MODES 1, 2 (may equal out)
+  float2* out;       // MODES 0, 1, 2 (complex rows)
+  float* planar;     // MODE 2
+};
+
+// Row <-> shared memory with 16-byte accesses, eight in flight per thread
+// (one block per SM holds a row, so the loads' latency is covered by their
+// number, not by other blocks).
+__device__ __forceinline__ void row_load(float2* x, const float2* __restrict__ src, int P) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  const int n4 = P / 2;
+  for (int b = threadIdx.x; b < n4; b += 8 * blockDim.x) {
+    float4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = b + u * blockDim.x;
+      v[u] = i < n4 ? __ldg(s4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    A[t] = v;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = b + u * blockDim.x;
+      if (i < n4) {
+        x[spad(2 * i)] = make_float2(v[u].x, v[u].y);
+        x[spad(2 * i + 1)] = make_float2(v[u].z, v[u].w);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void row_store(float2* __restrict__ dst, const float2* x, int P) {
+  float4* d4 = reinterpret_cast<float4*>(dst);
+  for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
+    const float2 a = x[spad(2 * i)], b = x[spad(2 * i + 1)];
+    d4[i] = make_float4(a.x, a.y, b.x, b.y);
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(512, 1) k_sa_rows(const SaRowArgs a) {
+  extern __shared__ float2 x[];
+  const int P = (int)a.P, logP = a.logP;
+  const int64_t row = blockIdx.x;
+  if (MODE == 0) {
+    const int64_t o = a.P / 2 - a.m.mg.c;
+    const int64_t j = row - o, dj = j - a.m.mg.c;
+    float2* dst = a.out + row * a.P;
+    if (j < a.m.j0 || j >= a.m.j1 || j < 0 || j >= a.m.N || dj * dj > a.m.mg.sR) {
+      float4* d4 = reinterpret_cast<float4*>(dst);
+      for (int i = threadIdx.x; i < P / 2; i += blockDim.x) d4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      return;
+    }
+    for (int q = threadIdx.x; q < P; q += blockDim.x) {
+      const int64_t i = q - o;
+      const bool open = i >= 0 && i < a.m.N && sa_open(a.m, dj, i - a.m.mg.c);
+      x[spad(q)] = make_float2(open ? 1.0f : 0.0f, 0.0f);
+    }
+    __syncthreads();
+    row_fft_fwd(x, P, logP, a.tw);
+    row_store(dst, x, P);
+    return;
+  }
+  row_load(x, a.in + row * a.P, P);
+  __syncthreads();
+  if (MODE == 1) {
+    row_fft_fwd(x, P, logP, a.tw);
+    // this row is the bit-reversed position of fb; element q of fa
+    const int rb = sa_brev((int)row, logP), fb = rb < P / 2 ? rb : rb - P;
+    for (int q = threadIdx.x; q < P; q += blockDim.x) {
+      const int ra = sa_brev(q, logP), fa = ra < P / 2 ? ra : ra - P;
+      const int64_t s2 = (int64_t)fa * fa + (int64_t)fb * fb;
+      float2 v = make_float2(0.0f, 0.0f);
+      if (s2 < a.ph.s_ev) {
+        float sn, cs;
+        sincospif(2.0f * sa_turns(a.ph, s2), &sn, &cs);
+        const float2 u = x[spad(q)];
+        v = make_float2(a.ph.scale * (u.x * cs - u.y * sn), a.ph.scale * (u.x * sn + u.y * cs));
+      }
+      x[spad(q)] = v;
+    }
+    __syncthreads();
+  }
+  row_fft_inv(x, P, logP, a.tw);
+  if (MODE == 2 && a.planar) {
+    float4* re = reinterpret_cast<float4*>(a.planar + row * a.P);
+    float4* im = reinterpret_cast<float4*>(a.planar + row * a.P + a.P * a.P);
+    for (int i = threadIdx.x; i < P / 4; i += blockDim.x) {
+      const float2 v0 = x[spad(4 * i)], v1 = x[spad(4 * i + 1)], v2 = x[spad(4 * i + 2)], v3 = x[spad(4 * i + 3)];
+      re[i] = make_float4(v0.x, v1.x, v2.x, v3.x);
+      im[i] = make_float4(v0.y, v1.y, v2.y, v3.y);
+    }
+  } else {
+    row_store(a.out + row * a.P, x, P);
   }
 }
 
@@ -217,10 +457,65 @@ SaMaskArgs mask_args(const Plan& P, int64_t j0, int64_t j1) {
   a.j0 = j0;
   a.j1 = j1;
   a.exact = P.sa.exact;
-  a.dx2 = P.dx2;
-  a.f = P.f;
-  a.lambda = P.lambda;
+  a.xthr = P.sa.d_xthr;
+  a.nx = P.sa.nx;
+  a.dx2f = (float)P.dx2;
+  a.ff = (float)P.f;
+  a.lamf = (float)P.lambda;
   return a;
+}
+
+// Zone index of the exact radii (Eq. 3) at s = (r / dx)^2, in FP64.
+int64_t zone_exact_host(const Plan& P, int64_t s) {
+  const double r2 = (double)s * P.dx2;
+  return (int64_t)std::floor(2.0 * r2 / (P.lambda * (std::sqrt(P.f * P.f + r2) + P.f)));
+}
+
+// First s of every zone m = 1 .. (the zone of s_R) of the exact radii, by
+// bisection (the zone index is non-decreasing in s).
+std::vector<int64_t> exact_thresholds(const Plan& P) {
+  std::vector<int64_t> t;
+  const int64_t zmax = zone_exact_host(P, P.mg.sR);
+  for (int64_t m = 1; m <= zmax; ++m) {
+    int64_t lo = t.empty() ? 0 : t.back(), hi = P.mg.sR;  // zone(hi) >= m
+    while (lo < hi) {
+      const int64_t mid = lo + (hi - lo) / 2;
+      if (zone_exact_host(P, mid) >= m) hi = mid;
+      else lo = mid + 1;
+    }
+    t.push_back(lo);
+  }
+  return t;
+}
+
+size_t rows_smem(int64_t P) { return (size_t)(P + P / 32) * sizeof(float2); }
+
+// 512 threads (a group of 16 elements each per pass, two at P = 16384): the
+// 16 values of a group stay in registers without spilling.
+unsigned rows_threads(int64_t P) { return (unsigned)std::max<int64_t>(32, std::min<int64_t>(512, P / 16)); }
+
+// Host constants of k_sa_phase (FP64 here, split into float-float pairs and
+// 64-bit fixed point).
+SaPhase sa_phase_consts(const Plan& P) {
+  const SaCzt& s = P.sa;
+  SaPhase c{};
+  const double lr = P.lambda / ((double)s.P * P.dx);
+  const double eps = lr * lr;
+  const double A = P.f / P.lambda;
+  const double k0 = 2.0 * M_PI / P.lambda;
+  const double C = A * (s.d * k0 / s.kmax) * eps;
+  c.eh = (float)eps;
+  c.el = (float)(eps - (double)c.eh);
+  c.ah = (float)A;
+  c.al = (float)(A - (double)c.ah);
+  c.cneg = C < 0 ? 1 : 0;
+  c.cfix = (uint64_t)std::ldexp(std::fabs(C), 64);
+  int64_t sev = (int64_t)std::ceil(1.0 / eps);
+  while (sev > 0 && eps * (double)(sev - 1) >= 1.0) --sev;
+  while (eps * (double)sev < 1.0) ++sev;
+  c.s_ev = sev;
+  c.scale = (float)(1.0 / ((double)s.P * (double)s.P));
+  return c;
 }
 
 unsigned grid_for(int64_t items) { return (unsigned)std::min<int64_t>((items + 255) / 256, 152 * 32); }
@@ -244,6 +539,9 @@ fzp_status saczt_layout(Plan& P) {
   return FZP_OK;
 }
 
+// The zoom runs on the tensor cores when the column pass's 128-row tiles fit M.
+static bool saczt_zoom_tc(const Plan& P) { return P.M % 128 == 0; }
+
 fzp_status saczt_build(Plan& P) {
   SaCzt& s = P.sa;
   fzp_status st = saczt_layout(P);
@@ -253,15 +551,34 @@ fzp_status saczt_build(Plan& P) {
   FZP_CUDA_TRY(cudaMalloc(&s.d_G, grid));
   FZP_CUDA_TRY(cudaMalloc(&s.d_T, grid));
   FZP_CUDA_TRY(cudaMalloc(&s.d_tw, (size_t)s.P / 2 * sizeof(float2)));
+  P.device_bytes += 2 * grid + (size_t)s.P / 2 * sizeof(float2);
+  static std::atomic<uint64_t> attr0{0}, attr1{0}, attr2{0};
+  FZP_CUDA_TRY(smem_attr_once((const void*)k_sa_rows<0>, (int)rows_smem(SA_PMAX), attr0));
+  FZP_CUDA_TRY(smem_attr_once((const void*)k_sa_rows<1>, (int)rows_smem(SA_PMAX), attr1));
+  FZP_CUDA_TRY(smem_attr_once((const void*)k_sa_rows<2>, (int)rows_smem(SA_PMAX), attr2));
+  if (s.exact) {
+    const std::vector<int64_t> t = exact_thresholds(P);
+    s.nx = (int64_t)t.size();
+    FZP_CUDA_TRY(cudaMalloc(&s.d_xthr, std::max<size_t>(1, t.size()) * sizeof(int64_t)));
+    if (!t.empty())
+      FZP_CUDA_TRY(cudaMemcpy(s.d_xthr, t.data(), t.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    P.device_bytes += t.size() * sizeof(int64_t);
+  }
+  k_sa_twiddles<<<grid_for(s.P / 2), 256>>>(s.P, reinterpret_cast<float2*>(s.d_tw));
+  P.launches += 1;
+  FZP_CUDA_TRY(cudaGetLastError());
+  if (saczt_zoom_tc(P)) {
+    // kernel images of K over the P padded columns: u = (q - P/2) dx, so the
+    // phase is di^2 kappa / 2 - (m - msh) di delta turns with z_F for f
+    const double lz = P.lambda * s.zF;
+    return dense_zoom_build(P, s.P, s.P / 2, P.dx2 / lz, P.p * P.dx / lz);
+  }
   FZP_CUDA_TRY(cudaMalloc(&s.d_K, kern));
   FZP_CUDA_TRY(cudaMalloc(&s.d_RT, kern));
-  P.device_bytes += 2 * grid + 2 * kern + (size_t)s.P / 2 * sizeof(float2);
-  static std::atomic<uint64_t> attr{0};
-  FZP_CUDA_TRY(smem_attr_once((const void*)k_sa_fft_rows, (int)(SA_PMAX * sizeof(float2)), attr));
-  k_sa_twiddles<<<grid_for(s.P / 2), 256>>>(s.P, reinterpret_cast<float2*>(s.d_tw));
+  P.device_bytes += 2 * kern;
   k_sa_kernel<<<grid_for((int64_t)P.M * s.P), 256>>>(P.M, s.P, P.msh, P.p, P.dx, P.lambda * s.zF,
                                                       reinterpret_cast<float2*>(s.d_K));
-  P.launches += 2;
+  P.launches += 1;
   FZP_CUDA_TRY(cudaGetLastError());
   return FZP_OK;
 }
@@ -271,32 +588,53 @@ fzp_status saczt_propagate(Plan& P, int64_t j0, int64_t j1, cudaStream_t st) {
   float2* G = reinterpret_cast<float2*>(s.d_G);
   float2* T = reinterpret_cast<float2*>(s.d_T);
   const float2* tw = reinterpret_cast<const float2*>(s.d_tw);
-  const size_t smem = (size_t)s.P * sizeof(float2);
   const dim3 tgrid((unsigned)(s.P / 32), (unsigned)(s.P / 32)), tblock(32, 8);
-  P.dominant = "saczt_pipeline";
-  prof_begin(P, st);
-  k_sa_mask<<<grid_for(s.P * s.P), 256, 0, st>>>(mask_args(P, j0, j1), G);
-  // FFT2: rows, transpose, rows (the spectrum in transposed layout)
-  k_sa_fft_rows<<<(unsigned)s.P, FFT_THREADS, smem, st>>>(G, s.P, s.logP, tw, 0);
+  const bool tc = saczt_zoom_tc(P);
+  SaRowArgs ra{};
+  ra.P = s.P;
+  ra.logP = s.logP;
+  ra.tw = tw;
+  ra.m = mask_args(P, j0, j1);
+  ra.ph = sa_phase_consts(P);
+  const unsigned nb = (unsigned)s.P, nt = rows_threads(s.P);
+  const size_t smem = rows_smem(s.P);
+  // step 1: mask rows and their forward transforms (G), transposed (T)
+  ra.out = G;
+  k_sa_rows<0><<<nb, nt, smem, st>>>(ra);
   k_sa_transpose<<<tgrid, tblock, 0, st>>>(G, T, s.P);
-  k_sa_fft_rows<<<(unsigned)s.P, FFT_THREADS, smem, st>>>(T, s.P, s.logP, tw, 0);
-  const double k0 = 2.0 * M_PI / P.lambda;
-  k_sa_phase<<<grid_for(s.P * s.P), 256, 0, st>>>(T, s.P, P.dx, k0, P.f, s.kmax, s.d,
-                                                  (float)(1.0 / ((double)s.P * (double)s.P)));
-  // inverse FFT2: rows, transpose back, rows
-  k_sa_fft_rows<<<(unsigned)s.P, FFT_THREADS, smem, st>>>(T, s.P, s.logP, tw, 1);
+  // steps 2-3 along the other axis: forward, residual phase, inverse (T in place)
+  ra.in = T;
+  ra.out = T;
+  P.dominant = "k_sa_rows<1> (forward transforms, residual phase, inverse transforms)";
+  prof_begin(P, st);
+  k_sa_rows<1><<<nb, nt, smem, st>>>(ra);
+  prof_end(P, st);
   k_sa_transpose<<<tgrid, tblock, 0, st>>>(T, G, s.P);
-  k_sa_fft_rows<<<(unsigned)s.P, FFT_THREADS, smem, st>>>(G, s.P, s.logP, tw, 1);
-  // the Fresnel part on the ROI: RT[m][v] = sum_u K[m][u] U1[v][u], then
-  // U[n][m] = sum_v K[n][v] RT[m][v] into the FP64 accumulator
+  // the last inverse rows: U1 in place, or as two real planes in T for the tensor cores
+  ra.in = G;
+  ra.out = G;
+  ra.planar = tc ? reinterpret_cast<float*>(T) : nullptr;
+  k_sa_rows<2><<<nb, nt, smem, st>>>(ra);
+  P.launches += 5;
+  FZP_CUDA_TRY(cudaGetLastError());
+  // the Fresnel part on the ROI: C1[m][v] = sum_u K[m][u] U1[v][u], then
+  // U[n][m] += sum_v K[n][v] C1[m][v] into the FP64 accumulator
+  if (tc) {
+    const float* re = reinterpret_cast<const float*>(T);
+    for (int part = 0; part < 2; ++part) {
+      fzp_status e = dense_zoom_rows(P, re + (size_t)part * s.P * s.P, s.P, s.P, st);
+      if (e == FZP_OK) e = column_pass_tc_w(P, 0, s.P, part ? 0.0 : 1.0, part ? 1.0 : 0.0, st);
+      if (e != FZP_OK) return e;
+    }
+    return FZP_OK;
+  }
   const float2* K = reinterpret_cast<const float2*>(s.d_K);
   float2* RT = reinterpret_cast<float2*>(s.d_RT);
   k_sa_gemm_nt<float2><<<dim3((unsigned)((s.P + 63) / 64), (unsigned)((P.M + 63) / 64)), 256, 0, st>>>(
       K, G, P.M, s.P, s.P, RT);
   k_sa_gemm_nt<double2><<<dim3((unsigned)((P.M + 63) / 64), (unsigned)((P.M + 63) / 64)), 256, 0, st>>>(
       K, RT, P.M, P.M, s.P, P.d_Uacc);
-  prof_end(P, st);
-  P.launches += 11;
+  P.launches += 2;
   FZP_CUDA_TRY(cudaGetLastError());
   return FZP_OK;
 }

@@ -87,3 +87,18 @@ def test_disc_sample_count_of_the_roofline(oracle_mod):
         mid = N // 3
         assert bench.disc_samples(N, c, sR, 0, mid) + bench.disc_samples(N, c, sR, mid, N) == \
             bench.disc_samples(N, c, sR, 0, N)
+
+
+def test_reference_arm_saczt_line():
+    """The SA-CZT workload's reference arm: the oracle's SA-CZT of the 2 mm
+    sample plate, whole, with the sample named."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                          "saczt-d8mm", "--steps", "1", "--warmup", "0"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["config"]["workload"] == "saczt-d8mm"
+    assert d["config"]["sample_N"] == 2529 and "4096^2" in d["cpu_baseline"]["sample"]
+    assert d["e2e"]["value"] == d["value"]

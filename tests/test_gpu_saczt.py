@@ -47,11 +47,13 @@ def test_saczt_matches_oracle(env, exact, D, M):
     assert rel_l2(U, Uref) <= 1e-3
 
 
-def test_saczt_rows_add_and_offaxis(env):
+@pytest.mark.parametrize("M", [64, 128])
+def test_saczt_rows_add_and_offaxis(env, M):
     """Row ranges are linear (two ranges accumulate to the whole plate), and an
-    off-axis ROI origin matches the oracle's."""
+    off-axis ROI origin matches the oracle's; M = 64 takes the CUDA-core zoom,
+    M = 128 the tensor-core one."""
     fzp, torch, O, SA = env
-    g = O.Geometry(D=2e-3, f=10e-3, lam=LAM, M=64, p=LAM * 5 / 8, kind=O.FZP_EXACT)
+    g = O.Geometry(D=2e-3, f=10e-3, lam=LAM, M=M, p=LAM * 5 / 8, kind=O.FZP_EXACT)
     with _plan(fzp, g, 1) as plan:
         U1, _ = run_plan(fzp, torch, plan, g.M, 0, g.N)
         dev = torch.device("cuda:0")
@@ -62,7 +64,7 @@ def test_saczt_rows_add_and_offaxis(env):
         torch.cuda.synchronize()
         assert rel_l2(acc.cpu().numpy(), U1) < 1e-5
     x0 = -(g.M // 2) * g.p + 17.5 * g.p
-    g2 = O.Geometry(D=2e-3, f=10e-3, lam=LAM, M=64, p=LAM * 5 / 8, kind=O.FZP_EXACT, x0=x0)
+    g2 = O.Geometry(D=2e-3, f=10e-3, lam=LAM, M=M, p=LAM * 5 / 8, kind=O.FZP_EXACT, x0=x0)
     with _plan(fzp, g2, 1, x0=x0) as plan:
         _, I = run_plan(fzp, torch, plan, g2.M, 0, g2.N)
     assert rel_l2(I, np.abs(SA.field_saczt(g2)) ** 2) <= 1e-4
