@@ -81,6 +81,10 @@ WORKLOADS = {
     # --train PSFs from the dense membrane passes, --test held out and judged by
     # the plain FP32 CZT
     "surrogate": dict(D=0.2, lam=0.0, fnum=5.0, M=128),
+    # one deformed membrane through the main path: the first config-4 draw
+    # (seed 0) with its deformation scaled onto a D = 0.05 m plate (N = 72,729),
+    # ROI 256^2 (the small case of the membrane-pass profiles)
+    "membrane-d0.05m": dict(D=0.05, lam=0.0, fnum=5.0, M=256, membrane=0),
     # the SA-CZT form (Sec. 3.6, Fig. 5): exact-radii plate (Eq. 3), D = 8 mm at
     # f/# = 5 (N = 10,115, padded grid 16,384^2), exact angular-spectrum residual,
     # Fresnel chirp and zoom onto the 512^2 ROI
@@ -97,10 +101,8 @@ KERNEL_SOURCES = {
     "bluestein": ["bluestein.cu", "fzp_internal.cuh"],
 }
 TRAFFIC = {
-    ("fzp-d0.25m", "dense"): (82.608e9 + 79.682e9,
-                              "44a8a75ba5b1d7274c10bff31019ec239016b446b28da4aef503d52a8bc189e0"),
-    ("fzp-d1m", "dense"): (1818.244e9 + 1258.300e9,
-                           "44a8a75ba5b1d7274c10bff31019ec239016b446b28da4aef503d52a8bc189e0"),
+    ("fzp-d0.25m", "dense"): (83.366e9 + 79.586e9, "4eb750e6dc0dd4810bfe3574cd35b6095ecdf5e8a77c1b38dbd5de158ddde882"),
+    ("fzp-d1m", "dense"): (1977.863e9 + 1258.218e9, "4eb750e6dc0dd4810bfe3574cd35b6095ecdf5e8a77c1b38dbd5de158ddde882"),
 }
 METRIC = "aperture Gsamples/s into 512² ROI, split-BF16 vs FP32 CZT at ≤1e-4 PSF error"
 UNIT = "Gsamples/s"
@@ -383,6 +385,8 @@ def _config(args, wl, N):
            "roi_pitch_m": wl["lam"] * wl["fnum"] / 8, "l2": "256 MiB buffer written between steps (flush)"}
     if wl.get("levels"):
         cfg.update(levels=wl["levels"], dx_m=_dx(wl))
+    if wl.get("deform"):
+        cfg.update(membrane=f"config-4 draw {wl['membrane']} (seed 0) scaled to D", deform=wl["deform"])
     if rows < N:
         cfg["rows_timed"] = f"{rows} central aperture rows of {N} per step (a sample)"
     return cfg
@@ -397,7 +401,23 @@ def _oracle_geometry(O, wl):
     kw = dict(D=wl["D"], f=wl["D"] * wl["fnum"], lam=wl["lam"], M=wl["M"], p=wl["lam"] * wl["fnum"] / 8)
     if wl.get("levels"):
         kw.update(kind=O.FZP_PHASE, levels=wl["levels"], dx=_dx(wl))
+    if wl.get("deform"):
+        kw.update(deform=O.Deform(**wl["deform"]))
     return O.Geometry(**kw)
+
+
+def _resolve(wl):
+    """A membrane workload takes its wavelength and deformation from its seeded
+    config-4 draw, the deformation's lengths scaled from the draw's D to the
+    workload's."""
+    if wl.get("membrane") is None:
+        return wl
+    import fzp_inputs
+    m = fzp_inputs.batch_draws(8, seed=0)[wl["membrane"]]
+    k = wl["D"] / m.D
+    d = dict(amp=m.amp, period=m.period * k, theta=m.theta, taper=m.taper,
+             ridges=[(px * k, py * k, al, h, w * k) for (px, py, al, h, w) in m.ridges])
+    return dict(wl, lam=m.lam, deform=d)
 
 
 def run_reference(args, wl):
@@ -556,7 +576,7 @@ def main():
     ap.add_argument("--rows", type=int, default=0,
                     help="time only this many central aperture rows per step (a sample; 0: all N)")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = _resolve(WORKLOADS[args.workload])
     ws, rank, local = _dist()
 
     if args.impl == "reference":
@@ -612,6 +632,8 @@ def main():
             raise SystemExit("the SA-CZT form transforms the whole padded grid: run it with --replicas")
     if wl.get("levels"):
         params.update(levels=wl["levels"], dx=_dx(wl))
+    if wl.get("deform"):
+        params.update(deform=fzp.make_deform(**wl["deform"]))
     plan = fzp.Plan(**params)
     info = plan.info
     N = info["N"]
@@ -675,13 +697,14 @@ def main():
         # L/2 passes); samples outside the disc carry no work and are skipped
         launches = max(1, prof["dominant_launches"])
         inside = disc_samples(N, info["c"], info["s_R"], j0, j1)
-        flops_launch = 8.0 * M * inside * info["passes"] * args.steps / launches
+        per = 12.0 if wl.get("deform") else 8.0  # a membrane pass takes 3 split products, not 2
+        flops_launch = per * M * inside * info["passes"] * args.steps / launches
         achieved = flops_launch / (avg_ms / 1e3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": _traffic(args.workload, "dense"), "kernel": prof["dominant_name"],
                 "peak_source": peak_kind + " bf16 sustained",
-                "work": "8 M flops per aperture sample inside the disc and mask pass",
+                "work": f"{per:g} M flops per aperture sample inside the disc and mask pass",
                 "disc_samples_per_launch": inside * args.steps / launches}
     elif args.form == "saczt":
         # k_sa_rows<1>: one pass of the padded grid through HBM (P^2 complex64
@@ -762,7 +785,7 @@ def main():
                   "tolerance": 1e-4,
                   f"rel_l2_I_{args.form}": _rel_l2(_rows_intensity(fzp, torch, plan, M, pa, pb_, stream, dev), Iref)}
         airy, lobe = cb.pop("_airy_fwhm"), cb.pop("_lobe_de")
-        if rows == N:
+        if rows == N and not wl.get("deform"):  # the closed forms are the flat plate's
             parity["full_aperture_vs_closed_forms"] = {
                 "fwhm_x_over_airy_minus_1": m["fwhm_x"] / airy - 1,
                 "de_lobe_over_ee_efficiency_minus_1": m["de_lobe"] / lobe - 1}
@@ -801,7 +824,8 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "strong" if sharded else "weak",
-           "vs_baseline": None, "dtype": dtype, "data": "synthetic (procedural binary zone plate)",
+           "vs_baseline": None, "dtype": dtype,
+           "data": "synthetic (procedural zone plate" + (", seeded membrane deformation)" if wl.get("deform") else ")"),
            "config": _config(args, wl, N),
            "roofline": roof, "e2e": e2e, "gpu_launches": prof["kernel_launches"], "clocks": clocks,
            "metrics_last_step": {k: m[k] for k in ("fwhm_x", "de_lobe", "mtf_half_cut")}}
