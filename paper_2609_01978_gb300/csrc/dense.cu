@@ -554,11 +554,6 @@ __device__ __forceinline__ void cx_row_init(const DeformCoef& d, int64_t dj, CxR
   for (int e = 0; e < 3; ++e) r.cr[e] = (fj - d.pj[e]) * d.ny[e] - d.pi_[e] * d.nx[e];
 }
 
-__device__ __forceinline__ uint32_t bf16_pair(float a, float b) {
-  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
-         ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
-}
-
 // Two FP32 values -> packed BF16 hi (RN) and lo (RN of the remainder), lower
 // half from a: one cvt.rn.bf16x2 per plane (a goes to the upper half of the
 // instruction's result when given first, so b is given first).
@@ -1240,7 +1235,34 @@ fzp_status layout_cols(Plan& P, int64_t ncols, FormSizes* out) {
     if (nclusters < 1) return set_error(FZP_E_UNSUPPORTED, "no %d-CTA cluster of the dense kernel fits", d.cluster);
     d.max_ctas = std::min(nclusters * d.cluster, d.num_sms / d.cluster * d.cluster);
   }
+  d.extra_ctas = d.cluster > 1 ? d.num_sms - d.max_ctas : 0;
   return FZP_OK;
+}
+
+// Rows [jm, j_end) for the single-CTA launch on the SMs that hold no whole
+// cluster: a stripe-aligned band at the end of the range carrying about the
+// share of the disc's area those SMs can take (each at `eff` of a cluster
+// CTA's rate).  Returns j_end when the band would be empty.
+int64_t extra_band(const Plan& P, int64_t j_begin, int64_t j_end, double eff) {
+  const Dense& d = P.dn;
+  const double R = std::sqrt((double)P.mg.sR);
+  auto F = [&](double y) {  // area of the disc below row offset y (continuous)
+    y = std::max(-R, std::min(R, y));
+    return y * std::sqrt(std::max(0.0, R * R - y * y)) + R * R * std::asin(y / R);
+  };
+  const double y0 = (double)(j_begin - P.c) - 0.5, y1 = (double)(j_end - P.c) - 0.5;
+  const double total = F(y1) - F(y0);
+  if (!(total > 0)) return j_end;
+  const double share = d.extra_ctas * eff / (d.max_ctas + d.extra_ctas * eff);
+  double lo = y0, hi = y1;  // F(y1) - F(y) = share * total
+  for (int it = 0; it < 60; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (F(y1) - F(mid) > share * total) lo = mid;
+    else hi = mid;
+  }
+  int64_t jm = (int64_t)std::llround(hi + 0.5) + P.c;
+  jm = j_begin + (jm - j_begin + BN / 2) / BN * BN;  // whole stripes of the main launch
+  return jm <= j_begin || jm >= j_end ? j_end : jm;   // no band unless both launches get rows
 }
 
 // Memsets C1, builds the work list and launches k_dense over `a` (its rows and
@@ -1249,6 +1271,13 @@ fzp_status layout_cols(Plan& P, int64_t ncols, FormSizes* out) {
 // plan's dominant kernel.
 fzp_status run_dense(Plan& P, DenseArgs& a, int mode, const char* name, cudaStream_t s) {
   const Dense& d = P.dn;
+  // binary and phase-plate passes of a single plan also use the SMs left over
+  // by the clusters: a single-CTA launch on a second stream takes a band of
+  // stripes, both add into C1
+  // (a single CTA, walking its 256 rows alone, runs at about 0.64 of a
+  // cluster CTA's rate: measured, each launch timed alone at D = 0.25 m)
+  const int64_t jm = (mode == 0 && d.d_sched2 && d.extra_ctas > 0) ? extra_band(P, a.j_begin, a.j_end, 0.62)
+                                                                    : a.j_end;
   const int CL = d.cluster;
   a.npairs = d.npairs;
   a.M = P.M;
@@ -1262,11 +1291,21 @@ fzp_status run_dense(Plan& P, DenseArgs& a, int mode, const char* name, cudaStre
   a.err = P.d_err;
   a.nchunks = (int)((d.kblocks + d.group_kblocks - 1) / d.group_kblocks);
   a.sched = d.d_sched;
+  DenseArgs b = a;  // the band [jm, j_end) of the single-CTA launch (same C1 columns)
+  b.j_begin = jm;
+  b.n_stripes = (b.j_end - jm + BN - 1) / BN;
+  b.sched = d.d_sched2;
+  a.j_end = jm;
+  a.n_stripes = (jm - a.j_begin + BN - 1) / BN;
+  const bool split = jm < b.j_end;
   // every unit adds its promotion into C1 (units of one stripe run in any order)
   FZP_CUDA_TRY(cudaMemsetAsync(P.d_C1, 0, (size_t)P.c1_rows * (size_t)P.chunk_rows * sizeof(float), s));
   k_dense_sched<<<1, 1024, 0, s>>>(a, a.npairs / CL, d.d_sched);
   P.launches += 1;
   FZP_CUDA_TRY(cudaGetLastError());
+  // the band's stream starts after the main work list is built (C1 zeroed),
+  // so the cluster launch is ready first and its clusters are placed first
+  if (split) FZP_CUDA_TRY(cudaEventRecord(d.ev_fork, s));
   // a grid of every resident cluster (the work list's length is known on the device only)
   const int grid = d.max_ctas;
   CUtensorMap tm;
@@ -1275,7 +1314,7 @@ fzp_status run_dense(Plan& P, DenseArgs& a, int mode, const char* name, cudaStre
     if (st != FZP_OK) return st;
   }
   if (name) {
-    P.dominant = name;
+    P.dominant = split ? "k_dense (cluster launch + single-CTA band on the leftover SMs, concurrent)" : name;
     prof_begin(P, s);
   }
   if (CL > 1) {
@@ -1307,6 +1346,15 @@ fzp_status run_dense(Plan& P, DenseArgs& a, int mode, const char* name, cudaStre
     k_dense<1, true><<<grid, NUM_THREADS, dense_smem_bytes(), s>>>(a, tm);
   } else {
     k_dense<1, false><<<grid, NUM_THREADS, dense_smem_bytes(), s>>>(a, tm);
+  }
+  if (split) {
+    // the band on the leftover SMs; joined before the launch's end is read
+    FZP_CUDA_TRY(cudaStreamWaitEvent(d.s2, d.ev_fork, 0));
+    k_dense_sched<<<1, 1024, 0, d.s2>>>(b, b.npairs, d.d_sched2);
+    k_dense<1, false><<<d.extra_ctas, NUM_THREADS, dense_smem_bytes(), d.s2>>>(b, tm);
+    FZP_CUDA_TRY(cudaEventRecord(d.ev_join, d.s2));
+    FZP_CUDA_TRY(cudaStreamWaitEvent(s, d.ev_join, 0));
+    P.launches += 2;
   }
   if (name) prof_end(P, s);
   P.launches += 1;
@@ -1361,6 +1409,13 @@ fzp_status dense_build_tables(Plan& P) {
   FZP_CUDA_TRY(cudaMalloc(&P.dn.d_A, z.A));
   FZP_CUDA_TRY(cudaMalloc(&P.dn.d_sched, z.sched));
   P.device_bytes += z.A + z.sched;
+  if (P.dn.extra_ctas > 0) {
+    FZP_CUDA_TRY(cudaMalloc(&P.dn.d_sched2, z.sched));
+    FZP_CUDA_TRY(cudaStreamCreateWithFlags(&P.dn.s2, cudaStreamNonBlocking));
+    FZP_CUDA_TRY(cudaEventCreateWithFlags(&P.dn.ev_fork, cudaEventDisableTiming));
+    FZP_CUDA_TRY(cudaEventCreateWithFlags(&P.dn.ev_join, cudaEventDisableTiming));
+    P.device_bytes += z.sched;
+  }
   return dense_fill_tables(P, 0);
 }
 

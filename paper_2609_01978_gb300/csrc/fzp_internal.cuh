@@ -194,6 +194,12 @@ struct Dense {
   int num_sms = 0;
   int max_ctas = 0;        // CTAs that can be resident at once (whole clusters)
   int* d_sched = nullptr;  // work list of a row-pass launch (3 nchunks + 1 ints)
+  // SMs that hold no whole cluster: a concurrent single-CTA launch takes a
+  // band of stripes there (single plans of cluster launches only)
+  int extra_ctas = 0;
+  int* d_sched2 = nullptr;
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 // SA-CZT (Sec. 3.6, Fig. 5): padded grid and its buffers.

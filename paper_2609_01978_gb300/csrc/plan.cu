@@ -81,6 +81,10 @@ void release_plan(Plan* P) {
     cudaEventDestroy(e.second);
   }
   if (P->d_thr) cudaFree(P->d_thr);
+  if (P->dn.d_sched2) cudaFree(P->dn.d_sched2);
+  if (P->dn.ev_fork) cudaEventDestroy(P->dn.ev_fork);
+  if (P->dn.ev_join) cudaEventDestroy(P->dn.ev_join);
+  if (P->dn.s2) cudaStreamDestroy(P->dn.s2);
   if (P->owns_buffers) {
     void* ptrs[] = {P->d_C1, P->d_C1d, P->d_Uacc, P->d_err, P->d_metrics,
                     P->bs.d_pre, P->bs.d_H, P->bs.d_Z, P->bs.d_G, P->bs.d_tab, P->dn.d_A, P->dn.d_sched,

@@ -106,3 +106,31 @@ def test_saczt_rejects(env):
         with pytest.raises(fzp.FzpError) as e:
             fzp.Plan(**base, **kw)
         assert e.value.status == status, kw
+
+
+def test_saczt_bench_plate_vs_stored_oracle(env):
+    """The SA-CZT bench workload in the bench's launch configuration: the
+    8 mm exact-radii plate (N = 10,115, padded grid 16,384^2, ROI 512^2,
+    tensor-core zoom) against the oracle's FP64 SA-CZT field of the whole
+    plate (tests/golden/saczt_d8mm_field.npy, written by
+    tests/golden/make_saczt_oracle.py): relative L2 of I <= 1e-4, FWHM within
+    0.01 % and lobe DE within 0.01 percentage points of the oracle's extractor
+    on the oracle's field."""
+    import json
+    import os
+    fzp, torch, O, SA = env
+    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    meta = json.load(open(os.path.join(golden, "saczt_d8mm.json")))
+    Uref = np.load(os.path.join(golden, meta["field_file"])).astype(np.complex128)
+    mref = meta["metrics_fp64"]
+    g = O.Geometry(D=8e-3, f=40e-3, lam=LAM, M=512, p=LAM * 5 / 8, kind=O.FZP_EXACT)
+    with _plan(fzp, g, 1) as plan:
+        assert plan.info["fft_length"] == meta["geometry"]["P"] == 16384
+        U, I = run_plan(fzp, torch, plan, g.M, 0, g.N)
+        m = plan.metrics(torch.from_numpy(U).to("cuda:0"))
+    err = rel_l2(I, np.abs(Uref) ** 2)
+    print(f"SA-CZT 8 mm plate: rel L2 of I {err:.3e}, of U {rel_l2(U, Uref):.3e}, "
+          f"FWHM {m['fwhm_x'] / mref['fwhm_x'] - 1:.2e}, DE {m['de_lobe'] - mref['de_lobe']:.2e}")
+    assert err <= 1e-4
+    assert abs(m["fwhm_x"] / mref["fwhm_x"] - 1) < 1e-4
+    assert abs(m["de_lobe"] - mref["de_lobe"]) < 1e-4
