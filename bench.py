@@ -17,7 +17,8 @@ focus.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--form dense|bluestein]
                   [--impl ours|reference] [--workload NAME] [--rows R]
                   [--plain-rows R] [--e2e-steps E] [--no-plain] [--no-cpu-baseline]
-                  [--ref-rows R] [--instances I] [--replicas]
+                  [--ref-rows R] [--instances I] [--seed S] [--replicas]
+                  [--train T] [--test E] [--flat F] [--train-steps S]
 
 Workloads: fzp-d0.05m (small case for profiler captures), fzp-d0.25m,
 fzp-d1m ... fzp-d5m (the D sweep at f/# = 5), fzp-t1 ... fzp-t5 (the phase
@@ -94,15 +95,18 @@ WORKLOADS = {
 # D = 2 mm plate (N = 2,529, padded grid 4096^2), whole, repeated
 SACZT_SAMPLE_D = 2e-3
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the dominant kernel, from a one-pass ncu capture of this workload; reported
-# only while the kernel's sources hash to what was captured (null otherwise).
+# the dominant kernel (for the dense form: one row pass, both of its
+# launches), from a one-pass ncu capture of this workload; reported only while
+# the kernel's sources hash to what was captured (null otherwise).
 KERNEL_SOURCES = {
     "dense": ["dense.cu", "tc_ptx.cuh", "fzp_internal.cuh"],
     "bluestein": ["bluestein.cu", "fzp_internal.cuh"],
 }
 TRAFFIC = {
-    ("fzp-d0.25m", "dense"): (83.366e9 + 79.586e9, "4eb750e6dc0dd4810bfe3574cd35b6095ecdf5e8a77c1b38dbd5de158ddde882"),
-    ("fzp-d1m", "dense"): (1977.863e9 + 1258.218e9, "4eb750e6dc0dd4810bfe3574cd35b6095ecdf5e8a77c1b38dbd5de158ddde882"),
+    # both launches of a row pass (the cluster launch and the single-CTA band
+    # on the leftover SMs), captured one after the other
+    ("fzp-d0.25m", "dense"): (80.086e9 + 76.915e9 + 2.096e9 + 1.919e9, "33e229776226efa01fcb512edb40a45c1fe1e6f968fc539c0d67fa55a905efb0"),
+    ("fzp-d1m", "dense"): (1694.948e9 + 1216.615e9 + 44.293e9 + 41.776e9, "33e229776226efa01fcb512edb40a45c1fe1e6f968fc539c0d67fa55a905efb0"),
 }
 METRIC = "aperture Gsamples/s into 512² ROI, split-BF16 vs FP32 CZT at ≤1e-4 PSF error"
 UNIT = "Gsamples/s"
@@ -214,7 +218,7 @@ def run_membranes(args, fzp, torch, dev, ws, pg, rank, local):
     import fzp_inputs
     wl = WORKLOADS["membranes"]
     fnum, M = wl["fnum"], wl["M"]
-    mem = fzp_inputs.batch_draws(256, seed=0)[:args.instances]
+    mem = fzp_inputs.batch_draws(256, seed=args.seed)[:args.instances]
     probs = [dict(D=m.D, f=fnum * m.D, lam=m.lam, M=M, pitch=m.lam * fnum / 8, precision=fzp.PREC_AUTO_1E4,
                   deform=fzp.make_deform(m.amp, m.period, m.theta, m.taper, m.ridges)) for m in mem]
     stream = torch.cuda.current_stream(dev)
@@ -303,7 +307,7 @@ def run_membranes(args, fzp, torch, dev, ws, pg, rank, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "mixed (autotuned per instance)",
             "data": "synthetic (seeded deformed membranes)",
-            "config": {"workload": "membranes", "instances": len(probs), "of": 256, "seed": 0, "roi": M,
+            "config": {"workload": "membranes", "instances": len(probs), "of": 256, "seed": args.seed, "roi": M,
                        "f_number": fnum, "samples_per_step": samples, "forms": forms,
                        "l2": "256 MiB buffer written between steps (flush)"},
             "roofline": roof, "e2e": e2e, "gpu_launches": kernels * args.steps, "clocks": clocks,
@@ -569,6 +573,7 @@ def main():
     ap.add_argument("--replicas", action="store_true",
                     help="N > 1: every rank propagates the whole aperture (weak scaling) instead of its rows")
     ap.add_argument("--instances", type=int, default=256, help="membranes workload: instances per batch")
+    ap.add_argument("--seed", type=int, default=0, help="membranes workload: seed of the 256 draws (0: config 4's)")
     ap.add_argument("--train", type=int, default=768, help="surrogate workload: training PSFs")
     ap.add_argument("--test", type=int, default=64, help="surrogate workload: held-out PSFs (judged by the plain CZT)")
     ap.add_argument("--flat", type=int, default=32, help="surrogate workload: held-out PSFs of the flat baseline")

@@ -1239,12 +1239,17 @@ fzp_status layout_cols(Plan& P, int64_t ncols, FormSizes* out) {
   return FZP_OK;
 }
 
-// Rows [jm, j_end) for the single-CTA launch on the SMs that hold no whole
-// cluster: a stripe-aligned band at the end of the range carrying about the
-// share of the disc's area those SMs can take (each at `eff` of a cluster
-// CTA's rate).  Returns j_end when the band would be empty.
-int64_t extra_band(const Plan& P, int64_t j_begin, int64_t j_end, double eff) {
+// The band of rows for the single-CTA launch on the SMs that hold no whole
+// cluster: stripe-aligned, at the end of the row range farther from the axis
+// and only where that end reaches the rim (there a row's chord is short and
+// crosses few zone boundaries per block, and a single CTA, which generates
+// all 256 rows of each of its units alone, keeps `eff` of a cluster CTA's
+// rate: 0.64 measured at the rim, 0.51 across the middle of the disc), sized
+// to the share of the disc's area the leftover SMs can take.  Sets [b0, b1);
+// empty (b0 = b1) when there is no band.
+void extra_band(const Plan& P, int64_t j_begin, int64_t j_end, double eff, int64_t& b0, int64_t& b1) {
   const Dense& d = P.dn;
+  b0 = b1 = j_end;
   const double R = std::sqrt((double)P.mg.sR);
   auto F = [&](double y) {  // area of the disc below row offset y (continuous)
     y = std::max(-R, std::min(R, y));
@@ -1252,17 +1257,24 @@ int64_t extra_band(const Plan& P, int64_t j_begin, int64_t j_end, double eff) {
   };
   const double y0 = (double)(j_begin - P.c) - 0.5, y1 = (double)(j_end - P.c) - 0.5;
   const double total = F(y1) - F(y0);
-  if (!(total > 0)) return j_end;
-  const double share = d.extra_ctas * eff / (d.max_ctas + d.extra_ctas * eff);
-  double lo = y0, hi = y1;  // F(y1) - F(y) = share * total
+  const bool at_end = std::fabs(y1) >= std::fabs(y0);
+  if (!(total > 0) || std::fabs(at_end ? y1 : y0) < 0.95 * R) return;
+  const double want = d.extra_ctas * eff / (d.max_ctas + d.extra_ctas * eff) * total;
+  double lo = y0, hi = y1;  // the band's inner edge y: its area from the outer end is `want`
   for (int it = 0; it < 60; ++it) {
     const double mid = 0.5 * (lo + hi);
-    if (F(y1) - F(mid) > share * total) lo = mid;
+    const double area = at_end ? F(y1) - F(mid) : F(mid) - F(y0);
+    if ((area > want) == at_end) lo = mid;
     else hi = mid;
   }
-  int64_t jm = (int64_t)std::llround(hi + 0.5) + P.c;
-  jm = j_begin + (jm - j_begin + BN / 2) / BN * BN;  // whole stripes of the main launch
-  return jm <= j_begin || jm >= j_end ? j_end : jm;   // no band unless both launches get rows
+  int64_t jm = (int64_t)std::llround(0.5 * (lo + hi) + 0.5) + P.c;
+  jm = j_begin + (jm - j_begin + BN / 2) / BN * BN;  // whole stripes for both launches
+  if (jm <= j_begin || jm >= j_end) return;
+  if (at_end) b0 = jm;
+  else {
+    b0 = j_begin;
+    b1 = jm;
+  }
 }
 
 // Memsets C1, builds the work list and launches k_dense over `a` (its rows and
@@ -1274,10 +1286,8 @@ fzp_status run_dense(Plan& P, DenseArgs& a, int mode, const char* name, cudaStre
   // binary and phase-plate passes of a single plan also use the SMs left over
   // by the clusters: a single-CTA launch on a second stream takes a band of
   // stripes, both add into C1
-  // (a single CTA, walking its 256 rows alone, runs at about 0.64 of a
-  // cluster CTA's rate: measured, each launch timed alone at D = 0.25 m)
-  const int64_t jm = (mode == 0 && d.d_sched2 && d.extra_ctas > 0) ? extra_band(P, a.j_begin, a.j_end, 0.62)
-                                                                    : a.j_end;
+  int64_t b0 = a.j_end, b1 = a.j_end;
+  if (mode == 0 && d.d_sched2 && d.extra_ctas > 0) extra_band(P, a.j_begin, a.j_end, 0.62, b0, b1);
   const int CL = d.cluster;
   a.npairs = d.npairs;
   a.M = P.M;
@@ -1291,13 +1301,17 @@ fzp_status run_dense(Plan& P, DenseArgs& a, int mode, const char* name, cudaStre
   a.err = P.d_err;
   a.nchunks = (int)((d.kblocks + d.group_kblocks - 1) / d.group_kblocks);
   a.sched = d.d_sched;
-  DenseArgs b = a;  // the band [jm, j_end) of the single-CTA launch (same C1 columns)
-  b.j_begin = jm;
-  b.n_stripes = (b.j_end - jm + BN - 1) / BN;
+  const bool split = b0 < b1;
+  DenseArgs b = a;  // the band [b0, b1) of the single-CTA launch (same C1 columns)
+  b.j_begin = b0;
+  b.j_end = b1;
+  b.n_stripes = (b1 - b0 + BN - 1) / BN;
   b.sched = d.d_sched2;
-  a.j_end = jm;
-  a.n_stripes = (jm - a.j_begin + BN - 1) / BN;
-  const bool split = jm < b.j_end;
+  if (split) {
+    if (b0 == a.j_begin) a.j_begin = b1;
+    else a.j_end = b0;
+    a.n_stripes = (a.j_end - a.j_begin + BN - 1) / BN;
+  }
   // every unit adds its promotion into C1 (units of one stripe run in any order)
   FZP_CUDA_TRY(cudaMemsetAsync(P.d_C1, 0, (size_t)P.c1_rows * (size_t)P.chunk_rows * sizeof(float), s));
   k_dense_sched<<<1, 1024, 0, s>>>(a, a.npairs / CL, d.d_sched);
