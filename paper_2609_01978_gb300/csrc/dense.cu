@@ -1328,7 +1328,7 @@ fzp_status run_dense(Plan& P, DenseArgs& a, int mode, const char* name, cudaStre
     if (st != FZP_OK) return st;
   }
   if (name) {
-    P.dominant = split ? "k_dense (cluster launch + single-CTA band on the leftover SMs, concurrent)" : name;
+    P.dominant = split ? "k_dense clusters + single-CTA band" : name;
     prof_begin(P, s);
   }
   if (CL > 1) {
