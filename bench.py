@@ -212,6 +212,26 @@ def bluestein_f2_flops(info: dict, rows: int) -> float:
     return rows * L1 * (10.0 * L2 * lg + 6.0 * L2)
 
 
+def partitioned_flops(info: dict, j0: int, j1: int) -> float:
+    """Algorithmic FP32 flops of the partitioned row pass over rows [j0, j1):
+    per block of S columns that meets a row's disc chord, one forward
+    4096-point FFT (5 P log2 P) and the spectrum product-sum (8 P); per row one
+    inverse 4096-point FFT.  S = 256 min(15, floor((4097 - M) / 256))."""
+    import numpy as np
+    P, lgP = 4096, 12
+    S = 256 * min(15, (4097 - info["M"]) // 256)
+    N, c, s_R = info["N"], info["c"], info["s_R"]
+    rem = s_R - (np.arange(j0, j1, dtype=np.int64) - c) ** 2
+    rem = rem[rem >= 0]
+    b = np.floor(np.sqrt(rem.astype(np.float64))).astype(np.int64)  # exact after the corrections
+    b -= (b * b > rem).astype(np.int64)
+    b += ((b + 1) * (b + 1) <= rem).astype(np.int64)
+    lo, hi = np.maximum(c - b, 0), np.minimum(c + b, N - 1)
+    blocks = float(np.sum(hi // S - lo // S + 1))
+    fft = 5.0 * P * lgP
+    return blocks * (fft + 8.0 * P) + (j1 - j0) * fft
+
+
 def run_membranes(args, fzp, torch, dev, ws, pg, rank, local):
     """Config 4: a batch of deformed membranes (autotuned form per instance), the
     whole batch replayed as one CUDA graph, metrics of every instance per step."""
@@ -387,6 +407,8 @@ def _config(args, wl, N):
     cfg = {"workload": args.workload, "form": args.form, "D_m": wl["D"], "lambda_m": wl["lam"],
            "f_number": wl["fnum"], "N": N, "samples_per_step": rows * N, "roi": wl["M"],
            "roi_pitch_m": wl["lam"] * wl["fnum"] / 8, "l2": "256 MiB buffer written between steps (flush)"}
+    if args.form == "bluestein":
+        cfg["conv"] = args.conv
     if wl.get("levels"):
         cfg.update(levels=wl["levels"], dx_m=_dx(wl))
     if wl.get("deform"):
@@ -564,6 +586,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fzp-d1m", choices=sorted(WORKLOADS))
     ap.add_argument("--form", default="dense", choices=["dense", "bluestein", "saczt"])
+    ap.add_argument("--conv", default="partitioned", choices=["partitioned", "single"],
+                    help="--form bluestein: the row convolution (fzp_params.conv)")
     ap.add_argument("--ref-rows", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -631,6 +655,8 @@ def main():
     else:
         form, prec, dtype = fzp.FORM_BLUESTEIN, fzp.PREC_FP32, "f32"
     params = dict(D=D, f=D * fnum, lam=lam, M=M, pitch=lam * fnum / 8, form=form, precision=prec)
+    if args.form == "bluestein":
+        params.update(conv=fzp.CONV_SINGLE if args.conv == "single" else fzp.CONV_PARTITIONED)
     if args.form == "saczt":
         params.update(exact_radii=1)
         if ws > 1 and not args.replicas:
@@ -723,12 +749,18 @@ def main():
                 "work": "16 P^2 bytes per launch (P = padded grid side)"}
     else:
         launches = max(1, prof["dominant_launches"])
-        rows_per_launch = rows * args.steps / launches
-        flops_launch = bluestein_f2_flops(info, rows_per_launch)
+        if info["conv"] == 2:
+            flops_launch = partitioned_flops(info, j0, j1) * args.steps / launches
+            work = ("per block of S columns meeting a row's chord 5 P log2 P + 8 P, per row 5 P log2 P "
+                    "(P = 4096)")
+        else:
+            flops_launch = bluestein_f2_flops(info, rows * args.steps / launches)
+            work = "per row L1 (10 L2 log2 L2 + 6 L2)"
         achieved = flops_launch / (avg_ms / 1e3) / 1e12
         peak = SM_COUNT * 128 * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12  # FP32 FMA lanes x clock
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": _traffic(args.workload, "bluestein"), "kernel": prof["dominant_name"],
+                "traffic": _traffic(args.workload, "bluestein") if info["conv"] == 1 else None,
+                "kernel": prof["dominant_name"], "work": work,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
 
     # end to end through the public API with host buffers: plan from host
@@ -797,30 +829,45 @@ def main():
     plan.close()
 
     # the plain FP32 Bluestein form on the same workload (the metric compares
-    # the split-BF16 dense form with it): one warm and one timed step
-    plain = None
+    # the split-BF16 dense form with it), both of its row convolutions:
+    # partitioned (the library's FP32 default) and single (one L-point
+    # convolution per row, the paper's structure); one warm and one timed
+    # step each, on the whole aperture or on 16 stripes spread evenly over it
+    plain = {}
     if args.form == "dense" and not args.no_plain:
         prow = args.plain_rows if args.plain_rows >= 0 else (0 if N <= 316057 else 16384)
         rows = N if prow <= 0 else min(N, prow)
-        r0 = (N - rows) // 2
-        with fzp.Plan(**dict(params, form=fzp.FORM_BLUESTEIN, precision=fzp.PREC_FP32)) as pb:
-            pb.propagate_roi(r0, r0 + rows, U, stream=stream)
-            torch.cuda.synchronize(dev)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            pb.propagate_roi(r0, r0 + rows, U, stream=stream)
-            mb = pb.metrics(U, stream=stream)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            pms = e0.elapsed_time(e1)
-            if parity is not None:
-                pa, pb_ = parity["rows"]
-                parity["rel_l2_I_bluestein_fp32"] = _rel_l2(
-                    _rows_intensity(fzp, torch, pb, M, pa, pb_, stream, dev), Iref)
-        plain = {"form": "bluestein", "dtype": "f32", "value": rows * N / (pms / 1e3) / 1e9, "unit": UNIT,
-                 "ms_per_step": pms, "rows": rows}
         if rows == N:
-            plain.update(fwhm_x=mb["fwhm_x"], de_lobe=mb["de_lobe"])
+            ranges = [(0, N)]
+        else:
+            ns, h = 16, max(1, rows // 16)
+            ranges = [(max(0, int((k + 0.5) * N / ns) - h // 2), max(0, int((k + 0.5) * N / ns) - h // 2) + h)
+                      for k in range(ns)]
+            rows = ns * h
+        for conv, key in ((fzp.CONV_PARTITIONED, "partitioned"), (fzp.CONV_SINGLE, "single")):
+            with fzp.Plan(**dict(params, form=fzp.FORM_BLUESTEIN, precision=fzp.PREC_FP32, conv=conv)) as pb:
+                def run_rows():
+                    for k, (a, b) in enumerate(ranges):
+                        pb.propagate_roi(a, b, U, accumulate=k > 0, stream=stream)
+                run_rows()
+                torch.cuda.synchronize(dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                run_rows()
+                mb = pb.metrics(U, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                pms = e0.elapsed_time(e1)
+                if parity is not None:
+                    pa, pb_ = parity["rows"]
+                    parity[f"rel_l2_I_bluestein_fp32_{key}"] = _rel_l2(
+                        _rows_intensity(fzp, torch, pb, M, pa, pb_, stream, dev), Iref)
+            rec = {"form": "bluestein", "conv": key, "dtype": "f32", "value": rows * N / (pms / 1e3) / 1e9,
+                   "unit": UNIT, "ms_per_step": pms, "rows": rows,
+                   "row_sample": "whole aperture" if rows == N else f"16 stripes of {rows // 16} rows spread over N"}
+            if rows == N:
+                rec.update(fwhm_x=mb["fwhm_x"], de_lobe=mb["de_lobe"])
+            plain[key] = rec
 
     if rank != 0:
         if pg:
@@ -839,8 +886,10 @@ def main():
     if sharded:
         out["config"]["parallelism"] = f"rows split over {ws} ranks by open-sample count, one all_reduce per step"
     if plain:
-        out["plain_fp32"] = plain
-        out["speedup_vs_plain_fp32"] = value / plain["value"]
+        out["plain_fp32"] = plain["partitioned"]
+        out["speedup_vs_plain_fp32"] = value / plain["partitioned"]["value"]
+        out["plain_fp32_single"] = plain["single"]
+        out["speedup_vs_plain_fp32_single"] = value / plain["single"]["value"]
     if cb is not None:
         out["cpu_baseline"] = cb
         out["parity"] = parity

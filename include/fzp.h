@@ -153,7 +153,20 @@ typedef struct fzp_params {
                           (m lambda / 2)^2, the binary amplitude plate under
                           FZP_FORM_SACZT only (the paraxial forms' kernel would
                           aberrate it; FZP_E_UNSUPPORTED elsewhere)          */
-  int32_t reserved2;   /* must be 0                                            */
+  int32_t conv;        /* Bluestein row convolution (Sec. 2.6: the row CZT as a
+                          convolution with the chirp h_k = e^{i pi delta k^2}):
+                          0 -> partitioned with FP32, single with FP64;
+                          1 = single: one L-point FFT convolution per row
+                          (four-step FFTs through a global-memory workspace,
+                          the paper's structure);
+                          2 = partitioned: the row cut into blocks of S
+                          columns, S = 256 min(15, floor((4097 - M) / 256)),
+                          each block's 4096-point spectrum times the
+                          precomputed spectrum of its chirp piece, summed over
+                          the blocks that meet the row's disc chord, then one
+                          inverse 4096-point FFT per row, all on chip; FP32
+                          only (FZP_E_UNSUPPORTED with FP64).  Other values
+                          are invalid; the other forms ignore it            */
 } fzp_params;
 
 /* Opaque plan: geometry, zone-threshold table, chirp / kernel tables and the
@@ -189,7 +202,8 @@ typedef struct fzp_plan_info {
   int32_t passes;        /* dense form: signed-mask passes per row chunk (1, or L/2
                             for a phase plate with L >= 4)                         */
   int32_t centre_open;   /* 1: positive-centred binary plate (even zones open)     */
-  int32_t reserved;
+  int32_t conv;          /* Bluestein: 1 single L-point convolution per row, 2
+                            partitioned into 4096-point blocks; 0 other forms      */
   int64_t s_R;           /* largest squared distance from the axis, in samples, of a
                             sample inside the aperture disc (fl(s_R dx^2) <= fl(R^2)) */
 } fzp_plan_info;

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libfzp.so")
 FZP_OK, FZP_E_INVALID, FZP_E_OOM, FZP_E_CUDA, FZP_E_TIMEOUT, FZP_E_UNSUPPORTED = range(6)
 FORM_AUTO, FORM_BLUESTEIN, FORM_DENSE, FORM_SACZT = 0, 1, 2, 3
 PREC_FP64, PREC_FP32, PREC_SPLIT_BF16, PREC_BF16, PREC_AUTO_1E4 = 0, 1, 2, 3, 4
+CONV_AUTO, CONV_SINGLE, CONV_PARTITIONED = 0, 1, 2
 
 _STATUS = {0: "FZP_OK", 1: "FZP_E_INVALID", 2: "FZP_E_OOM", 3: "FZP_E_CUDA", 4: "FZP_E_TIMEOUT",
            5: "FZP_E_UNSUPPORTED"}
@@ -49,7 +50,7 @@ class Params(ctypes.Structure):
                 ("promote", ctypes.c_int32), ("row_batch", ctypes.c_int32), ("cluster", ctypes.c_int32),
                 ("levels", ctypes.c_int32), ("centre_open", ctypes.c_int32), ("roi_origin", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("x0", ctypes.c_double), ("y0", ctypes.c_double),
-                ("exact_radii", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("exact_radii", ctypes.c_int32), ("conv", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -61,7 +62,7 @@ class PlanInfo(ctypes.Structure):
                 ("promote", ctypes.c_int32), ("row_batch", ctypes.c_int32), ("chunk_rows", ctypes.c_int64),
                 ("cluster", ctypes.c_int32), ("fft_inner", ctypes.c_int32), ("ctas", ctypes.c_int32),
                 ("levels", ctypes.c_int32), ("passes", ctypes.c_int32), ("centre_open", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("s_R", ctypes.c_int64)]
+                ("conv", ctypes.c_int32), ("s_R", ctypes.c_int64)]
 
 
 class Metrics(ctypes.Structure):
@@ -180,15 +181,17 @@ class Plan:
     def __init__(self, D: float, f: float, lam: float, M: int, pitch: float, dx: float = 0.0, N: int = 0,
                  form: int = FORM_AUTO, precision: int = PREC_FP32, stripe_rows: int = 0,
                  deform: Optional[Deform] = None, promote: int = 0, row_batch: int = 0, cluster: int = 0,
-                 levels: int = 0, centre_open: int = 0, x0: Optional[float] = None, exact_radii: int = 0):
+                 levels: int = 0, centre_open: int = 0, x0: Optional[float] = None, exact_radii: int = 0,
+                 conv: int = CONV_AUTO):
         """x0: first ROI coordinate on both axes (None: the ROI centred on the focus);
-        exact_radii: the zone radii of Eq. 3 (FORM_SACZT only)."""
+        exact_radii: the zone radii of Eq. 3 (FORM_SACZT only); conv: the
+        Bluestein row convolution (CONV_SINGLE, CONV_PARTITIONED, CONV_AUTO)."""
         self._deform = deform
         org, ox, oy = _origin(x0)
         p = Params(D=D, f=f, lam=lam, dx=dx, N=N, M=M, form=form, pitch=pitch, precision=precision,
                    stripe_rows=stripe_rows, deform=ctypes.pointer(deform) if deform is not None else None,
                    promote=promote, row_batch=row_batch, cluster=cluster, levels=levels,
-                   centre_open=centre_open, roi_origin=org, x0=ox, y0=oy, exact_radii=exact_radii)
+                   centre_open=centre_open, roi_origin=org, x0=ox, y0=oy, exact_radii=exact_radii, conv=conv)
         h = ctypes.c_void_p()
         _check(lib().fzp_plan(ctypes.byref(p), ctypes.byref(h)))
         self._h = h
@@ -268,7 +271,7 @@ class Batch:
                             deform=ctypes.pointer(d) if d is not None else None, promote=pr.get("promote", 0),
                             row_batch=pr.get("row_batch", 0), cluster=pr.get("cluster", 0),
                             levels=pr.get("levels", 0), centre_open=pr.get("centre_open", 0),
-                            roi_origin=org, x0=ox, y0=oy)
+                            roi_origin=org, x0=ox, y0=oy, conv=pr.get("conv", CONV_AUTO))
         h = ctypes.c_void_p()
         _check(lib().fzp_batch_plan(arr, n, ctypes.byref(h)))
         self._h = h
@@ -362,11 +365,12 @@ class SurrogateNet:
 
 
 def _params(D, f, lam, M, pitch, dx=0.0, N=0, form=FORM_AUTO, precision=PREC_FP32, stripe_rows=0, promote=0,
-            row_batch=0, cluster=0, levels=0, centre_open=0, x0=None, exact_radii=0) -> Params:
+            row_batch=0, cluster=0, levels=0, centre_open=0, x0=None, exact_radii=0, conv=0) -> Params:
     org, ox, oy = _origin(x0)
     return Params(D=D, f=f, lam=lam, dx=dx, N=N, M=M, form=form, pitch=pitch, precision=precision,
                   stripe_rows=stripe_rows, deform=None, promote=promote, row_batch=row_batch, cluster=cluster,
-                  levels=levels, centre_open=centre_open, roi_origin=org, x0=ox, y0=oy, exact_radii=exact_radii)
+                  levels=levels, centre_open=centre_open, roi_origin=org, x0=ox, y0=oy, exact_radii=exact_radii,
+                  conv=conv)
 
 
 def plan_query(**kw) -> dict:

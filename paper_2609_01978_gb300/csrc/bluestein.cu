@@ -153,6 +153,8 @@ struct RowArgs {
   int64_t c1_stride; // row length of C1
   int64_t c1_j0;     // aperture row of C1 column 0
   const void* vin;   // input sequence for the table-building mode (length L)
+  int S;             // partitioned convolution: columns per block
+  int64_t nseg;      // partitioned convolution: blocks per row (spectra in H)
 };
 
 // Aperture transmission of sample (j, i): T e^{i phi}, optional deformation.
@@ -655,6 +657,243 @@ __global__ void __launch_bounds__(256) k_f3(RowArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Partitioned convolution (FP32).  The row's convolution (y * h)[m], m < M, is
+// a sum over blocks of S input columns, i in [i_s, i_s + S), i_s = s S.  With
+// P = 4096 >= S + M - 1 a block's share is one P-point circular convolution of
+// the zero-padded block with the chirp piece
+//   g_s[q] = h_{q - i_s} (q < M),  g_s[q] = h_{q - P - i_s} (P - S < q < P),
+// read at q = m < M: the two ranges hold every lag m - i the block needs and
+// do not overlap.  The transform is linear, so a row needs one inverse
+// transform of sum_s FFT_P(y_s) .* G_s, G_s = FFT_P(g_s) precomputed per block
+// (the same for every row); blocks that miss the row's disc chord are skipped.
+// A row's working set (the block, the spectrum sum, the transposes) stays in
+// registers and shared memory.
+//
+// The P-point FFT: 256 threads, thread t holding elements t + 256 r, r < 16;
+// P = 16 * 16 * 16 as three in-register 16-point DFTs with two shared-memory
+// transposes (index t = a + 16 b + 256 r, frequency k = k0 + 16 c + 256 d):
+//   pass A: over r -> k0, times e^{-2 pi i t k0 / P}
+//   pass B: thread (a, k0) over b -> c, times e^{-2 pi i a c / 256}
+//   pass C: thread (k0, c) over a -> d; thread t = k0 + 16 c then holds
+//           X[t + 256 d], the same distribution as its input.
+// ---------------------------------------------------------------------------
+constexpr int SP = 4096;          // partition transform length
+constexpr int STH = 256;          // threads per block
+constexpr int SB0 = 256 * 17;     // transpose buffer A->B: [t][k0], row pitch 17
+constexpr int SB1 = 16 * 273;     // transpose buffer B->C: [k0][c][a], pitches 273 and 17
+constexpr int SBUF = SB1 > SB0 ? SB1 : SB0;
+constexpr size_t SEG_SMEM = sizeof(float2) * (2 * SBUF + 15 * 256 + 256);
+
+// v e^{-2 pi i K / 16}
+template <int K>
+__device__ __forceinline__ float2 w16mul(float2 v) {
+  constexpr float C1 = 0.923879532511286756f, S1 = 0.382683432365089772f, R2 = 0.707106781186547524f;
+  if constexpr (K == 0) {
+    return v;
+  } else if constexpr (K == 4) {
+    return make_float2(v.y, -v.x);
+  } else if constexpr (K == 2) {
+    return make_float2(R2 * (v.x + v.y), R2 * (v.y - v.x));
+  } else if constexpr (K == 6) {
+    return make_float2(R2 * (v.y - v.x), -R2 * (v.x + v.y));
+  } else {
+    constexpr float wr = K == 1 ? C1 : (K == 3 ? S1 : -C1);  // K = 1, 3, 9
+    constexpr float wi = K == 1 ? -S1 : (K == 3 ? -C1 : S1);
+    return make_float2(v.x * wr - v.y * wi, v.x * wi + v.y * wr);
+  }
+}
+
+// Forward 4-point DFT in place.
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = csub(a1, a3);
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = make_float2(t1.x + t3.y, t1.y - t3.x);
+  a3 = make_float2(t1.x - t3.y, t1.y + t3.x);
+}
+
+// x[k] <- sum_n x[n] e^{-2 pi i n k / 16}: n = q + 4 n1, k = p + 4 k1; 4-point
+// DFTs over n1, twiddles e^{-2 pi i q p / 16}, 4-point DFTs over q.
+__device__ __forceinline__ void dft16(float2 (&x)[16]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dft4(x[q], x[q + 4], x[q + 8], x[q + 12]);  // (q, p) at q + 4 p
+  x[5] = w16mul<1>(x[5]);
+  x[9] = w16mul<2>(x[9]);
+  x[13] = w16mul<3>(x[13]);
+  x[6] = w16mul<2>(x[6]);
+  x[10] = w16mul<4>(x[10]);
+  x[14] = w16mul<6>(x[14]);
+  x[7] = w16mul<3>(x[7]);
+  x[11] = w16mul<6>(x[11]);
+  x[15] = w16mul<9>(x[15]);
+#pragma unroll
+  for (int p = 0; p < 4; ++p) dft4(x[4 * p], x[4 * p + 1], x[4 * p + 2], x[4 * p + 3]);  // (p, k1) at 4 p + k1
+  float2 y[16];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) y[p + 4 * k1] = x[4 * p + k1];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[k] = y[k];
+}
+
+// Forward P-point DFT of the block distributed as v[r] = x[t + 256 r];
+// on return v[d] = X[t + 256 d].  Two barriers; b0 and b1 alternate, so
+// back-to-back calls need no further barrier.  twA[(k0 - 1) 256 + t] =
+// e^{-2 pi i t k0 / P}, twB[c 16 + a] = e^{-2 pi i a c / 256}.
+__device__ __forceinline__ void fft_p(float2 (&v)[16], float2* b0, float2* b1, const float2* twA,
+                                      const float2* twB) {
+  const int t = threadIdx.x;
+  dft16(v);
+#pragma unroll
+  for (int k0 = 1; k0 < 16; ++k0) v[k0] = cmul(v[k0], twA[(k0 - 1) * 256 + t]);
+#pragma unroll
+  for (int k0 = 0; k0 < 16; ++k0) b0[t * 17 + k0] = v[k0];
+  __syncthreads();
+  {
+    const int a = t & 15, k0 = t >> 4;
+#pragma unroll
+    for (int b = 0; b < 16; ++b) v[b] = b0[(a + 16 * b) * 17 + k0];
+    dft16(v);
+#pragma unroll
+    for (int c = 1; c < 16; ++c) v[c] = cmul(v[c], twB[c * 16 + a]);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) b1[k0 * 273 + c * 17 + a] = v[c];
+  }
+  __syncthreads();
+  {
+    const int k0 = t & 15, c = t >> 4;
+#pragma unroll
+    for (int a = 0; a < 16; ++a) v[a] = b1[k0 * 273 + c * 17 + a];
+    dft16(v);
+  }
+}
+
+__device__ __forceinline__ void seg_twiddles(float2* twA, float2* twB) {
+  for (int e = threadIdx.x; e < 15 * 256; e += blockDim.x) {
+    const int k0 = e / 256 + 1, th = e % 256;
+    float sn, cs;
+    sincospif(-(float)(th * k0) / 2048.0f, &sn, &cs);  // exact argument: th k0 < 2^12
+    twA[e] = make_float2(cs, sn);
+  }
+  {
+    const int c = threadIdx.x >> 4, a = threadIdx.x & 15;
+    float sn, cs;
+    sincospif(-(float)(a * c) / 128.0f, &sn, &cs);
+    twB[threadIdx.x] = make_float2(cs, sn);
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ int64_t isqrt_row(int64_t t) {
+  int64_t b = (int64_t)sqrt((double)t);
+  while (b > 0 && b * b > t) --b;
+  while ((b + 1) * (b + 1) <= t) ++b;
+  return b;
+}
+
+// G_s = FFT_P(g_s) for every block s (one CTA per block, grid-strided).
+__global__ void __launch_bounds__(STH) k_seg_tables(int64_t nseg, int S, int M, double delta, float2* G) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* b0 = reinterpret_cast<float2*>(smem_raw);
+  float2* b1 = b0 + SBUF;
+  float2* twA = b1 + SBUF;
+  float2* twB = twA + 15 * 256;
+  seg_twiddles(twA, twB);
+  const int t = threadIdx.x;
+  for (int64_t s = blockIdx.x; s < nseg; s += gridDim.x) {
+    const int64_t is = s * (int64_t)S;
+    float2 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int q = t + 256 * r;
+      v[r] = make_float2(0.0f, 0.0f);
+      int64_t k = 0;
+      bool have = false;
+      if (q < M) { k = q - is; have = true; }
+      else if (q > SP - S) { k = (int64_t)q - SP - is; have = true; }
+      if (have) {
+        const double kk = (double)k;  // |k| < 2^24: k^2 exact in FP64
+        v[r] = cis_turns<float>(0.5 * delta * kk * kk);
+      }
+    }
+    fft_p(v, b0, b1, twA, twB);
+    float2* out = G + s * SP + t;
+#pragma unroll
+    for (int d = 0; d < 16; ++d) out[256 * d] = v[d];
+  }
+}
+
+// Row pass of the partitioned convolution: rows j0 + r, r = blockIdx.x,
+// blockIdx.x + gridDim.x, ... (interleaved, so every CTA gets rows from the
+// whole range of chord lengths); writes C1 like k_f3.
+__global__ void __launch_bounds__(STH, 2) k_seg(RowArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* b0 = reinterpret_cast<float2*>(smem_raw);
+  float2* b1 = b0 + SBUF;
+  float2* twA = b1 + SBUF;
+  float2* twB = twA + 15 * 256;
+  seg_twiddles(twA, twB);
+  const int t = threadIdx.x;
+  const float2* pre = reinterpret_cast<const float2*>(a.pre);
+  const float2* Gs = reinterpret_cast<const float2*>(a.H);
+  const float2* post = reinterpret_cast<const float2*>(a.post);
+  float* C1 = reinterpret_cast<float*>(a.C1);
+  const int S = a.S, RS = a.S / 256;
+  const float scale = (float)a.L / (float)SP;  // post carries 1/L; the inverse below is unnormalised
+  for (int64_t r = blockIdx.x; r < a.rows; r += gridDim.x) {
+    const int64_t j = a.j0 + r;
+    const int64_t dj = j - a.mg.c;
+    const int64_t rem = a.mg.sR - dj * dj;
+    float2 acc[16];
+#pragma unroll
+    for (int d = 0; d < 16; ++d) acc[d] = make_float2(0.0f, 0.0f);
+    if (rem >= 0) {
+      const int64_t bmax = isqrt_row(rem);
+      // the row's disc chord, within the grid (a given N may cut the disc)
+      const int64_t lo = max(a.mg.c - bmax, (int64_t)0), hi = min(a.mg.c + bmax, a.N - 1);
+      const int64_t s1 = hi / S;
+      for (int64_t s = lo / S; s <= s1; ++s) {
+        const int64_t is = s * (int64_t)S;
+        float2 v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int64_t i = is + t + 256 * q;
+          float2 x = make_float2(0.0f, 0.0f);
+          if (q < RS && i >= lo && i <= hi) {
+            x = aperture<float>(a, j, i);
+            if (x.x != 0.0f || x.y != 0.0f) x = cmul(x, __ldg(pre + i));
+          }
+          v[q] = x;
+        }
+        fft_p(v, b0, b1, twA, twB);
+        const float2* G = Gs + s * SP + t;
+#pragma unroll
+        for (int d = 0; d < 16; ++d) {
+          const float2 g = __ldg(G + 256 * d);
+          acc[d].x = fmaf(v[d].x, g.x, fmaf(-v[d].y, g.y, acc[d].x));
+          acc[d].y = fmaf(v[d].x, g.y, fmaf(v[d].y, g.x, acc[d].y));
+        }
+      }
+    }
+    // inverse transform as conj(FFT(conj(.))), outputs m = t + 256 d < M
+#pragma unroll
+    for (int d = 0; d < 16; ++d) acc[d].y = -acc[d].y;
+    fft_p(acc, b0, b1, twA, twB);
+    const int64_t jl = j - a.c1_j0;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const int m = t + 256 * d;
+      if (m < a.M) {
+        const float2 y = cmul(make_float2(acc[d].x * scale, -acc[d].y * scale), post[m]);
+        C1[(int64_t)c1_row_re(m) * a.c1_stride + jl] = y.x;
+        C1[(int64_t)c1_row_im(m) * a.c1_stride + jl] = y.y;
+      }
+    }
+  }
+}
+
 // Tables: pre(i), post(m)/L, convolution chirp v (length L), twiddles.
 template <typename R>
 __global__ void k_tables(int64_t N, int M, double msh, int64_t L, int64_t c, double kappa, double delta, void* pre,
@@ -751,6 +990,8 @@ static RowArgs make_args(const Plan& P) {
   a.c1_stride = P.chunk_rows;
   a.C1 = P.precision == FZP_PREC_FP64 ? (void*)P.d_C1d : (void*)P.d_C1;
   a.vin = b.d_tab;
+  a.S = b.S;
+  a.nseg = b.nseg;
   return a;
 }
 
@@ -766,6 +1007,22 @@ fzp_status layout_t(Plan& P, FormSizes* out) {
   // the F1 twiddles are read from the L2-entry table with stride L2 / L1
   if (b.L1 > b.L2) return set_error(FZP_E_UNSUPPORTED, "FFT length %lld above %lld", (long long)b.L,
                                     (long long)b.L2 * b.L2);
+  b.seg = (sizeof(R) == 4 && P.conv_req != 1) ? 1 : 0;
+  if (b.seg) {
+    // partitioned convolution: S + M - 1 <= 4096, S a multiple of 256 (at most 15 x 256)
+    b.S = 256 * std::min(15, (4097 - P.M) / 256);
+    b.nseg = (P.N + b.S - 1) / b.S;
+    b.rows = P.chunk_rows;
+    out->pre = sizeof(C) * P.N;
+    out->H = sizeof(C) * (size_t)SP * (size_t)b.nseg;
+    out->tab = sizeof(C) * (b.L + (int)b.L2 + P.M + 4096);
+    out->Z = 0;
+    out->G = 0;
+    static std::atomic<uint64_t> attr_seg{0}, attr_segt{0};
+    FZP_CUDA_TRY(smem_attr_once((const void*)k_seg, (int)SEG_SMEM, attr_seg));
+    FZP_CUDA_TRY(smem_attr_once((const void*)k_seg_tables, (int)SEG_SMEM, attr_segt));
+    return FZP_OK;
+  }
   // rows per pass: requested, else a transform workspace of about 1 GiB
   const int64_t zbytes = (int64_t)sizeof(C) * b.L;
   int64_t rows = P.row_batch_req > 0 ? P.row_batch_req : (1ll << 30) / zbytes;
@@ -795,6 +1052,13 @@ fzp_status fill_tables_t(Plan& P, cudaStream_t s) {
   k_tables<R><<<1024, 256, 0, s>>>(P.N, P.M, P.msh, b.L, P.c, P.kappa, P.delta, b.d_pre, b.d_post, b.d_tab, b.d_tw, twN,
                                    b.d_twL);
   FZP_CUDA_TRY(cudaGetLastError());
+  if (b.seg) {
+    const unsigned g = (unsigned)std::min<int64_t>(b.nseg, 1024);
+    k_seg_tables<<<g, STH, SEG_SMEM, s>>>(b.nseg, b.S, P.M, P.delta, reinterpret_cast<float2*>(b.d_H));
+    FZP_CUDA_TRY(cudaGetLastError());
+    P.launches += 2;
+    return FZP_OK;
+  }
   // H = FFT_L(v) in the [k1][k2] order: F1 (table mode) + F2 (forward only) into Z row 0, then copy.
   RowArgs a = make_args(P);
   a.j0 = 0;
@@ -817,7 +1081,7 @@ fzp_status build_tables_t(Plan& P) {
   FZP_CUDA_TRY(cudaMalloc(&b.d_pre, z.pre));
   FZP_CUDA_TRY(cudaMalloc(&b.d_H, z.H));
   FZP_CUDA_TRY(cudaMalloc(&b.d_tab, z.tab));
-  FZP_CUDA_TRY(cudaMalloc(&b.d_Z, z.Z));
+  if (z.Z) FZP_CUDA_TRY(cudaMalloc(&b.d_Z, z.Z));
   if (z.G) FZP_CUDA_TRY(cudaMalloc(&b.d_G, z.G));
   P.device_bytes += z.pre + z.H + z.tab + z.Z + z.G;
   return fill_tables_t<R>(P, 0);
@@ -829,6 +1093,23 @@ fzp_status rows_t(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
   const Bluestein& b = P.bs;
   RowArgs a = make_args(P);
   a.c1_j0 = j0;
+  if (b.seg) {
+    // resident CTAs only: each takes every gridDim.x-th row of the range
+    int ctas_per_sm = 0, sms = 0, dev = 0;
+    FZP_CUDA_TRY(cudaGetDevice(&dev));
+    FZP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    FZP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, k_seg, STH, SEG_SMEM));
+    if (ctas_per_sm < 1) ctas_per_sm = 1;
+    a.j0 = j0;
+    a.rows = rows;
+    const int64_t grid = std::min<int64_t>(rows, (int64_t)ctas_per_sm * sms);
+    prof_begin(P, s);
+    k_seg<<<(unsigned)grid, STH, SEG_SMEM, s>>>(a);
+    prof_end(P, s);
+    P.launches += 1;
+    FZP_CUDA_TRY(cudaGetLastError());
+    return FZP_OK;
+  }
   for (int64_t r0 = 0; r0 < rows; r0 += b.rows) {
     const int64_t rb = std::min<int64_t>(b.rows, rows - r0);
     a.j0 = j0 + r0;
@@ -885,7 +1166,8 @@ fzp_status bluestein_fill_tables(Plan& P, cudaStream_t s) {
 }
 
 fzp_status bluestein_rows(Plan& P, int64_t j0, int64_t rows, cudaStream_t stream) {
-  P.dominant = P.precision == FZP_PREC_FP64 ? "bluestein_f2<double>" : "bluestein_f2<float>";
+  P.dominant = P.precision == FZP_PREC_FP64 ? "bluestein_f2<double>"
+                                             : (P.bs.seg ? "k_seg (partitioned convolution)" : "bluestein_f2<float>");
   return P.precision == FZP_PREC_FP64 ? rows_t<double>(P, j0, rows, stream) : rows_t<float>(P, j0, rows, stream);
 }
 

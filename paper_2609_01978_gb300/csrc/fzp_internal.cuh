@@ -172,6 +172,11 @@ struct Bluestein {
   void* d_post = nullptr; // into d_tab
   void* d_twL = nullptr;  // into d_tab: e^{-2 pi i t / L}, t < 4096
   int64_t rows = 0;       // rows per batch of the workspace
+  // partitioned convolution (FP32): blocks of S columns, 4096-point spectra of
+  // the chirp pieces in d_H as [nseg][4096]; d_Z, d_G unused
+  int seg = 0;
+  int S = 0;
+  int64_t nseg = 0;
 };
 
 // One signed-mask pass of a phase plate in the dense form: the mask is +1 on
@@ -226,6 +231,7 @@ struct Plan {
   int M;
   int form, precision, stripe_rows;
   int promote_req = 0, row_batch_req = 0, cluster_req = 0;  // tuning knobs as requested (0: default)
+  int conv_req = 0;  // Bluestein row convolution as requested (fzp_params.conv)
   bool owns_buffers = true;  // false: tables and workspace belong to a batch
   // derived
   double kappa, delta, dx2, R2;

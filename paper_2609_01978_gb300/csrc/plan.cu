@@ -114,7 +114,9 @@ fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
   if (in->promote < 0 || in->row_batch < 0) return set_error(FZP_E_INVALID, "promote and row_batch must be >= 0");
   if (in->form < FZP_FORM_AUTO || in->form > FZP_FORM_SACZT) return set_error(FZP_E_INVALID, "unknown form");
   if (in->exact_radii != 0 && in->exact_radii != 1) return set_error(FZP_E_INVALID, "exact_radii must be 0 or 1");
-  if (in->reserved2 != 0) return set_error(FZP_E_INVALID, "reserved2 must be 0");
+  if (in->conv < 0 || in->conv > 2) return set_error(FZP_E_INVALID, "conv must be 0, 1 or 2");
+  if (in->conv == 2 && in->precision == FZP_PREC_FP64)
+    return set_error(FZP_E_UNSUPPORTED, "the partitioned Bluestein convolution runs in FP32 only");
   if (in->precision < FZP_PREC_FP64 || in->precision > FZP_PREC_AUTO_1E4)
     return set_error(FZP_E_INVALID, "unknown precision");
   if (in->deform && (in->deform->n_ridges < 0 || in->deform->n_ridges > 3))
@@ -249,6 +251,7 @@ fzp_status validate_and_derive(const fzp_params* in, Plan& P) {
   P.stripe_rows = in->stripe_rows;
   P.promote_req = in->promote;
   P.row_batch_req = in->row_batch;
+  P.conv_req = in->conv;
   if (in->cluster != 0 && in->cluster != 1 && in->cluster != 2 && in->cluster != 4)
     return set_error(FZP_E_INVALID, "cluster must be 0, 1, 2 or 4");
   P.cluster_req = in->cluster;
@@ -445,6 +448,8 @@ fzp_status fzp_plan_query(const fzp_params* params, fzp_plan_info* out) {
     // the four-step split L = L1 L2 with L1 <= L2 <= 4096 (bluestein.cu)
     if (L > (1ll << 24)) return set_error(FZP_E_UNSUPPORTED, "FFT length %lld above %lld", (long long)L, 1ll << 24);
     out->fft_length = L;
+    out->conv = (P.precision == FZP_PREC_FP32 && P.conv_req != 1) ? 2 : 1;
+    out->fft_inner = out->conv == 2 ? 4096 : (int32_t)std::min<int64_t>(L, 4096);
   }
   if (!tuned && P.form == FZP_FORM_SACZT) {
     const fzp_status sst = saczt_layout(P);  // host only
@@ -487,7 +492,8 @@ fzp_status fzp_plan_info_get(fzp_plan_t plan, fzp_plan_info* out) {
   out->row_batch = P.form == FZP_FORM_BLUESTEIN ? (int32_t)P.bs.rows : 0;
   out->chunk_rows = P.chunk_rows;
   out->cluster = P.form == FZP_FORM_DENSE ? P.dn.cluster : 0;
-  out->fft_inner = P.form == FZP_FORM_BLUESTEIN ? (int32_t)P.bs.L2 : 0;
+  out->fft_inner = P.form == FZP_FORM_BLUESTEIN ? (P.bs.seg ? 4096 : (int32_t)P.bs.L2) : 0;
+  out->conv = P.form == FZP_FORM_BLUESTEIN ? (P.bs.seg ? 2 : 1) : 0;
   out->ctas = P.form == FZP_FORM_DENSE ? P.dn.max_ctas : 0;
   out->levels = P.levels;
   out->passes = P.passes.empty() ? 1 : (int32_t)P.passes.size();

@@ -83,7 +83,10 @@ def test_roi_origin_validation(fzp):
     for kw, status in [(dict(roi_origin=1, x0=1e-6, y0=2e-6), fzp.FZP_E_UNSUPPORTED),
                        (dict(roi_origin=2), fzp.FZP_E_INVALID),
                        (dict(roi_origin=1, x0=float("inf"), y0=float("inf")), fzp.FZP_E_INVALID),
-                       (dict(reserved=1), fzp.FZP_E_INVALID)]:
+                       (dict(reserved=1), fzp.FZP_E_INVALID),
+                       (dict(conv=3), fzp.FZP_E_INVALID),
+                       (dict(conv=-1), fzp.FZP_E_INVALID),
+                       (dict(conv=2, precision=0), fzp.FZP_E_UNSUPPORTED)]:
         p = fzp._params(**base)
         for k, v in kw.items():
             setattr(p, k, v)

@@ -37,16 +37,18 @@ def config1(env):
     return g, U, O.metrics(g, U)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_config1_full_aperture(env, config1, precision):
+@pytest.mark.parametrize("precision,conv", [(0, 0), (1, 1), (1, 2)])
+def test_config1_full_aperture(env, config1, precision, conv):
     """Config 1: D = 4 mm, f/# = 5, 632.8 nm, N = 5057 (FP64 runs the four-step
-    split L = 2 x 4096, FP32 the single 8192-point pass), 256^2 ROI at 0.2 um."""
+    split L = 2 x 4096, FP32 the single 8192-point pass or two partitioned
+    blocks of 3840 columns), 256^2 ROI at 0.2 um."""
     fzp, torch, O = env
     g, Uref, mref = config1
-    with _plan(fzp, g, precision) as plan:
+    with _plan(fzp, g, precision, conv=conv) as plan:
         info = plan.info
         assert info["N"] == g.N == 5057 and info["total_zones"] == g.total_zones()
         assert info["fft_length"] == 8192
+        assert info["conv"] == (2 if conv == 2 else 1)
         U, I = run_plan(fzp, torch, plan, g.M, 0, g.N)
         Iref = np.abs(Uref) ** 2
         assert rel_l2(I, Iref) <= TOL[precision]
@@ -72,11 +74,13 @@ def test_metrics_extractor_on_oracle_field(env, config1):
     assert np.max(np.abs(np.array(m["mtf16"]) - mref["mtf16"])) < 1e-9
 
 
-def test_four_step_fp32_and_ragged_rows(env):
-    """FP32 with L = 16384 = 2 x 8192 (four-step path), odd row ranges, accumulation."""
+@pytest.mark.parametrize("conv", [1, 2])
+def test_four_step_fp32_and_ragged_rows(env, conv):
+    """FP32 with L = 16384 = 2 x 8192 (four-step path) or three partitioned
+    blocks, odd row ranges, a single row on the axis."""
     fzp, torch, O = env
     g = O.Geometry(D=4e-3 * 9001 / 5057, f=20e-3 * 9001 / 5057, lam=632.8e-9, M=128, p=0.3e-6, N=9001)
-    with _plan(fzp, g, 1) as plan:
+    with _plan(fzp, g, 1, conv=conv) as plan:
         assert plan.info["fft_length"] == 16384
         for (j0, j1) in [(0, g.N), (4321, 4321 + 777), (g.c, g.c + 1)]:
             _, I = run_plan(fzp, torch, plan, g.M, j0, j1)
@@ -103,8 +107,8 @@ def test_row_range_linearity_and_empty(env):
             plan.propagate_roi(5, 4, U)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_deformed_membrane(env, precision):
+@pytest.mark.parametrize("precision,conv", [(0, 0), (1, 1), (1, 2)])
+def test_deformed_membrane(env, precision, conv):
     """Membrane deformation phase (4 pi / lambda) w with a sine wrinkle, taper
     and two crease ridges (config 4's model) against the oracle."""
     fzp, torch, O = env
@@ -113,22 +117,24 @@ def test_deformed_membrane(env, precision):
              ridges=[(5e-5, -1e-4, 0.4, lam / 8, 8e-5), (-2e-4, 3e-5, 2.2, lam / 10, 1.2e-4)])
     g = O.Geometry(D=2e-3, f=1e-2, lam=lam, M=128, p=lam * 5 / 8, deform=O.Deform(**d))
     with fzp.Plan(D=g.D, f=g.f, lam=g.lam, M=g.M, pitch=g.p, dx=g.dx, N=g.N, form=fzp.FORM_BLUESTEIN,
-                  precision=precision, deform=fzp.make_deform(**d)) as plan:
+                  precision=precision, deform=fzp.make_deform(**d), conv=conv) as plan:
         _, I = run_plan(fzp, torch, plan, g.M, 0, g.N)
     Iref = np.abs(O.field_czt(g)) ** 2
     assert rel_l2(I, Iref) <= TOL[precision]
 
 
-def test_config2_sampled_stripes(env):
+@pytest.mark.parametrize("conv", [1, 2])
+def test_config2_sampled_stripes(env, conv):
     """Config 2 (D = 0.25 m, N = 316,057, L = 2^19, 512^2 ROI at lambda f/#/8):
     the field is linear in rows, so 1024-row stripes at random offsets are
-    compared with the oracle on the same rows."""
+    compared with the oracle on the same rows (single convolution, or 89
+    partitioned blocks of 3584 columns)."""
     fzp, torch, O = env
     lam, F = 632.8e-9, 5.0
     g = O.Geometry(D=0.25, f=1.25, lam=lam, M=512, p=lam * F / 8)
     assert g.N == 316057
     rng = np.random.default_rng(1)
-    with _plan(fzp, g, 1) as plan:
+    with _plan(fzp, g, 1, conv=conv) as plan:
         assert plan.info["fft_length"] == 1 << 19
         for j0 in [g.c - 512, int(rng.integers(0, g.N - 1024))]:
             _, I = run_plan(fzp, torch, plan, g.M, j0, j0 + 1024)

@@ -67,7 +67,7 @@ def test_dense_config2_sampled_stripes(env):
 
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-FORMS2 = [("dense", 2, 2), ("bluestein_fp32", 1, 1)]
+FORMS2 = [("dense", 2, 2, 0), ("bluestein_fp32", 1, 1, 2), ("bluestein_fp32_single", 1, 1, 1)]
 
 
 @pytest.mark.parametrize("form", FORMS2, ids=[f[0] for f in FORMS2])
@@ -83,9 +83,10 @@ def test_full_aperture_config2_vs_oracle(env, form):
     meta = json.load(open(os.path.join(GOLDEN, "config2_d0.25m.json")))
     Uref = np.load(os.path.join(GOLDEN, meta["field_file"])).astype(np.complex128)
     mref = meta["metrics_fp64"]
-    name, form_id, prec = form
+    name, form_id, prec, conv = form
     lam = 632.8e-9
-    with fzp.Plan(D=0.25, f=1.25, lam=lam, M=512, pitch=lam * 5 / 8, form=form_id, precision=prec) as plan:
+    with fzp.Plan(D=0.25, f=1.25, lam=lam, M=512, pitch=lam * 5 / 8, form=form_id, precision=prec,
+                  conv=conv) as plan:
         N = plan.info["N"]
         assert N == meta["geometry"]["N"]
         U, I = run_plan(fzp, torch, plan, 512, 0, N)
@@ -162,9 +163,10 @@ def test_d_sweep_stripes_vs_oracle(env, D, form):
     meta = json.load(open(os.path.join(GOLDEN, "dsweep_stripes.json")))
     rec = meta["plates"][f"{D:g}"]
     Iref = np.load(os.path.join(GOLDEN, rec["file"])).astype(np.float64)
-    name, form_id, prec = form
+    name, form_id, prec, conv = form
     lam = 632.8e-9
-    with fzp.Plan(D=D, f=5 * D, lam=lam, M=512, pitch=lam * 5 / 8, form=form_id, precision=prec) as plan:
+    with fzp.Plan(D=D, f=5 * D, lam=lam, M=512, pitch=lam * 5 / 8, form=form_id, precision=prec,
+                  conv=conv) as plan:
         assert plan.info["N"] == rec["N"]
         dev = torch.device("cuda:0")
         U = torch.zeros((512, 512), dtype=torch.complex128, device=dev)
