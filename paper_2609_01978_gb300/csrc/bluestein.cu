@@ -827,7 +827,13 @@ __global__ void __launch_bounds__(STH) k_seg_tables(int64_t nseg, int S, int M, 
 
 // Row pass of the partitioned convolution: rows j0 + r, r = blockIdx.x,
 // blockIdx.x + gridDim.x, ... (interleaved, so every CTA gets rows from the
-// whole range of chord lengths); writes C1 like k_f3.
+// whole range of chord lengths); writes C1 like k_f3.  FLAT: binary amplitude
+// plate without deformation, the zone rule evaluated on the squared radius
+// stepped from column to column of the thread (s += 512 di + 256^2); otherwise
+// the general transmission (phase levels, membrane phase).  A block's input
+// chirp loads are issued together before the mask is evaluated, and the
+// spectra G_s before the last FFT pass, so each waits one memory latency.
+template <bool FLAT>
 __global__ void __launch_bounds__(STH, 2) k_seg(RowArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* b0 = reinterpret_cast<float2*>(smem_raw);
@@ -860,20 +866,59 @@ __global__ void __launch_bounds__(STH, 2) k_seg(RowArgs a) {
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           const int64_t i = is + t + 256 * q;
-          float2 x = make_float2(0.0f, 0.0f);
-          if (q < RS && i >= lo && i <= hi) {
-            x = aperture<float>(a, j, i);
-            if (x.x != 0.0f || x.y != 0.0f) x = cmul(x, __ldg(pre + i));
-          }
-          v[q] = x;
+          v[q] = (q < RS && i >= lo && i <= hi) ? __ldg(pre + i) : make_float2(0.0f, 0.0f);
         }
-        fft_p(v, b0, b1, twA, twB);
+        if (FLAT) {
+          // inside [lo, hi] every column is inside the disc; elsewhere v is
+          // already 0 and the clamp keeps the zone rule inside its table
+          int64_t di = is + t - a.mg.c;
+          int64_t sq = dj * dj + di * di;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int64_t z = zone_of(min(sq, a.mg.sR), a.mg);
+            if (((z ^ a.mg.centre_open) & 1) == 0) v[q] = make_float2(0.0f, 0.0f);
+            sq += 512 * di + 65536;
+            di += 256;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int64_t i = is + t + 256 * q;
+            if (q < RS && i >= lo && i <= hi) v[q] = cmul(aperture<float>(a, j, i), v[q]);
+          }
+        }
+        // forward FFT (passes A and B), spectrum loads, pass C, product-sum
+        dft16(v);
+#pragma unroll
+        for (int k0 = 1; k0 < 16; ++k0) v[k0] = cmul(v[k0], twA[(k0 - 1) * 256 + t]);
+#pragma unroll
+        for (int k0 = 0; k0 < 16; ++k0) b0[t * 17 + k0] = v[k0];
+        __syncthreads();
+        {
+          const int aa = t & 15, k0 = t >> 4;
+#pragma unroll
+          for (int b = 0; b < 16; ++b) v[b] = b0[(aa + 16 * b) * 17 + k0];
+          dft16(v);
+#pragma unroll
+          for (int c = 1; c < 16; ++c) v[c] = cmul(v[c], twB[c * 16 + aa]);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) b1[k0 * 273 + c * 17 + aa] = v[c];
+        }
+        __syncthreads();
+        float2 g[16];
         const float2* G = Gs + s * SP + t;
 #pragma unroll
+        for (int d = 0; d < 16; ++d) g[d] = __ldg(G + 256 * d);
+        {
+          const int k0 = t & 15, c = t >> 4;
+#pragma unroll
+          for (int aa = 0; aa < 16; ++aa) v[aa] = b1[k0 * 273 + c * 17 + aa];
+          dft16(v);
+        }
+#pragma unroll
         for (int d = 0; d < 16; ++d) {
-          const float2 g = __ldg(G + 256 * d);
-          acc[d].x = fmaf(v[d].x, g.x, fmaf(-v[d].y, g.y, acc[d].x));
-          acc[d].y = fmaf(v[d].x, g.y, fmaf(v[d].y, g.x, acc[d].y));
+          acc[d].x = fmaf(v[d].x, g[d].x, fmaf(-v[d].y, g[d].y, acc[d].x));
+          acc[d].y = fmaf(v[d].x, g[d].y, fmaf(v[d].y, g[d].x, acc[d].y));
         }
       }
     }
@@ -1019,7 +1064,9 @@ fzp_status layout_t(Plan& P, FormSizes* out) {
     out->Z = 0;
     out->G = 0;
     static std::atomic<uint64_t> attr_seg{0}, attr_segt{0};
-    FZP_CUDA_TRY(smem_attr_once((const void*)k_seg, (int)SEG_SMEM, attr_seg));
+    static std::atomic<uint64_t> attr_segg{0};
+    FZP_CUDA_TRY(smem_attr_once((const void*)k_seg<true>, (int)SEG_SMEM, attr_seg));
+    FZP_CUDA_TRY(smem_attr_once((const void*)k_seg<false>, (int)SEG_SMEM, attr_segg));
     FZP_CUDA_TRY(smem_attr_once((const void*)k_seg_tables, (int)SEG_SMEM, attr_segt));
     return FZP_OK;
   }
@@ -1098,13 +1145,17 @@ fzp_status rows_t(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
     int ctas_per_sm = 0, sms = 0, dev = 0;
     FZP_CUDA_TRY(cudaGetDevice(&dev));
     FZP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    FZP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, k_seg, STH, SEG_SMEM));
+    const bool flat = P.levels < 2 && !P.has_deform;
+    FZP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, flat ? (const void*)k_seg<true>
+                                                                                 : (const void*)k_seg<false>,
+                                                               STH, SEG_SMEM));
     if (ctas_per_sm < 1) ctas_per_sm = 1;
     a.j0 = j0;
     a.rows = rows;
     const int64_t grid = std::min<int64_t>(rows, (int64_t)ctas_per_sm * sms);
     prof_begin(P, s);
-    k_seg<<<(unsigned)grid, STH, SEG_SMEM, s>>>(a);
+    if (flat) k_seg<true><<<(unsigned)grid, STH, SEG_SMEM, s>>>(a);
+    else k_seg<false><<<(unsigned)grid, STH, SEG_SMEM, s>>>(a);
     prof_end(P, s);
     P.launches += 1;
     FZP_CUDA_TRY(cudaGetLastError());
