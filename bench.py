@@ -15,6 +15,7 @@ samples per outermost zone width (dx = 0.791 um, N = 1,264,223 per side,
 focus.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--form dense|bluestein]
+                  [--conv partitioned|single]
                   [--impl ours|reference] [--workload NAME] [--rows R]
                   [--plain-rows R] [--e2e-steps E] [--no-plain] [--no-cpu-baseline]
                   [--ref-rows R] [--instances I] [--seed S] [--replicas]
@@ -28,13 +29,19 @@ surrogate (training-set generation and the trained network's held-out
 error), saczt-d8mm (the SA-CZT form on an exact-radii plate; its roofline is
 the zoom product's, and its oracle sample a 2 mm plate of the same method).
 --rows R times R central aperture rows per step (a sample, named in the
-config); --plain-rows R does the same for the plain FP32 form (its cost per
-row does not depend on the row; default: all rows up to D = 0.25 m, 16,384
-central rows above); --e2e-steps 0 leaves out the end-to-end leg; --ref-rows
-sets the oracle's rows per step in the reference arm.
+config); --form bluestein times the plain FP32 form itself, with --conv its
+row convolution (partitioned into 4096-point blocks, the default, or the
+paper's single L-point convolution).  Beside the dense form the line carries
+the plain FP32 form with both convolutions ("plain_fp32": partitioned,
+"plain_fp32_single"), each timed on the whole aperture up to D = 0.25 m and
+on 16 stripes spread evenly over the aperture above (--plain-rows R rows in
+all; the partitioned convolution's cost per row follows the row's disc
+chord, so a central sample would understate it); --e2e-steps 0 leaves out
+the end-to-end leg; --ref-rows sets the oracle's rows per step in the
+reference arm.
 
 The cpu_baseline leg also checks parity: the oracle's FP64 field of its timed
-row sample against both GPU forms' fields of the same rows (relative L2 of I,
+row sample against the GPU forms' fields of the same rows (relative L2 of I,
 tolerance 1e-4), outside the timed region.
 
 Under torchrun (N > 1) the aperture is split into contiguous row ranges of

@@ -683,7 +683,7 @@ constexpr int STH = 256;          // threads per block
 constexpr int SB0 = 256 * 17;     // transpose buffer A->B: [t][k0], row pitch 17
 constexpr int SB1 = 16 * 273;     // transpose buffer B->C: [k0][c][a], pitches 273 and 17
 constexpr int SBUF = SB1 > SB0 ? SB1 : SB0;
-constexpr size_t SEG_SMEM = sizeof(float2) * (2 * SBUF + 15 * 256 + 256);
+constexpr size_t SEG_SMEM = sizeof(float2) * (2 * SBUF + 15 * 256 + 256) + sizeof(uint32_t) * 256;
 
 // v e^{-2 pi i K / 16}
 template <int K>
@@ -793,6 +793,47 @@ __device__ __forceinline__ int64_t isqrt_row(int64_t t) {
   return b;
 }
 
+// Open bits of the 16 columns [x, x + 16) of a row (bit p: column x + p) of
+// the binary plate, dj2 = dj^2.  Between the chunk's two ends the zone index
+// steps through the boundaries m in (zn, zf] (zn, zf: the zones at the ends
+// nearer to and farther from the axis, squared radius clamped into the
+// disc); boundary m sits at distance a_m = ceil(sqrt(S_m - dj^2)) from the
+// axis: at column c + a_m right of the axis (the zone reaches m there), at
+// c - a_m + 1 left of it (the zone drops below m there).  With the chunk at
+// distance d >= 128 from the axis, a_m = d + k, k in [1, 15] the smallest k
+// with k (k + 2d) >= S_m - dj^2 - d^2 (below 30 d + 225: 32-bit); the
+// estimate (S_m - dj^2 - d^2) / (2d) exceeds k by k^2 / (2d) < 1, and with
+// FP32 rounding it lies within [k - 1, k + 2]: one step up and two down make
+// k exact.  Chunks nearer the axis take the zone rule column by column.
+// Columns outside the disc chord come out arbitrary (their input is zero).
+__device__ __forceinline__ uint32_t chunk_bits(int64_t x, int64_t dj2, const MaskGeom& g) {
+  const int64_t dr = x - g.c, dl = g.c - (x + 15);
+  if (dr < 128 && dl < 128) {
+    uint32_t bits = 0;
+    for (int p = 0; p < 16; ++p) {
+      const int64_t di = x + p - g.c, sq = dj2 + di * di;
+      if (sq <= g.sR && ((zone_of(sq, g) ^ g.centre_open) & 1) != 0) bits |= 1u << p;
+    }
+    return bits;
+  }
+  const bool right = dr >= 128;
+  const int64_t d = right ? dr : dl;
+  const int64_t sn = dj2 + d * d, sf = dj2 + (d + 15) * (d + 15);
+  const int64_t zn = zone_of(min(sn, g.sR), g), zf = zone_of(min(sf, g.sR), g);
+  uint32_t bits = ((((right ? zn : zf) ^ g.centre_open) & 1) != 0) ? 0xFFFFu : 0u;  // parity at p = 0
+  const float inv2d = 0.5f / (float)d;
+  const int32_t td = (int32_t)(2 * d);
+  for (int64_t m = zn + 1; m <= zf; ++m) {
+    const int32_t D = (int32_t)(__ldg(g.thr + (m - 1)) - sn);
+    int32_t k = __float2int_ru((float)D * inv2d);
+    k += (k * (k + td) < D) ? 1 : 0;
+    k -= (k > 0 && (k - 1) * (k - 1 + td) >= D) ? 1 : 0;
+    k -= (k > 0 && (k - 1) * (k - 1 + td) >= D) ? 1 : 0;
+    bits ^= (0xFFFFu << (right ? k : 16 - k)) & 0xFFFFu;
+  }
+  return bits;
+}
+
 // G_s = FFT_P(g_s) for every block s (one CTA per block, grid-strided).
 __global__ void __launch_bounds__(STH) k_seg_tables(int64_t nseg, int S, int M, double delta, float2* G) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -840,6 +881,7 @@ __global__ void __launch_bounds__(STH, 2) k_seg(RowArgs a) {
   float2* b1 = b0 + SBUF;
   float2* twA = b1 + SBUF;
   float2* twB = twA + 15 * 256;
+  uint32_t* mk = reinterpret_cast<uint32_t*>(twB + 256);  // open bits of a block, 16 columns per word
   seg_twiddles(twA, twB);
   const int t = threadIdx.x;
   const float2* pre = reinterpret_cast<const float2*>(a.pre);
@@ -869,17 +911,16 @@ __global__ void __launch_bounds__(STH, 2) k_seg(RowArgs a) {
           v[q] = (q < RS && i >= lo && i <= hi) ? __ldg(pre + i) : make_float2(0.0f, 0.0f);
         }
         if (FLAT) {
-          // inside [lo, hi] every column is inside the disc; elsewhere v is
-          // already 0 and the clamp keeps the zone rule inside its table
-          int64_t di = is + t - a.mg.c;
-          int64_t sq = dj * dj + di * di;
-#pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const int64_t z = zone_of(min(sq, a.mg.sR), a.mg);
-            if (((z ^ a.mg.centre_open) & 1) == 0) v[q] = make_float2(0.0f, 0.0f);
-            sq += 512 * di + 65536;
-            di += 256;
+          // thread t < S/16 makes the bits of columns is + 16 t ... + 15;
+          // element (t, q) is column is + 256 q + t: chunk 16 q + t/16, bit t % 16
+          if (t < S / 16) {
+            const int64_t x = is + 16 * t;
+            mk[t] = (x + 15 < lo || x > hi) ? 0u : chunk_bits(x, dj * dj, a.mg);
           }
+          __syncthreads();
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (((mk[16 * q + (t >> 4)] >> (t & 15)) & 1u) == 0) v[q] = make_float2(0.0f, 0.0f);
         } else {
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
