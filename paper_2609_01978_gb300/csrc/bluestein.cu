@@ -905,23 +905,37 @@ __global__ void __launch_bounds__(STH, 2) k_seg(RowArgs a) {
       for (int64_t s = lo / S; s <= s1; ++s) {
         const int64_t is = s * (int64_t)S;
         float2 v[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int64_t i = is + t + 256 * q;
-          v[q] = (q < RS && i >= lo && i <= hi) ? __ldg(pre + i) : make_float2(0.0f, 0.0f);
-        }
         if (FLAT) {
-          // thread t < S/16 makes the bits of columns is + 16 t ... + 15;
-          // element (t, q) is column is + 256 q + t: chunk 16 q + t/16, bit t % 16
-          if (t < S / 16) {
-            const int64_t x = is + 16 * t;
-            mk[t] = (x + 15 < lo || x > hi) ? 0u : chunk_bits(x, dj * dj, a.mg);
+          // the block's chord [olo, ohi] in block offsets; loads clamped into
+          // the grid, every element's value decided by its bit alone
+          const int olo = (int)max(lo - is, (int64_t)0), ohi = (int)min(hi - is, (int64_t)(S - 1));
+          const int lim = (int)min(a.N - 1 - is, (int64_t)(SP - 1));
+          const float2* pb = pre + is;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) v[q] = __ldg(pb + min(t + 256 * q, lim));
+          // thread t < S/16 makes the bits of block offsets 16 t ... 16 t + 15
+          // (zero outside the chord and beyond S); element (t, q) is offset
+          // 256 q + t: word 16 q + t/16, bit t % 16
+          {
+            const int xo = 16 * t;
+            uint32_t w = 0u;
+            if (t < S / 16 && xo + 15 >= olo && xo <= ohi) {
+              w = chunk_bits(is + xo, dj * dj, a.mg);
+              const int p0 = max(olo - xo, 0), p1 = min(ohi - xo, 15);  // chord within the chunk
+              w &= (0xFFFFu >> (15 - p1 + p0)) << p0;
+            }
+            mk[t] = w;
           }
           __syncthreads();
 #pragma unroll
           for (int q = 0; q < 16; ++q)
             if (((mk[16 * q + (t >> 4)] >> (t & 15)) & 1u) == 0) v[q] = make_float2(0.0f, 0.0f);
         } else {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int64_t i = is + t + 256 * q;
+            v[q] = (q < RS && i >= lo && i <= hi) ? __ldg(pre + i) : make_float2(0.0f, 0.0f);
+          }
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
             const int64_t i = is + t + 256 * q;
