@@ -112,8 +112,8 @@ KERNEL_SOURCES = {
 TRAFFIC = {
     # both launches of a row pass (the cluster launch and the single-CTA band
     # on the leftover SMs), captured one after the other
-    ("fzp-d0.25m", "dense"): (80.086e9 + 76.915e9 + 2.096e9 + 1.919e9, "3f6d4871cadf67d2eba48ed33d64bd586b9116721b569e1a845c2f931ee43035"),
-    ("fzp-d1m", "dense"): (1694.948e9 + 1216.615e9 + 44.293e9 + 41.776e9, "3f6d4871cadf67d2eba48ed33d64bd586b9116721b569e1a845c2f931ee43035"),
+    ("fzp-d0.25m", "dense"): (80.311e9 + 76.917e9 + 1.657e9 + 1.776e9, "3c073e7364fc6793e3ba5531cd0932794ecbf242e89dca2de577b8b85171f0c2"),
+    ("fzp-d1m", "dense"): (1796.474e9 + 1216.386e9 + 43.721e9 + 41.508e9, "3c073e7364fc6793e3ba5531cd0932794ecbf242e89dca2de577b8b85171f0c2"),
 }
 METRIC = "aperture Gsamples/s into 512² ROI, split-BF16 vs FP32 CZT at ≤1e-4 PSF error"
 UNIT = "Gsamples/s"

@@ -2,7 +2,8 @@
 //
 // Autotuner: for FZP_PREC_AUTO_1E4 (any arithmetic whose ROI-intensity error is
 // <= 1e-4) it builds the candidate plans -- the split-BF16 dense form with two
-// accumulation-chunk lengths, and the FP32 Bluestein form -- times each on a
+// accumulation-chunk lengths, and the FP32 Bluestein form (its partitioned
+// convolution unless the request asks for conv = 1) -- times each on a
 // probe stripe of central aperture rows sized to fill the GPU twice with dense
 // work items, and keeps the fastest.  Deformed membranes (complex
 // transmission) are dense candidates as binary amplitude plates (two membrane

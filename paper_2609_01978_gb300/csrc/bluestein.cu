@@ -169,7 +169,16 @@ __device__ __forceinline__ typename Cplx<R>::T aperture(const RowArgs& a, int64_
   if (a.mg.levels >= 2) {
     // L-level phase plate: e^{-2 pi i q / L}, q = zone mod L (Fig. 18 Stage 3)
     const int64_t q = z % a.mg.levels;
-    v = cis_turns<R>(-(double)q / (double)a.mg.levels);
+    if (sizeof(R) == 4) {
+      // FP32 form: -q / L turns lies in (-1, 0], so FP32 carries it to within
+      // an ulp without the FP64 reduction
+      float sn, cs;
+      sincospif(-2.0f * (float)q / (float)a.mg.levels, &sn, &cs);
+      v.x = cs;
+      v.y = sn;
+    } else {
+      v = cis_turns<R>(-(double)q / (double)a.mg.levels);
+    }
     if (!a.has_deform) return v;
   } else {
     if (((z ^ a.mg.centre_open) & 1) == 0) return v;  // binary amplitude: odd zones open (even: positive-centred)
@@ -189,7 +198,14 @@ __device__ __forceinline__ typename Cplx<R>::T aperture(const RowArgs& a, int64_
       const float d = (fi - a.df.pi_[k]) * a.df.nx[k] + (fj - a.df.pj[k]) * a.df.ny[k];
       wz += a.df.h2[k] * __expf(-a.df.q[k] * d * d);
     }
-    return cmul(v, cis_turns<R>((double)wz));
+    // wz - rint(wz) is exact in FP32, so the reduction adds nothing to wz's
+    // own rounding (the FP64 reduction of the same FP32 value gave the same)
+    float sn, cs;
+    sincospif(2.0f * (wz - rintf(wz)), &sn, &cs);
+    typename Cplx<R>::T e;
+    e.x = cs;
+    e.y = sn;
+    return cmul(v, e);
   }
   const double u = (double)(i - a.mg.c) * a.dx, w = (double)(j - a.mg.c) * a.dx;
   const fzp_deform& d = a.def;
