@@ -168,7 +168,8 @@ __device__ __forceinline__ typename Cplx<R>::T aperture(const RowArgs& a, int64_
   const int64_t z = zone_of(s, a.mg);
   if (a.mg.levels >= 2) {
     // L-level phase plate: e^{-2 pi i q / L}, q = zone mod L (Fig. 18 Stage 3)
-    const int64_t q = z % a.mg.levels;
+    // fewer than 2^24 zone steps (a plan limit): a 32-bit remainder
+    const int q = (int)((uint32_t)z % (uint32_t)a.mg.levels);
     if (sizeof(R) == 4) {
       // FP32 form: -q / L turns lies in (-1, 0], so FP32 carries it to within
       // an ulp without the FP64 reduction

@@ -107,3 +107,14 @@ def test_partitioned_equals_single(env):
         err = rel_l2(out[2], out[1])
         print(f"N = {g.N}: single vs partitioned, rel L2 of U {err:.3e}")
         assert err <= 2e-5
+
+
+def test_grid_narrower_than_the_disc(env):
+    """N = 4801 samples for a plate that needs 5057 (config 1's geometry): the
+    grid cuts the disc, so row chords are clipped to [0, N) on both sides."""
+    fzp, torch, O = env
+    g = O.Geometry(D=4e-3, f=20e-3, lam=LAM, M=256, p=0.2e-6, N=4801)
+    assert g.R / g.dx > g.c  # the disc reaches past the grid's edges
+    with _plan(fzp, g) as plan:
+        _, I = run_plan(fzp, torch, plan, g.M, 0, g.N)
+    assert rel_l2(I, np.abs(O.field_czt(g)) ** 2) <= 1e-4
