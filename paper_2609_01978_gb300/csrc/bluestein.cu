@@ -23,6 +23,11 @@
 //   pass F3 (L1 > 1): sum over k1, times e^{2 pi i post(m)} / L -> row intermediate.
 // The mask and the input chirp are generated inside F1 (or F2 when L1 = 1):
 // the aperture is never stored.
+//
+// FP32 default (fzp_params.conv): the same convolution partitioned into
+// 4096-point blocks, each row on chip from its mask to its M outputs
+// (k_seg, below); the four-step passes above remain the FP64 path and the
+// single-convolution FP32 option.
 #include <algorithm>
 #include <cmath>
 
@@ -337,13 +342,7 @@ __global__ void __launch_bounds__(512) k_f2(RowArgs a, int mode) {
 }
 
 // ---------------------------------------------------------------- FP32 pass F2, radix 16
-// L2 = 4096 = 16^3 points, 256 threads x 16 values in registers, Stockham
-// order (pass s, Ns = 16^s: x_r = in[j + 256 r] times W_{16 Ns}^{r k},
-// k = j mod Ns, 16-point DFT, y_q -> out[(j / Ns) 16 Ns + q Ns + k]).  The
-// 16-point DFT is 4 x 4 (two radix-4 layers with W_16^{ac} between); shared
-// memory is padded by one element per 16 against bank conflicts.
-constexpr int RL = 4096, RT = 256;
-__device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
+constexpr int RL = 4096;  // inner FFT length of the FP32 four-step split
 
 __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3, bool inv) {
   const float2 s02 = make_float2(a0.x + a2.x, a0.y + a2.y), d02 = make_float2(a0.x - a2.x, a0.y - a2.y);
@@ -353,143 +352,6 @@ __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2&
   a2 = make_float2(s02.x - s13.x, s02.y - s13.y);
   a1 = make_float2(d02.x + t.x, d02.y + t.y);
   a3 = make_float2(d02.x - t.x, d02.y - t.y);
-}
-
-// In place; afterwards y_q sits in v[4 (q % 4) + q / 4].
-__device__ __forceinline__ void dft16(float2 (&v)[16], bool inv) {
-#pragma unroll
-  for (int a = 0; a < 4; ++a) dft4(v[a], v[a + 4], v[a + 8], v[a + 12], inv);
-  // W_16^{a c}, a, c in 1..3: cos / sin of 2 pi k / 16 for k = 1, 2, 3, 4, 6, 9
-  const float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f, c2 = 0.70710678118654752f;
-#pragma unroll
-  for (int a = 1; a < 4; ++a)
-#pragma unroll
-    for (int c = 1; c < 4; ++c) {
-      const int k = a * c;
-      float cs, sn;
-      switch (k) {
-        case 1: cs = c1; sn = s1; break;
-        case 2: cs = c2; sn = c2; break;
-        case 3: cs = s1; sn = c1; break;
-        case 4: cs = 0.f; sn = 1.f; break;
-        case 6: cs = -c2; sn = c2; break;
-        default: cs = -c1; sn = -s1; break;  // k = 9
-      }
-      if (!inv) sn = -sn;
-      float2& x = v[a + 4 * c];
-      x = make_float2(x.x * cs - x.y * sn, x.x * sn + x.y * cs);
-    }
-#pragma unroll
-  for (int c = 0; c < 4; ++c) dft4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3], inv);
-}
-
-__device__ __forceinline__ float2 y_of(const float2 (&v)[16], int q) { return v[4 * (q & 3) + (q >> 2)]; }
-
-__device__ __forceinline__ void twiddle16(float2 (&v)[16], int k, int step, const float2* __restrict__ tw, bool inv) {
-#pragma unroll
-  for (int r = 1; r < 16; ++r) {
-    float2 w = __ldg(tw + r * k * step);
-    if (inv) w.y = -w.y;
-    v[r] = make_float2(v[r].x * w.x - v[r].y * w.y, v[r].x * w.y + v[r].y * w.x);
-  }
-}
-
-// mode 0: row transform; mode 1: forward FFT only, natural order -> Z row (table build).
-__global__ void __launch_bounds__(RT) k_f2_r16(RowArgs a, int mode) {
-  __shared__ float2 sm[RL + RL / 16];
-  const int j = threadIdx.x;
-  const int64_t k1 = blockIdx.x, r = blockIdx.y, row = a.j0 + r;
-  const float2* tw = reinterpret_cast<const float2*>(a.tw);
-  float2 v[16];
-  if (a.L1 == 1) {
-    const float2* pre = reinterpret_cast<const float2*>(a.pre);
-    const float2* vin = reinterpret_cast<const float2*>(a.vin);
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int n = j + RT * q;
-      if (mode == 0) {
-        float2 x = aperture<float>(a, row, n);
-        if (x.x != 0.f || x.y != 0.f) x = cmul(x, pre[n]);
-        v[q] = x;
-      } else {
-        v[q] = vin[n];
-      }
-    }
-  } else {
-    const float2* Z = reinterpret_cast<const float2*>(a.Z) + r * a.L + k1 * RL;
-#pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = Z[j + RT * q];
-  }
-  // forward: passes Ns = 1, 16, 256
-  dft16(v, false);
-#pragma unroll
-  for (int q = 0; q < 16; ++q) sm[pidx(j * 16 + q)] = y_of(v, q);
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = sm[pidx(j + RT * q)];
-  __syncthreads();
-  twiddle16(v, j & 15, 16, tw, false);
-  dft16(v, false);
-#pragma unroll
-  for (int q = 0; q < 16; ++q) sm[pidx((j >> 4) * 256 + q * 16 + (j & 15))] = y_of(v, q);
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = sm[pidx(j + RT * q)];
-  __syncthreads();
-  twiddle16(v, j, 1, tw, false);
-  dft16(v, false);
-  if (mode == 1) {
-    float2* out = reinterpret_cast<float2*>(a.Z) + r * a.L + k1 * RL;
-#pragma unroll
-    for (int q = 0; q < 16; ++q) out[q * 256 + j] = y_of(v, q);
-    return;
-  }
-  const float2* H = reinterpret_cast<const float2*>(a.H) + k1 * RL;
-#pragma unroll
-  for (int q = 0; q < 16; ++q) sm[pidx(q * 256 + j)] = cmul(y_of(v, q), H[q * 256 + j]);
-  __syncthreads();
-  // inverse: same passes with conjugate twiddles
-#pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = sm[pidx(j + RT * q)];
-  __syncthreads();
-  dft16(v, true);
-#pragma unroll
-  for (int q = 0; q < 16; ++q) sm[pidx(j * 16 + q)] = y_of(v, q);
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = sm[pidx(j + RT * q)];
-  __syncthreads();
-  twiddle16(v, j & 15, 16, tw, true);
-  dft16(v, true);
-#pragma unroll
-  for (int q = 0; q < 16; ++q) sm[pidx((j >> 4) * 256 + q * 16 + (j & 15))] = y_of(v, q);
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = sm[pidx(j + RT * q)];
-  twiddle16(v, j, 1, tw, true);
-  dft16(v, true);
-  // outputs m = q * 256 + j < M
-  if (a.L1 == 1) {
-    const float2* post = reinterpret_cast<const float2*>(a.post);
-    float* C1 = reinterpret_cast<float*>(a.C1);
-    const int64_t jl = row - a.c1_j0;
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int m = q * 256 + j;
-      if (m < a.M) {
-        const float2 z = cmul(y_of(v, q), post[m]);
-        C1[(int64_t)c1_row_re(m) * a.c1_stride + jl] = z.x;
-        C1[(int64_t)c1_row_im(m) * a.c1_stride + jl] = z.y;
-      }
-    }
-    return;
-  }
-  float2* G = reinterpret_cast<float2*>(a.G) + (r * a.L1 + k1) * a.M;
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int m = q * 256 + j;
-    if (m < a.M) G[m] = cmul(y_of(v, q), twiddle_L<float>(a, (k1 * m) & (a.L - 1), true));
-  }
 }
 
 // ---------------------------------------------------------------- FP32 pass F2, radix 8
