@@ -67,8 +67,8 @@ def test_batch_graph_matches_single_plans_and_oracle(env):
 
 
 def test_autotune_picks_dense_for_large_flat_aperture(env):
-    """At D = 0.25 m the split-BF16 dense form is an order of magnitude faster
-    than the FP32 Bluestein form on the probe stripe."""
+    """At D = 0.25 m the split-BF16 dense form is faster than the FP32
+    Bluestein form (partitioned convolution: about 1.5x) on the probe stripe."""
     fzp, torch, O = env
     lam = 632.8e-9
     with fzp.Plan(D=0.25, f=1.25, lam=lam, M=512, pitch=lam * 5 / 8, precision=fzp.PREC_AUTO_1E4) as plan:
@@ -79,3 +79,23 @@ def test_autotune_picks_dense_for_large_flat_aperture(env):
         j0 = g.c + 777
         _, I = run_plan(fzp, torch, plan, 512, j0, j0 + 512)
     assert rel_l2(I, np.abs(O.field_czt(g, j0, j0 + 512)) ** 2) <= 1e-4
+
+
+def test_autotune_picks_partitioned_fp32_for_sixteen_levels(env):
+    """A 16-level phase plate (D = 0.02 m at f/5 on Fig. 18 Stage 1's grid,
+    N = 202,277): the dense form takes L/2 = 8 signed-mask passes, the
+    partitioned FP32 Bluestein form one pass whatever L, so the autotuner,
+    which times both on its probe stripe, keeps the FP32 form; the tuned plan
+    matches the oracle on 64 rows at v = R/3."""
+    fzp, torch, O = env
+    lam = 632.8e-9
+    with fzp.Plan(D=0.02, f=0.1, lam=lam, M=256, pitch=lam * 5 / 8, levels=16,
+                  precision=fzp.PREC_AUTO_1E4) as plan:
+        info = plan.info
+        assert info["form"] == fzp.FORM_BLUESTEIN and info["precision"] == fzp.PREC_FP32
+        assert info["conv"] == 2
+        g = O.Geometry(D=0.02, f=0.1, lam=lam, M=256, p=lam * 5 / 8, kind=O.FZP_PHASE, levels=16)
+        assert info["N"] == g.N
+        j0 = g.c + int(g.R / g.dx / 3)
+        _, I = run_plan(fzp, torch, plan, 256, j0, j0 + 64)
+    assert rel_l2(I, np.abs(O.field_czt(g, j0, j0 + 64)) ** 2) <= 1e-4
