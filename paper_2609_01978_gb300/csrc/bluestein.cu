@@ -562,7 +562,10 @@ constexpr int STH = 256;          // threads per block
 constexpr int SB0 = 256 * 17;     // transpose buffer A->B: [t][k0], row pitch 17
 constexpr int SB1 = 16 * 273;     // transpose buffer B->C: [k0][c][a], pitches 273 and 17
 constexpr int SBUF = SB1 > SB0 ? SB1 : SB0;
-constexpr size_t SEG_SMEM = sizeof(float2) * (2 * SBUF + 15 * 256 + 256) + sizeof(uint32_t) * 256;
+constexpr size_t SEG_SMEM = sizeof(float2) * (2 * SBUF + 15 * 256 + 256 + 64) + sizeof(uint32_t) * 512;
+// row kernels: binary plate (chunk bits), phase plate (chunk zone steps),
+// general transmission (membrane phase)
+enum { SEG_FLAT = 0, SEG_LEVELS = 1, SEG_GENERAL = 2 };
 
 // v e^{-2 pi i K / 16}
 template <int K>
@@ -713,6 +716,53 @@ __device__ __forceinline__ uint32_t chunk_bits(int64_t x, int64_t dj2, const Mas
   return bits;
 }
 
+// Zone steps of the 16 columns [x, x + 16) of a row of the phase plate:
+// *z0 the zone at column x, *ud the columns at which the zone steps up
+// (bits 0-15) or down (bits 16-31), so that z(x + p) = z0 + popc(up & m_p) -
+// popc(down & m_p), m_p = bits 0..p.  Away from the axis the steps are the
+// boundaries between the chunk's ends, placed by the window search of
+// chunk_bits (all up right of the axis, all down left of it); within 128
+// columns of it the zone rule runs column by column.  Returns false when two
+// boundaries share a column (possible only at a sampling finer than one
+// sample per level step); the caller then evaluates the zone rule per
+// element.  Columns outside the disc come out arbitrary.
+__device__ __forceinline__ bool chunk_zones(int64_t x, int64_t dj2, const MaskGeom& g, uint32_t* z0, uint32_t* ud) {
+  const int64_t dr = x - g.c, dl = g.c - (x + 15);
+  if (dr < 128 && dl < 128) {
+    int64_t zp = zone_of(min(dj2 + dr * dr, g.sR), g);
+    *z0 = (uint32_t)zp;
+    uint32_t up = 0u, dn = 0u;
+    for (int p = 1; p < 16; ++p) {
+      const int64_t di = dr + p, z = zone_of(min(dj2 + di * di, g.sR), g);
+      if (z == zp + 1) up |= 1u << p;
+      else if (z == zp - 1) dn |= 1u << p;
+      else if (z != zp) return false;
+      zp = z;
+    }
+    *ud = up | (dn << 16);
+    return true;
+  }
+  const bool right = dr >= 128;
+  const int64_t d = right ? dr : dl;
+  const int64_t sn = dj2 + d * d, sf = dj2 + (d + 15) * (d + 15);
+  const int64_t zn = zone_of(min(sn, g.sR), g), zf = zone_of(min(sf, g.sR), g);
+  const float inv2d = 0.5f / (float)d;
+  const int32_t td = (int32_t)(2 * d);
+  uint32_t ev = 0u;
+  for (int64_t m = zn + 1; m <= zf; ++m) {
+    const int32_t D = (int32_t)(__ldg(g.thr + (m - 1)) - sn);
+    int32_t k = __float2int_ru((float)D * inv2d);
+    k += (k * (k + td) < D) ? 1 : 0;
+    k -= (k > 0 && (k - 1) * (k - 1 + td) >= D) ? 1 : 0;
+    k -= (k > 0 && (k - 1) * (k - 1 + td) >= D) ? 1 : 0;
+    ev |= 1u << (right ? k : 16 - k);
+  }
+  if ((int64_t)__popc(ev) != zf - zn) return false;
+  *z0 = (uint32_t)(right ? zn : zf);
+  *ud = right ? ev : (ev << 16);
+  return true;
+}
+
 // G_s = FFT_P(g_s) for every block s (one CTA per block, grid-strided).
 __global__ void __launch_bounds__(STH) k_seg_tables(int64_t nseg, int S, int M, double delta, float2* G) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -747,20 +797,31 @@ __global__ void __launch_bounds__(STH) k_seg_tables(int64_t nseg, int S, int M, 
 
 // Row pass of the partitioned convolution: rows j0 + r, r = blockIdx.x,
 // blockIdx.x + gridDim.x, ... (interleaved, so every CTA gets rows from the
-// whole range of chord lengths); writes C1 like k_f3.  FLAT: binary amplitude
-// plate without deformation, the zone rule evaluated on the squared radius
-// stepped from column to column of the thread (s += 512 di + 256^2); otherwise
-// the general transmission (phase levels, membrane phase).  A block's input
-// chirp loads are issued together before the mask is evaluated, and the
-// spectra G_s before the last FFT pass, so each waits one memory latency.
-template <bool FLAT>
+// whole range of chord lengths); writes C1 like k_f3.  The transmission of a
+// block's samples: SEG_FLAT, binary amplitude plate without deformation, open
+// bits per chunk of 16 columns (chunk_bits); SEG_LEVELS, phase plate without
+// deformation, zone steps per chunk (chunk_zones) and the level's phasor from
+// a table; SEG_GENERAL, the transmission function per sample (membrane
+// phase).  A block's input chirp loads are issued together before the
+// transmission is evaluated, and the spectra G_s before the last FFT pass,
+// so each waits one memory latency.
+template <int MODE>
 __global__ void __launch_bounds__(STH, 2) k_seg(RowArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* b0 = reinterpret_cast<float2*>(smem_raw);
   float2* b1 = b0 + SBUF;
   float2* twA = b1 + SBUF;
   float2* twB = twA + 15 * 256;
-  uint32_t* mk = reinterpret_cast<uint32_t*>(twB + 256);  // open bits of a block, 16 columns per word
+  float2* phs = twB + 256;                             // SEG_LEVELS: e^{-2 pi i q / L}, q < L <= 64
+  uint32_t* mk = reinterpret_cast<uint32_t*>(phs + 64);  // per chunk: open bits, or zone at its first column
+  uint32_t* mk2 = mk + 256;                             // per chunk: zone steps up | down << 16
+  const uint32_t nlev = (uint32_t)max(a.mg.levels, 1);
+  const uint32_t lmagic = 0xFFFFFFFFu / nlev + 1u;     // z / L = umulhi(z, ceil(2^32 / L)) for z < 2^24
+  if (MODE == SEG_LEVELS && threadIdx.x < nlev) {
+    float sn, cs;
+    sincospif(-2.0f * (float)threadIdx.x / (float)nlev, &sn, &cs);
+    phs[threadIdx.x] = make_float2(cs, sn);
+  }
   seg_twiddles(twA, twB);
   const int t = threadIdx.x;
   const float2* pre = reinterpret_cast<const float2*>(a.pre);
@@ -784,7 +845,7 @@ __global__ void __launch_bounds__(STH, 2) k_seg(RowArgs a) {
       for (int64_t s = lo / S; s <= s1; ++s) {
         const int64_t is = s * (int64_t)S;
         float2 v[16];
-        if (FLAT) {
+        if (MODE == SEG_FLAT) {
           // the block's chord [olo, ohi] in block offsets; loads clamped into
           // the grid, every element's value decided by its bit alone
           const int olo = (int)max(lo - is, (int64_t)0), ohi = (int)min(hi - is, (int64_t)(S - 1));
@@ -809,6 +870,41 @@ __global__ void __launch_bounds__(STH, 2) k_seg(RowArgs a) {
 #pragma unroll
           for (int q = 0; q < 16; ++q)
             if (((mk[16 * q + (t >> 4)] >> (t & 15)) & 1u) == 0) v[q] = make_float2(0.0f, 0.0f);
+        } else if (MODE == SEG_LEVELS) {
+          const int olo = (int)max(lo - is, (int64_t)0), ohi = (int)min(hi - is, (int64_t)(S - 1));
+          const int lim = (int)min(a.N - 1 - is, (int64_t)(SP - 1));
+          const float2* pb = pre + is;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) v[q] = __ldg(pb + min(t + 256 * q, lim));
+          // chunk t: zone at its first column (bit 31: evaluate per element) and its steps
+          {
+            const int xo = 16 * t;
+            uint32_t z0 = 0u, ud = 0u;
+            if (t < S / 16 && xo + 15 >= olo && xo <= ohi)
+              if (!chunk_zones(is + xo, dj * dj, a.mg, &z0, &ud)) z0 = 0x80000000u;
+            mk[t] = z0;
+            mk2[t] = ud;
+          }
+          __syncthreads();
+          const uint32_t mp = (2u << (t & 15)) - 1u;  // steps at or before this thread's column of a chunk
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int o = t + 256 * q;
+            if ((unsigned)(o - olo) > (unsigned)(ohi - olo)) {
+              v[q] = make_float2(0.0f, 0.0f);  // outside the chord (and beyond S)
+              continue;
+            }
+            const uint32_t z0 = mk[16 * q + (t >> 4)], ud = mk2[16 * q + (t >> 4)];
+            uint32_t z;
+            if (z0 & 0x80000000u) {
+              const int64_t di = is + o - a.mg.c;
+              z = (uint32_t)zone_of(min(dj * dj + di * di, a.mg.sR), a.mg);
+            } else {
+              z = z0 + __popc(ud & mp) - __popc((ud >> 16) & mp);
+            }
+            const uint32_t lv = z - nlev * __umulhi(z, lmagic);
+            v[q] = cmul(v[q], phs[lv]);
+          }
         } else {
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
@@ -998,9 +1094,10 @@ fzp_status layout_t(Plan& P, FormSizes* out) {
     out->Z = 0;
     out->G = 0;
     static std::atomic<uint64_t> attr_seg{0}, attr_segt{0};
-    static std::atomic<uint64_t> attr_segg{0};
-    FZP_CUDA_TRY(smem_attr_once((const void*)k_seg<true>, (int)SEG_SMEM, attr_seg));
-    FZP_CUDA_TRY(smem_attr_once((const void*)k_seg<false>, (int)SEG_SMEM, attr_segg));
+    static std::atomic<uint64_t> attr_segl{0}, attr_segg{0};
+    FZP_CUDA_TRY(smem_attr_once((const void*)k_seg<SEG_FLAT>, (int)SEG_SMEM, attr_seg));
+    FZP_CUDA_TRY(smem_attr_once((const void*)k_seg<SEG_LEVELS>, (int)SEG_SMEM, attr_segl));
+    FZP_CUDA_TRY(smem_attr_once((const void*)k_seg<SEG_GENERAL>, (int)SEG_SMEM, attr_segg));
     FZP_CUDA_TRY(smem_attr_once((const void*)k_seg_tables, (int)SEG_SMEM, attr_segt));
     return FZP_OK;
   }
@@ -1079,17 +1176,19 @@ fzp_status rows_t(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
     int ctas_per_sm = 0, sms = 0, dev = 0;
     FZP_CUDA_TRY(cudaGetDevice(&dev));
     FZP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const bool flat = P.levels < 2 && !P.has_deform;
-    FZP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, flat ? (const void*)k_seg<true>
-                                                                                 : (const void*)k_seg<false>,
-                                                               STH, SEG_SMEM));
+    const int mode = P.has_deform ? SEG_GENERAL : (P.levels >= 2 ? SEG_LEVELS : SEG_FLAT);
+    const void* kern = mode == SEG_FLAT ? (const void*)k_seg<SEG_FLAT>
+                                        : (mode == SEG_LEVELS ? (const void*)k_seg<SEG_LEVELS>
+                                                              : (const void*)k_seg<SEG_GENERAL>);
+    FZP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, kern, STH, SEG_SMEM));
     if (ctas_per_sm < 1) ctas_per_sm = 1;
     a.j0 = j0;
     a.rows = rows;
     const int64_t grid = std::min<int64_t>(rows, (int64_t)ctas_per_sm * sms);
     prof_begin(P, s);
-    if (flat) k_seg<true><<<(unsigned)grid, STH, SEG_SMEM, s>>>(a);
-    else k_seg<false><<<(unsigned)grid, STH, SEG_SMEM, s>>>(a);
+    if (mode == SEG_FLAT) k_seg<SEG_FLAT><<<(unsigned)grid, STH, SEG_SMEM, s>>>(a);
+    else if (mode == SEG_LEVELS) k_seg<SEG_LEVELS><<<(unsigned)grid, STH, SEG_SMEM, s>>>(a);
+    else k_seg<SEG_GENERAL><<<(unsigned)grid, STH, SEG_SMEM, s>>>(a);
     prof_end(P, s);
     P.launches += 1;
     FZP_CUDA_TRY(cudaGetLastError());

@@ -146,3 +146,95 @@ def test_chunk_rule_equals_column_rule(fzp, case):
             n_events += bin(want ^ (want << 1) & 0xFFFF).count("1")
     assert n_chunks > 1000 and n_events > 500, (n_chunks, n_events)
 
+
+
+def _chunk_zones(x, dj2, c, sR, thr, zone):
+    """The kernel's phase-plate chunk rule: (ok, z0, up, down)."""
+    dr, dl = x - c, c - (x + 15)
+    if dr < 128 and dl < 128:
+        zp = zone(min(dj2 + dr * dr, sR))
+        z0, up, dn = zp, 0, 0
+        for p in range(1, 16):
+            z = zone(min(dj2 + (dr + p) ** 2, sR))
+            if z == zp + 1:
+                up |= 1 << p
+            elif z == zp - 1:
+                dn |= 1 << p
+            elif z != zp:
+                return False, 0, 0, 0
+            zp = z
+        return True, z0, up, dn
+    right = dr >= 128
+    d = dr if right else dl
+    sn, sf = dj2 + d * d, dj2 + (d + 15) ** 2
+    zn, zf = zone(min(sn, sR)), zone(min(sf, sR))
+    ev = 0
+    for m in range(zn + 1, zf + 1):
+        k = int(window16(np.array([thr[m - 1] - sn], dtype=np.int64), d)[0])
+        ev |= 1 << (k if right else 16 - k)
+    if bin(ev).count("1") != zf - zn:
+        return False, 0, 0, 0
+    return (True, zn, ev, 0) if right else (True, zf, 0, ev)
+
+
+PHASE_CASES = {
+    "table4_grid_L4": dict(D=4.0, f=20.0, lam=532e-9, levels=4, dx=532e-9 * 20.0 / 2.0 / 16),
+    "d0.02m_L16": dict(D=0.02, f=0.1, lam=LAM, levels=16),
+    "d0.05m_L8": dict(D=0.05, f=0.25, lam=LAM, levels=8),
+    "d0.01m_L3": dict(D=0.01, f=0.05, lam=LAM, levels=3),
+}
+
+
+@pytest.mark.parametrize("case", sorted(PHASE_CASES))
+def test_chunk_zone_steps_equal_column_zones(fzp, case):
+    """Phase plates: the chunk's zone at its first column plus the up and down
+    steps at or before each column (two popcounts) give the zone of every
+    column inside the disc; then the level is z mod L, computed as
+    z - L umulhi(z, ceil(2^32 / L))."""
+    kw = dict(PHASE_CASES[case], M=512, pitch=LAM * 5 / 8)
+    q = fzp.plan_query(**kw)
+    thr = [int(x) for x in fzp.zone_thresholds(**kw)]
+    c, sR, L = q["c"], q["s_R"], kw["levels"]
+    magic = (0xFFFFFFFF // L) + 1
+
+    def zone(s):
+        return bisect.bisect_right(thr, s)
+
+    rng = np.random.default_rng(sum(map(ord, case)))
+    bmax0 = math.isqrt(sR)
+    n_chunks = n_steps = 0
+    for dj in [0, 5, bmax0 // 3, bmax0 - 2] + [int(x) for x in rng.integers(-bmax0, bmax0, 30)]:
+        dj2 = dj * dj
+        if dj2 > sR:
+            continue
+        b = math.isqrt(sR - dj2)
+        lo, hi = c - b, c + b
+        xs = [lo, hi - 15, c - 15, c - 7, c + 3, c - 143, c + 128]
+        xs += [int(x) for x in rng.integers(lo, max(lo + 1, hi - 15), 40)]
+        for x in xs:
+            if x + 15 < lo or x > hi:
+                continue
+            ok, z0, up, dn = _chunk_zones(x, dj2, c, sR, thr, zone)
+            assert ok, (case, dj, x)
+            for p in range(16):
+                s = dj2 + (x + p - c) ** 2
+                if s > sR:
+                    continue
+                mp = (2 << p) - 1
+                z = z0 + bin(up & mp).count("1") - bin(dn & mp).count("1")
+                assert z == zone(s), (case, dj, x, p)
+                lev = z - L * ((z * magic) >> 32)
+                assert lev == z % L
+            n_chunks += 1
+            n_steps += bin(up | dn).count("1")
+    assert n_chunks > 500 and n_steps > 200, (n_chunks, n_steps)
+
+
+def test_level_remainder_by_multiply_high():
+    rng = np.random.default_rng(9)
+    zs = [0, 1, (1 << 24) - 1] + [int(x) for x in rng.integers(0, 1 << 24, 3000)]
+    for L in range(2, 65):
+        magic = (0xFFFFFFFF // L) + 1
+        extra = [L * k + e for k in (1, 1000, (1 << 24) // L - 1) for e in (-1, 0, 1) if 0 <= L * k + e < (1 << 24)]
+        for z in zs + extra:
+            assert z - L * ((z * magic) >> 32) == z % L, (L, z)

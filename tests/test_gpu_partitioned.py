@@ -118,3 +118,20 @@ def test_grid_narrower_than_the_disc(env):
     with _plan(fzp, g) as plan:
         _, I = run_plan(fzp, torch, plan, g.M, 0, g.N)
     assert rel_l2(I, np.abs(O.field_czt(g)) ** 2) <= 1e-4
+
+
+@pytest.mark.parametrize("L,D,rows", [(3, 2e-3, None), (5, 1e-3, None), (16, 4e-3, 96)])
+def test_phase_plates_any_level_count(env, L, D, rows):
+    """Phase plates on the partitioned form's zone-step path (the dense form
+    takes even L only): L = 3 and 5 whole, L = 16 on rows at v = R/3 of a
+    plate of N = 40,457 (level steps four samples wide at the rim, the
+    grid of Fig. 18 Stage 1)."""
+    fzp, torch, O = env
+    g = O.Geometry(D=D, f=5 * D, lam=LAM, M=64 if rows is None else 128, p=LAM * 5 / 8, kind=O.FZP_PHASE,
+                   levels=L)
+    a, b = (0, g.N) if rows is None else (g.c + int(g.R / g.dx / 3), g.c + int(g.R / g.dx / 3) + rows)
+    with _plan(fzp, g, levels=L) as plan:
+        _, I = run_plan(fzp, torch, plan, g.M, a, b)
+    err = rel_l2(I, np.abs(O.field_czt(g, a, b)) ** 2)
+    print(f"partitioned phase plate L = {L}, N = {g.N}, rows [{a}, {b}): rel L2 of I {err:.3e}")
+    assert err <= 1e-4
