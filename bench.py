@@ -302,8 +302,10 @@ def run_membranes(args, fzp, torch, dev, ws, pg, rank, local):
         achieved = dense_flops * args.steps / (ms / 1e3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "whole step (graph of every instance's passes; dense membrane "
-                                           "passes dominate)", "peak_source": peak_kind + " bf16 sustained",
+                "traffic": None, "kernel": "whole step (graph of every instance's passes): tensor work of "
+                                           "the dense instances over the whole step's time, a lower bound "
+                                           "when some instances chose the FP32 form",
+                "peak_source": peak_kind + " bf16 sustained",
                 "work": "24 M flops per aperture sample inside the disc (dense instances only)"}
     # end to end through the public API with host buffers: batch from host
     # parameters (tuned choices cached in-process), propagate, fields to pinned

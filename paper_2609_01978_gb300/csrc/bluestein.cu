@@ -564,8 +564,36 @@ constexpr int SB1 = 16 * 273;     // transpose buffer B->C: [k0][c][a], pitches 
 constexpr int SBUF = SB1 > SB0 ? SB1 : SB0;
 constexpr size_t SEG_SMEM = sizeof(float2) * (2 * SBUF + 15 * 256 + 256 + 64) + sizeof(uint32_t) * 512;
 // row kernels: binary plate (chunk bits), phase plate (chunk zone steps),
-// general transmission (membrane phase)
-enum { SEG_FLAT = 0, SEG_LEVELS = 1, SEG_GENERAL = 2 };
+// deformed binary plate (chunk bits and the membrane phasor), general
+// transmission (a deformed phase plate)
+enum { SEG_FLAT = 0, SEG_LEVELS = 1, SEG_MEMBRANE = 2, SEG_GENERAL = 3 };
+
+// Membrane phasor e^{i phi} of the sample at (fi, fj) = (i - c, j - c) for the
+// FP32 partitioned pass: phi / 2 pi = 2 w / lambda from the FP32 coefficients
+// (the wrinkle's turns as in the transmission function: di kxh exact, its
+// integer part dropped exactly), the wrinkle's turns and the total reduced to
+// [-1/2, 1/2] before the hardware sine and cosine (absolute error below 4e-7
+// each).  Row terms: fjkh = fj kyh, fjkl = fj kyl, fj2 = fj^2, cr[e] = (fj -
+// pj_e) ny_e - pi_e nx_e, so a ridge's distance is fi nx_e + cr[e].
+__device__ __forceinline__ float2 membrane_phasor(const DeformCoef& d, float fi, float fjkh, float fjkl, float fj2,
+                                                  const float (&cr)[3]) {
+  constexpr float TWO_PI = 6.28318530717958648f;
+  const float th = fmaf(fi, d.kxh, fjkh);
+  float tt = (th - rintf(th)) + fmaf(fi, d.kxl, fjkl);
+  tt -= rintf(tt);
+  float wz = d.amp2 * __sinf(TWO_PI * tt) * fmaf(-d.tq, fmaf(fi, fi, fj2), 1.0f);
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    if (e < d.n) {
+      const float dd = fmaf(fi, d.nx[e], cr[e]);
+      wz = fmaf(d.h2[e], __expf(-d.q[e] * dd * dd), wz);
+    }
+  }
+  wz -= rintf(wz);
+  float sn, cs;
+  __sincosf(TWO_PI * wz, &sn, &cs);
+  return make_float2(cs, sn);
+}
 
 // v e^{-2 pi i K / 16}
 template <int K>
@@ -845,7 +873,7 @@ __global__ void __launch_bounds__(STH, 2) k_seg(RowArgs a) {
       for (int64_t s = lo / S; s <= s1; ++s) {
         const int64_t is = s * (int64_t)S;
         float2 v[16];
-        if (MODE == SEG_FLAT) {
+        if (MODE == SEG_FLAT || MODE == SEG_MEMBRANE) {
           // the block's chord [olo, ohi] in block offsets; loads clamped into
           // the grid, every element's value decided by its bit alone
           const int olo = (int)max(lo - is, (int64_t)0), ohi = (int)min(hi - is, (int64_t)(S - 1));
@@ -870,6 +898,18 @@ __global__ void __launch_bounds__(STH, 2) k_seg(RowArgs a) {
 #pragma unroll
           for (int q = 0; q < 16; ++q)
             if (((mk[16 * q + (t >> 4)] >> (t & 15)) & 1u) == 0) v[q] = make_float2(0.0f, 0.0f);
+          if (MODE == SEG_MEMBRANE) {
+            const float fj = (float)dj;
+            const float fjkh = fj * a.df.kyh, fjkl = fj * a.df.kyl, fj2 = fj * fj;
+            float cr[3];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) cr[e] = (fj - a.df.pj[e]) * a.df.ny[e] - a.df.pi_[e] * a.df.nx[e];
+            const float fi0 = (float)(is + t - a.mg.c);
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              if (v[q].x != 0.0f || v[q].y != 0.0f)
+                v[q] = cmul(v[q], membrane_phasor(a.df, fi0 + 256.0f * q, fjkh, fjkl, fj2, cr));
+          }
         } else if (MODE == SEG_LEVELS) {
           const int olo = (int)max(lo - is, (int64_t)0), ohi = (int)min(hi - is, (int64_t)(S - 1));
           const int lim = (int)min(a.N - 1 - is, (int64_t)(SP - 1));
@@ -1094,9 +1134,10 @@ fzp_status layout_t(Plan& P, FormSizes* out) {
     out->Z = 0;
     out->G = 0;
     static std::atomic<uint64_t> attr_seg{0}, attr_segt{0};
-    static std::atomic<uint64_t> attr_segl{0}, attr_segg{0};
+    static std::atomic<uint64_t> attr_segl{0}, attr_segm{0}, attr_segg{0};
     FZP_CUDA_TRY(smem_attr_once((const void*)k_seg<SEG_FLAT>, (int)SEG_SMEM, attr_seg));
     FZP_CUDA_TRY(smem_attr_once((const void*)k_seg<SEG_LEVELS>, (int)SEG_SMEM, attr_segl));
+    FZP_CUDA_TRY(smem_attr_once((const void*)k_seg<SEG_MEMBRANE>, (int)SEG_SMEM, attr_segm));
     FZP_CUDA_TRY(smem_attr_once((const void*)k_seg<SEG_GENERAL>, (int)SEG_SMEM, attr_segg));
     FZP_CUDA_TRY(smem_attr_once((const void*)k_seg_tables, (int)SEG_SMEM, attr_segt));
     return FZP_OK;
@@ -1176,10 +1217,11 @@ fzp_status rows_t(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
     int ctas_per_sm = 0, sms = 0, dev = 0;
     FZP_CUDA_TRY(cudaGetDevice(&dev));
     FZP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int mode = P.has_deform ? SEG_GENERAL : (P.levels >= 2 ? SEG_LEVELS : SEG_FLAT);
+    const int mode = P.has_deform ? (P.levels >= 2 ? SEG_GENERAL : SEG_MEMBRANE) : (P.levels >= 2 ? SEG_LEVELS : SEG_FLAT);
     const void* kern = mode == SEG_FLAT ? (const void*)k_seg<SEG_FLAT>
-                                        : (mode == SEG_LEVELS ? (const void*)k_seg<SEG_LEVELS>
-                                                              : (const void*)k_seg<SEG_GENERAL>);
+                       : mode == SEG_LEVELS ? (const void*)k_seg<SEG_LEVELS>
+                       : mode == SEG_MEMBRANE ? (const void*)k_seg<SEG_MEMBRANE>
+                                              : (const void*)k_seg<SEG_GENERAL>;
     FZP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, kern, STH, SEG_SMEM));
     if (ctas_per_sm < 1) ctas_per_sm = 1;
     a.j0 = j0;
@@ -1188,6 +1230,7 @@ fzp_status rows_t(Plan& P, int64_t j0, int64_t rows, cudaStream_t s) {
     prof_begin(P, s);
     if (mode == SEG_FLAT) k_seg<SEG_FLAT><<<(unsigned)grid, STH, SEG_SMEM, s>>>(a);
     else if (mode == SEG_LEVELS) k_seg<SEG_LEVELS><<<(unsigned)grid, STH, SEG_SMEM, s>>>(a);
+    else if (mode == SEG_MEMBRANE) k_seg<SEG_MEMBRANE><<<(unsigned)grid, STH, SEG_SMEM, s>>>(a);
     else k_seg<SEG_GENERAL><<<(unsigned)grid, STH, SEG_SMEM, s>>>(a);
     prof_end(P, s);
     P.launches += 1;

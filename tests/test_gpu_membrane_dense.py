@@ -100,10 +100,12 @@ def test_dense_membrane_config4_stripes(env):
                 assert err <= 1e-4, (form, j0, err)
 
 
-def test_autotune_picks_dense_for_a_large_membrane(env):
-    """A deformed 0.15 m plate: the dense membrane passes beat the FP32
-    Bluestein form on the probe stripe, and the tuned plan matches the
-    oracle on a stripe."""
+def test_autotune_on_a_large_membrane(env):
+    """A deformed 0.15 m plate: the autotuner times the dense membrane passes
+    (1-, 2- and 4-CTA clusters) and the FP32 Bluestein form (partitioned
+    convolution) on its probe stripe and keeps the faster -- the two are
+    within about 10 % of each other here (at D = 0.05 m, 184 against 194
+    Gsamples/s) -- and the tuned plan matches the oracle on a stripe."""
     fzp, torch, O = env
     import fzp_inputs
     m = fzp_inputs.batch_draws(8, seed=0)[0]
@@ -111,7 +113,10 @@ def test_autotune_picks_dense_for_a_large_membrane(env):
     with fzp.Plan(D=0.15, f=0.75, lam=m.lam, M=256, pitch=m.lam * 5 / 8, precision=fzp.PREC_AUTO_1E4,
                   deform=fzp.make_deform(**d)) as plan:
         info = plan.info
-        assert info["form"] == fzp.FORM_DENSE, info
+        assert (info["form"], info["precision"]) in ((fzp.FORM_DENSE, fzp.PREC_SPLIT_BF16),
+                                                     (fzp.FORM_BLUESTEIN, fzp.PREC_FP32)), info
+        if info["form"] == fzp.FORM_BLUESTEIN:
+            assert info["conv"] == 2
         g = O.Geometry(D=0.15, f=0.75, lam=m.lam, M=256, p=m.lam * 5 / 8, deform=O.Deform(**d))
         j0 = g.c + 300
         _, I = run_plan(fzp, torch, plan, 256, j0, j0 + 256)
