@@ -102,3 +102,48 @@ def test_reference_arm_saczt_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["config"]["workload"] == "saczt-d8mm"
     assert d["config"]["sample_N"] == 2529 and "4096^2" in d["cpu_baseline"]["sample"]
     assert d["e2e"]["value"] == d["value"]
+
+
+def test_partitioned_flop_model():
+    """The partitioned row pass's work count: per row one inverse 4096-point
+    FFT, per block of S columns that meets the row's chord a forward FFT and
+    the spectrum product-sum; the block count checked against a plain loop
+    over rows and columns on a small plate, and the rows' counts add up."""
+    import math
+    import paper_2609_01978_gb300 as fzp
+    import __graft_entry__
+    __graft_entry__.build()
+    q = fzp.plan_query(D=0.01, f=0.05, lam=632.8e-9, M=512, pitch=0.4e-6)
+    info = {"N": q["N"], "c": q["c"], "s_R": q["s_R"], "M": 512}
+    S = 256 * min(15, (4097 - 512) // 256)
+    assert S == 3584
+    N, c, sR = info["N"], info["c"], info["s_R"]
+    blocks = 0
+    for j in range(N):
+        rem = sR - (j - c) ** 2
+        if rem < 0:
+            continue
+        b = math.isqrt(rem)
+        blocks += len({i // S for i in range(max(c - b, 0), min(c + b, N - 1) + 1)})
+    fft = 5.0 * 4096 * 12
+    assert bench.partitioned_flops(info, 0, N) == blocks * (fft + 8.0 * 4096) + N * fft
+    assert bench.partitioned_flops(info, 0, N // 3) + bench.partitioned_flops(info, N // 3, N) == \
+        bench.partitioned_flops(info, 0, N)
+
+
+def test_plan_reports_the_row_convolution():
+    """fzp_plan_query resolves fzp_params.conv: partitioned by default in FP32
+    (4096-point inner transforms), single when asked for or in FP64."""
+    import paper_2609_01978_gb300 as fzp
+    import __graft_entry__
+    __graft_entry__.build()
+    base = dict(D=4e-3, f=20e-3, lam=632.8e-9, M=256, pitch=0.2e-6, form=fzp.FORM_BLUESTEIN)
+    q = fzp.plan_query(precision=fzp.PREC_FP32, **base)
+    assert q["conv"] == 2 and q["fft_inner"] == 4096 and q["fft_length"] == 8192
+    q = fzp.plan_query(precision=fzp.PREC_FP32, conv=fzp.CONV_SINGLE, **base)
+    assert q["conv"] == 1 and q["fft_inner"] == 4096
+    q = fzp.plan_query(precision=fzp.PREC_FP64, **base)
+    assert q["conv"] == 1
+    q = fzp.plan_query(precision=fzp.PREC_SPLIT_BF16, form=fzp.FORM_DENSE,
+                       **{k: v for k, v in base.items() if k != "form"})
+    assert q["conv"] == 0
