@@ -239,6 +239,50 @@ def partitioned_flops(info: dict, j0: int, j1: int) -> float:
     return blocks * (fft + 8.0 * P) + (j1 - j0) * fft
 
 
+def membrane_forms_and_roofline(fzp, infos: list, M: int, steps: int, ms: float):
+    """Forms chosen over a batch of membranes and the roofline of the step:
+    the tensor work of the dense instances (24 M flops per in-disc sample:
+    2 membrane passes x 3 split products x 2 real rows x M x 2 flops) when
+    dense instances are at least half the batch, else the FFT work of the
+    partitioned FP32 instances; either over the whole step's time, so a lower
+    bound for a mixed batch."""
+    forms = {}
+    dense_flops = fft_flops = 0.0
+    n_dense = n_fft = 0
+    for inf in infos:
+        k = ("dense" if inf["form"] == fzp.FORM_DENSE else "bluestein") + "/" + \
+            {0: "f64", 1: "f32", 2: "split-bf16", 3: "bf16"}[inf["precision"]]
+        forms[k] = forms.get(k, 0) + 1
+        if inf["form"] == fzp.FORM_DENSE:
+            dense_flops += 24.0 * M * disc_samples(inf["N"], inf["c"], inf["s_R"], 0, inf["N"])
+            n_dense += 1
+        elif inf["precision"] == fzp.PREC_FP32 and inf["conv"] == 2:
+            fft_flops += partitioned_flops(inf, 0, inf["N"])
+            n_fft += 1
+    peaks, peak_kind = _peaks()
+    whole = "whole step (graph of every instance's passes)"
+    if n_dense and n_dense >= n_fft:
+        achieved = dense_flops * steps / (ms / 1e3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        return forms, {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                       "frac": achieved / peak, "traffic": None,
+                       "kernel": whole + ": tensor work of the dense instances over the whole step's time "
+                                         "(a lower bound when some chose the FP32 form)",
+                       "peak_source": peak_kind + " bf16 sustained",
+                       "work": "24 M flops per aperture sample inside the disc (dense instances only)"}
+    if n_fft:
+        achieved = fft_flops * steps / (ms / 1e3) / 1e12
+        peak = SM_COUNT * 128 * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+        return forms, {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                       "frac": achieved / peak, "traffic": None,
+                       "kernel": whole + ": FFT work of the partitioned FP32 instances over the whole step's "
+                                         "time (a lower bound when some chose the dense form)",
+                       "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                       "work": "per block of S columns meeting a row's chord 5 P log2 P + 8 P, per row "
+                               "5 P log2 P (P = 4096; partitioned FP32 instances only)"}
+    return forms, None
+
+
 def run_membranes(args, fzp, torch, dev, ws, pg, rank, local):
     """Config 4: a batch of deformed membranes (autotuned form per instance), the
     whole batch replayed as one CUDA graph, metrics of every instance per step."""
@@ -286,41 +330,7 @@ def run_membranes(args, fzp, torch, dev, ws, pg, rank, local):
         ms = float(t.item())
     kernels = b.kernels
     b.close()
-    forms = {}
-    dense_flops = fft_flops = 0.0
-    n_dense = n_fft = 0
-    for inf in infos:
-        k = ("dense" if inf["form"] == fzp.FORM_DENSE else "bluestein") + "/" + \
-            {0: "f64", 1: "f32", 2: "split-bf16", 3: "bf16"}[inf["precision"]]
-        forms[k] = forms.get(k, 0) + 1
-        if inf["form"] == fzp.FORM_DENSE:
-            # membrane passes: 2 passes x 3 split products x 2 real rows x M x 2 flops
-            # = 24 M flops per aperture sample inside the disc
-            dense_flops += 24.0 * M * disc_samples(inf["N"], inf["c"], inf["s_R"], 0, inf["N"])
-            n_dense += 1
-        elif inf["precision"] == fzp.PREC_FP32 and inf["conv"] == 2:
-            fft_flops += partitioned_flops(inf, 0, inf["N"])
-            n_fft += 1
-    peaks, peak_kind = _peaks()
-    roof = None
-    whole = "whole step (graph of every instance's passes)"
-    if n_dense and n_dense >= n_fft:
-        achieved = dense_flops * args.steps / (ms / 1e3) / 1e12
-        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": whole + ": tensor work of the dense instances over the whole "
-                                                  "step's time (a lower bound when some chose the FP32 form)",
-                "peak_source": peak_kind + " bf16 sustained",
-                "work": "24 M flops per aperture sample inside the disc (dense instances only)"}
-    elif n_fft:
-        achieved = fft_flops * args.steps / (ms / 1e3) / 1e12
-        peak = SM_COUNT * 128 * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": whole + ": FFT work of the partitioned FP32 instances over the "
-                                                  "whole step's time (a lower bound when some chose the dense form)",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                "work": "per block of S columns meeting a row's chord 5 P log2 P + 8 P, per row 5 P log2 P "
-                        "(P = 4096; partitioned FP32 instances only)"}
+    forms, roof = membrane_forms_and_roofline(fzp, infos, M, args.steps, ms)
     # end to end through the public API with host buffers: batch from host
     # parameters (tuned choices cached in-process), propagate, fields to pinned
     # host memory, every instance's metrics, destroy

@@ -147,3 +147,25 @@ def test_plan_reports_the_row_convolution():
     q = fzp.plan_query(precision=fzp.PREC_SPLIT_BF16, form=fzp.FORM_DENSE,
                        **{k: v for k, v in base.items() if k != "form"})
     assert q["conv"] == 0
+
+
+def test_membrane_batch_roofline_follows_the_majority_form():
+    """The membranes line's roofline: tensor work of the dense instances when
+    they are at least half the batch, else the FFT work of the partitioned
+    FP32 instances, each over the whole step's time."""
+    import paper_2609_01978_gb300 as fzp
+    import __graft_entry__
+    __graft_entry__.build()
+    q = fzp.plan_query(D=0.01, f=0.05, lam=550e-9, M=256, pitch=550e-9 * 5 / 8)
+    base = {"N": q["N"], "c": q["c"], "s_R": q["s_R"], "M": 256}
+    dense = dict(base, form=fzp.FORM_DENSE, precision=fzp.PREC_SPLIT_BF16, conv=0)
+    fp32 = dict(base, form=fzp.FORM_BLUESTEIN, precision=fzp.PREC_FP32, conv=2)
+    ms = 1000.0
+    forms, roof = bench.membrane_forms_and_roofline(fzp, [fp32, fp32, dense], 256, 1, ms)
+    assert forms == {"bluestein/f32": 2, "dense/split-bf16": 1}
+    assert roof["bound"] == "alu"
+    assert abs(roof["achieved"] - 2 * bench.partitioned_flops(fp32, 0, base["N"]) / 1e12) < 1e-9
+    forms, roof = bench.membrane_forms_and_roofline(fzp, [dense, fp32], 256, 2, ms)
+    inside = bench.disc_samples(base["N"], base["c"], base["s_R"], 0, base["N"])
+    assert roof["bound"] == "tensor" and abs(roof["achieved"] - 2 * 24.0 * 256 * inside / 1e12) < 1e-9
+    assert bench.membrane_forms_and_roofline(fzp, [], 256, 1, ms) == ({}, None)
