@@ -122,7 +122,7 @@ __device__ __forceinline__ void dif_pass(float2* x, int P, int logP, int H, int 
       for (int j = 0; j < NE; ++j) {
         if (j & span) continue;
         const float2 u = v[j], w = v[j + span];
-        const float2 w2 = __ldg(tw + ((k0 + (j & (span - 1)) * sig) << tsh));
+        const float2 w2 = tw[(k0 + (j & (span - 1)) * sig) << tsh];
         v[j] = cadd(u, w);
         v[j + span] = cmul(csub(u, w), w2);
       }
@@ -152,7 +152,7 @@ __device__ __forceinline__ void dit_inv_pass(float2* x, int P, int logP, int lsi
 #pragma unroll
       for (int j = 0; j < NE; ++j) {
         if (j & span) continue;
-        float2 w2 = __ldg(tw + ((k0 + (j & (span - 1)) * sig) << tsh));
+        float2 w2 = tw[(k0 + (j & (span - 1)) * sig) << tsh];
         w2.y = -w2.y;
         const float2 u = v[j], b = cmul(v[j + span], w2);
         v[j] = cadd(u, b);
@@ -166,7 +166,7 @@ __device__ __forceinline__ void dit_inv_pass(float2* x, int P, int logP, int lsi
 
 // The row in shared memory, forward (bit-reversed result) or inverse (from
 // bit-reversed order), in passes of four stages and one shorter pass.
-__device__ void row_fft_fwd(float2* x, int P, int logP, const float2* __restrict__ tw) {
+__device__ __forceinline__ void row_fft_fwd(float2* x, int P, int logP, const float2* __restrict__ tw) {
   for (int done = 0; done < logP;) {
     const int r = logP - done < 4 ? logP - done : 4;
     const int lgH = logP - 1 - done;
@@ -181,7 +181,7 @@ __device__ void row_fft_fwd(float2* x, int P, int logP, const float2* __restrict
   }
 }
 
-__device__ void row_fft_inv(float2* x, int P, int logP, const float2* __restrict__ tw) {
+__device__ __forceinline__ void row_fft_inv(float2* x, int P, int logP, const float2* __restrict__ tw) {
   for (int done = 0; done < logP;) {
     const int r = logP - done < 4 ? logP - done : 4;
     switch (r) {
@@ -325,10 +325,22 @@ __device__ __forceinline__ void row_store(float2* __restrict__ dst, const float2
   }
 }
 
+// The twiddle table (P/2 entries) is copied into shared memory behind the
+// row at the start, so the transform passes read it from there.
+__device__ __forceinline__ void tw_load(float2* tws, const float2* __restrict__ tw, int P) {
+  const float4* t4 = reinterpret_cast<const float4*>(tw);
+  for (int i = threadIdx.x; i < P / 4; i += blockDim.x) {
+    const float4 w = __ldg(t4 + i);
+    tws[2 * i] = make_float2(w.x, w.y);
+    tws[2 * i + 1] = make_float2(w.z, w.w);
+  }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(512, 1) k_sa_rows(const SaRowArgs a) {
   extern __shared__ float2 x[];
   const int P = (int)a.P, logP = a.logP;
+  float2* tws = x + (P + P / 32);  // behind the padded row
   const int64_t row = blockIdx.x;
   if (MODE == 0) {
     const int64_t o = a.P / 2 - a.m.mg.c;
@@ -339,20 +351,22 @@ __global__ void __launch_bounds__(512, 1) k_sa_rows(const SaRowArgs a) {
       for (int i = threadIdx.x; i < P / 2; i += blockDim.x) d4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
       return;
     }
+    tw_load(tws, a.tw, P);
     for (int q = threadIdx.x; q < P; q += blockDim.x) {
       const int64_t i = q - o;
       const bool open = i >= 0 && i < a.m.N && sa_open(a.m, dj, i - a.m.mg.c);
       x[spad(q)] = make_float2(open ? 1.0f : 0.0f, 0.0f);
     }
     __syncthreads();
-    row_fft_fwd(x, P, logP, a.tw);
+    row_fft_fwd(x, P, logP, tws);
     row_store(dst, x, P);
     return;
   }
+  tw_load(tws, a.tw, P);
   row_load(x, a.in + row * a.P, P);
   __syncthreads();
   if (MODE == 1) {
-    row_fft_fwd(x, P, logP, a.tw);
+    row_fft_fwd(x, P, logP, tws);
     // this row is the bit-reversed position of fb; element q of fa
     const int rb = sa_brev((int)row, logP), fb = rb < P / 2 ? rb : rb - P;
     for (int q = threadIdx.x; q < P; q += blockDim.x) {
@@ -369,7 +383,7 @@ __global__ void __launch_bounds__(512, 1) k_sa_rows(const SaRowArgs a) {
     }
     __syncthreads();
   }
-  row_fft_inv(x, P, logP, a.tw);
+  row_fft_inv(x, P, logP, tws);
   if (MODE == 2 && a.planar) {
     float4* re = reinterpret_cast<float4*>(a.planar + row * a.P);
     float4* im = reinterpret_cast<float4*>(a.planar + row * a.P + a.P * a.P);
@@ -488,7 +502,7 @@ std::vector<int64_t> exact_thresholds(const Plan& P) {
   return t;
 }
 
-size_t rows_smem(int64_t P) { return (size_t)(P + P / 32) * sizeof(float2); }
+size_t rows_smem(int64_t P) { return (size_t)(P + P / 32 + P / 2) * sizeof(float2); }  // row + twiddles
 
 // 512 threads (a group of 16 elements each per pass, two at P = 16384): the
 // 16 values of a group stay in registers without spilling.
