@@ -9,8 +9,9 @@
 // transmission) are dense candidates as binary amplitude plates (two membrane
 // passes); odd-level phase plates and deformed phase plates have the
 // Bluestein form only.  Results are cached
-// per (N, M, deformed) for the process and, when FZP_TUNE_CACHE names a file,
-// in that file (one "key value..." line per problem).
+// per (N, M, deformed, levels, centre configuration, requested convolution)
+// for the process and, when FZP_TUNE_CACHE names a file, in that file (one
+// "key value..." line per problem).
 //
 // Batch: many apertures of different diameter, wavelength and deformation share
 // one set of device buffers sized for the largest; every instance regenerates
@@ -50,10 +51,12 @@ std::mutex g_tune_mu;
 std::map<std::string, Choice> g_tune;
 bool g_tune_loaded = false;
 
-std::string tune_key(int64_t N, int M, bool deformed, int levels, int centre_open) {
-  char buf[96];
-  snprintf(buf, sizeof(buf), "N=%lld,M=%d,deformed=%d,levels=%d,centre_open=%d", (long long)N, M, deformed ? 1 : 0,
-           levels, centre_open);
+// The request's Bluestein convolution is part of the key: a choice measured
+// with the partitioned convolution does not hold for the single one.
+std::string tune_key(int64_t N, int M, bool deformed, int levels, int centre_open, int conv) {
+  char buf[112];
+  snprintf(buf, sizeof(buf), "N=%lld,M=%d,deformed=%d,levels=%d,centre_open=%d,conv=%d", (long long)N, M,
+           deformed ? 1 : 0, levels, centre_open, conv);
   return buf;
 }
 
@@ -140,7 +143,7 @@ fzp_status autotune(const fzp_params* in, fzp_params* chosen, fzp_plan_t* keep) 
   fzp_status st = validate_and_derive(&probe, geo);
   if (st != FZP_OK) return st;
   const bool deformed = in->deform != nullptr;
-  const std::string key = tune_key(geo.N, geo.M, deformed, geo.levels, geo.mg.centre_open);
+  const std::string key = tune_key(geo.N, geo.M, deformed, geo.levels, geo.mg.centre_open, in->conv);
   *chosen = *in;
   std::lock_guard<std::mutex> lock(g_tune_mu);
   tune_load();
